@@ -1,0 +1,219 @@
+"""Physics pins of the oracle's 3D CTU+CT step (Sec. "MHD in Three
+Dimensions", Steps 1-11, with the App. A MHDTVD flux):
+  * a uniform state is a fixed point, bit for bit;
+  * periodic boxes conserve mass, momentum, energy and face flux (1e-13);
+  * constrained transport keeps div b at rounding level (<= 1e-13 |b|/dx);
+  * x-only data in a 3D box reduces exactly to the independent 1D scheme;
+  * mirror-symmetric and axis-permuted data evolve symmetrically;
+  * the B = 0 limit approaches the exact Sod solution (Toro) at first order;
+  * linear MHD eigenmodes converge at second order (Sec. 'Linear Wave
+    Convergence').
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import exact_riemann
+import linear_waves as lw
+from paper_1701_07452_gb300.initial_conditions import random_box
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b, guard=1e-3):
+    scale = np.maximum(np.abs(b), guard * max(np.abs(b).max(), 1e-300))
+    return float(np.max(np.abs(a - b) / scale))
+
+
+def test_uniform_state_fixed_point(oracle_mod):
+    n = (7, 6, 5)
+    W = np.zeros((5, n[2], n[1], n[0]))
+    W[0], W[1], W[2], W[3], W[4] = 1.3, 0.2, -0.1, 0.05, 0.7
+    bx = np.full((n[2], n[1], n[0] + 1), 0.4)
+    by = np.full((n[2], n[1] + 1, n[0]), -0.3)
+    bz = np.full((n[2] + 1, n[1], n[0]), 0.25)
+    g = oracle_mod.Grid(n, (1.0, 1.0, 1.0))
+    g.load_primitive(W, bx, by, bz)
+    before = g.read()
+    g.advance(4)
+    for a, b in zip(before, g.read()):
+        assert np.array_equal(a, b)
+
+
+def test_conservation_and_divb(oracle_mod):
+    n = (16, 16, 16)
+    st = random_box(n, seed=21)
+    g = oracle_mod.Grid(n, st["length"])
+    g.load_state(st)
+    t0 = g.totals()
+    U0 = g.read()[0]
+    bmax = max(np.abs(st["bx"]).max(), np.abs(st["by"]).max(), np.abs(st["bz"]).max())
+    dx = 1.0
+    for steps in (1, 9, 90):
+        g.advance(steps)
+        assert g.divb_max() <= 1e-13 * bmax / dx, steps
+    t1 = g.totals()
+    mom = float(np.sqrt(U0[1] ** 2 + U0[2] ** 2 + U0[3] ** 2).sum())
+    scale = np.array([np.abs(U0[0]).sum(), mom, mom, mom, np.abs(U0[4]).sum(), bmax * U0[0].size,
+                      bmax * U0[0].size, bmax * U0[0].size])
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
+    assert g.counters() == (0, 0)
+
+
+def x_only_state(n, ny, nz, seed):
+    rng = np.random.default_rng(seed)
+    q = np.zeros((n, 8))  # sweep-frame cells (rho, Mx, My, Mz, E, Bx, By, Bz)
+    rho = 1.0 + 0.2 * rng.uniform(-1, 1, n)
+    v = 0.3 * rng.uniform(-1, 1, (n, 3))
+    p = 0.6 + 0.2 * rng.uniform(-1, 1, n)
+    bxc = 0.7
+    byz = 0.5 * rng.uniform(-1, 1, (n, 2))
+    gam = 5.0 / 3.0
+    q[:, 0] = rho
+    q[:, 1:4] = rho[:, None] * v
+    q[:, 5] = bxc
+    q[:, 6:8] = byz
+    q[:, 4] = p / (gam - 1) + 0.5 * rho * (v ** 2).sum(1) + 0.5 * (bxc ** 2 + (byz ** 2).sum(1))
+    U = np.zeros((5, nz, ny, n))
+    for c in range(5):
+        U[c] = q[:, c][None, None, :]
+    bx = np.full((nz, ny, n + 1), bxc)
+    by = np.broadcast_to(q[:, 6][None, None, :], (nz, ny + 1, n)).copy()
+    bz = np.broadcast_to(q[:, 7][None, None, :], (nz + 1, ny, n)).copy()
+    return q, U, bx, by, bz
+
+
+def test_reduces_to_1d_scheme(oracle_mod):
+    n, ny, nz = 24, 3, 2
+    q, U, bx, by, bz = x_only_state(n, ny, nz, seed=4)
+    g = oracle_mod.Grid((n, ny, nz), (1.0, 0.125, 0.125))
+    g.load(U, bx, by, bz)
+    dt = 0.2 / n
+    q1 = q.copy()
+    for step in range(10):
+        assert g.step(dt) == 0
+        q1 = oracle_mod.step_1d(q1, 0.7, dt, 1.0 / n, 5.0 / 3.0)
+        U3, _, _, _, B3 = g.read()
+        for c in range(5):
+            col = U3[c]
+            assert np.all(col == col[:1, :1, :]), "transverse uniformity lost"
+            if step == 0:
+                assert np.array_equal(col[0, 0], q1[:, c]), c
+            else:
+                assert rel(col[0, 0], q1[:, c]) < 1e-13, (step, c)
+        for c in range(3):
+            assert rel(B3[c, 0, 0], q1[:, 5 + c]) < 1e-13, (step, c)
+
+
+def mirror_x(U, bx, by, bz, B=None):
+    """x -> -x: zone i -> n-1-i, face f -> n-f; v_x, B_y, B_z change sign."""
+    Um = U[..., ::-1].copy()
+    Um[1] *= -1.0
+    bxm = bx[..., ::-1].copy()
+    bym = -by[..., ::-1]
+    bzm = -bz[..., ::-1]
+    if B is None:
+        return Um, bxm, bym, bzm
+    Bm = B[..., ::-1].copy()
+    Bm[1] *= -1.0
+    Bm[2] *= -1.0
+    return Um, bxm, bym, bzm, Bm
+
+
+def test_mirror_symmetry(oracle_mod):
+    n = (12, 10, 8)
+    st = random_box(n, seed=31)
+    a = oracle_mod.Grid(n, st["length"])
+    a.load_state(st)
+    U, bx, by, bz, B = a.read()
+    m = oracle_mod.Grid(n, st["length"])
+    m.load(*mirror_x(U, bx, by, bz))
+    a.advance(3)
+    m.advance(3)
+    ra = a.read()
+    rm = mirror_x(*ra)
+    got = m.read()
+    for x, y in zip(got, rm):
+        assert rel(x, y) < 1e-13
+
+
+def permute(U, bx, by, bz):
+    """Relabel axes x->y->z->x: new (X, Y, Z) = old (Z, X, Y)."""
+    def perm(a):
+        # old [z][y][x] -> new [Z=y][Y=x][X=z]
+        return np.ascontiguousarray(np.transpose(a, (1, 2, 0)))
+    Up = np.stack([perm(U[0]), perm(U[3]), perm(U[1]), perm(U[2]), perm(U[4])])
+    # new bX (faces of new x = old z) = old bz, new bY = old bx, new bZ = old by
+    return Up, perm(bz), perm(bx), perm(by)
+
+
+def test_axis_permutation_symmetry(oracle_mod):
+    n = (10, 8, 6)
+    st = random_box(n, seed=41)
+    a = oracle_mod.Grid(n, (float(n[0]), float(n[1]), float(n[2])))
+    a.load_state(st)
+    U, bx, by, bz, _ = a.read()
+    Up, bxp, byp, bzp = permute(U, bx, by, bz)
+    np_ = (n[2], n[0], n[1])
+    p = oracle_mod.Grid(np_, (float(np_[0]), float(np_[1]), float(np_[2])))
+    p.load(Up, bxp, byp, bzp)
+    a.advance(2)
+    p.advance(2)
+    Ua, bxa, bya, bza, _ = a.read()
+    want = permute(Ua, bxa, bya, bza)
+    got = p.read()[:4]
+    for x, y in zip(got, want):
+        assert rel(x, y) < 1e-12
+
+
+def test_exact_riemann_pinned_to_textbook():
+    with open(os.path.join(GOLD, "sod_star_state.json")) as f:
+        g = json.load(f)
+    ps, us, rl, rr = exact_riemann.star_state(*g["left"], *g["right"], g["gamma"])
+    for got, want in ((ps, g["p_star"]), (us, g["u_star"]), (rl, g["rho_star_left"]),
+                      (rr, g["rho_star_right"])):
+        assert abs(got - want) <= 0.6e-5
+
+
+def sod_l1(oracle_mod, n):
+    W = np.zeros((5, 1, 1, n))
+    x = (np.arange(n) + 0.5) / n
+    W[0, 0, 0] = np.where(x < 0.5, 1.0, 0.125)
+    W[4, 0, 0] = np.where(x < 0.5, 1.0, 0.1)
+    g = oracle_mod.Grid((n, 1, 1), (1.0, 1e3, 1e3), gamma=1.4, bc=(1, 0, 0))
+    g.load_primitive(W, np.zeros((1, 1, n + 1)), np.zeros((1, 2, n)), np.zeros((2, 1, n)))
+    t = g.advance(100000, t_end=0.2)
+    assert abs(t - 0.2) < 1e-14
+    rho = g.read()[0][0, 0, 0]
+    ex = exact_riemann.sample(x, 0.2, 0.5, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+    return float(np.abs(rho - ex[0]).mean())
+
+
+def test_sod_hydro_limit(oracle_mod):
+    errs = [sod_l1(oracle_mod, n) for n in (100, 200, 400)]
+    assert errs[0] < 0.02 and errs[2] < 0.006, errs
+    assert errs[1] < errs[0] / 1.5 and errs[2] < errs[1] / 1.5, errs
+
+
+def wave_1d_error(oracle_mod, mode, n):
+    lam, U, bx, by, bz = lw.state_1d(mode, n)
+    g = oracle_mod.Grid((n, 1, 1), (1.0, 1.0 / n, 1.0 / n), gamma=lw.GAMMA)
+    g.load(U, bx, by, bz)
+    B0 = g.read()[4]
+    T = 1.0 / abs(lam)
+    steps = int(math.ceil(T / (0.8 / n / 3.0)))
+    for _ in range(steps):
+        assert g.step(T / steps) == 0
+    U1, _, _, _, B1 = g.read()
+    return lw.l1_error(U1, U, B1, B0)
+
+
+@pytest.mark.parametrize("mode", ["fast", "alfven", "slow", "entropy"])
+def test_linear_wave_second_order_1d(oracle_mod, mode):
+    errs = [wave_1d_error(oracle_mod, mode, n) for n in (32, 64, 128)]
+    slope = math.log2(errs[1] / errs[2])
+    assert errs[0] > errs[1] > errs[2]
+    assert slope > 1.7, (errs, slope)
