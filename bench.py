@@ -1,0 +1,291 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300-native WOMBAT per-patch ideal-MHD step.
+
+Workload (one GPU): the 256^3 periodic FP64 turbulence box (rho = 1, P = 1,
+solenoidal velocity modes 1 <= |k| <= 8 with amplitude ~ |k|^-2 at rms Mach 1,
+mean field along x at beta 100, 10 % field perturbation from a random vector
+potential), advanced with the CTU+CT MHDTVD step.  One bench "step" is one
+full step of that box: halo fill, CFL dt, six MHDTVD sweeps, EMFs, constrained
+transport and the conservative update.
+
+value      FP64 cell-updates/s with the state resident in HBM (CUDA events,
+           max over ranks); the state (1.6 GB) is larger than L2, so no flush.
+e2e        the same metric through the C ABI with host buffers: every step
+           loads the state from pinned host memory, advances one step and
+           reads the state back (copies inside the timed region).
+roofline   the MHDTVD sweep kernel against the FP64 pipe (the step is FP64
+           bound): algorithmic flops per face x faces per launch / measured
+           launch time, peak = FP64 DFMA probe run in this process.
+cpu_baseline  the plain FP64 oracle timed on the host cores on a bounded
+           sample of the same workload.
+
+--impl reference times the oracle (the slow CPU reading of the paper) as the
+reference arm.  --gpus N > 1 runs N independent replicas of the box, one per
+rank (the path has no data exchange between GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64 cell-updates/s"
+UNIT = "cell-updates/s"
+N_BOX = 256
+SEED = 2
+# FP64 flops the MHDTVD sweep performs per interface (add/sub/mul = 1, fma = 2,
+# div/sqrt/rsqrt = 1), counted from the face formulation of the sweep kernel
+# (see the kernel-level summary under profiles/).
+FLOPS_PER_FACE = 560.0
+
+
+def sweep_faces_per_step(n):
+    """Interfaces the six sweeps of one step must compute (one per zone and
+    direction, predictor and corrector) -- the algorithmic count; the kernel
+    also computes the patch-halo faces, which are not counted."""
+    return 6 * n ** 3
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(s[0]) for s in self.samples if s and s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if len(s) > 1 and s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for name, v in zip(names, s[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_sample(n_sample, steps, threads=0):
+    """Oracle (plain FP64 CPU restatement) on an n_sample^3 box of the same
+    turbulence data: returns (cell-updates/s, wall seconds, threads used)."""
+    import oracle
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box
+    used = oracle.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
+    st = turbulence_box(n_sample, SEED)
+    g = oracle.Grid((n_sample,) * 3, st["length"])
+    g.load_state(st)
+    t0 = time.perf_counter()
+    g.advance(steps)
+    wall = time.perf_counter() - t0
+    return n_sample ** 3 * steps / wall, wall, used
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    n_sample, steps_per = 64, 1
+    vals = []
+    for _ in range(args.warmup):
+        cpu_sample(n_sample, steps_per)
+    t_total = 0.0
+    used = 1
+    for _ in range(args.steps):
+        v, wall, used = cpu_sample(n_sample, steps_per)
+        vals.append(v)
+        t_total += wall
+    value = n_sample ** 3 * steps_per * args.steps / t_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{N_BOX}^3 periodic FP64 MHD turbulence box (CTU+CT MHDTVD)",
+                   "sample": f"{n_sample}^3 box of the same turbulence data, {steps_per} step per bench step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"{n_sample}^3 x {steps_per} step per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_BOX)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_1701_07452_gb300 import binding as wb
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box
+
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    st = turbulence_box(n, SEED + rank)
+    g = wb.Grid((n, n, n), length=st["length"])
+    g.load_state(st)
+    fp64_peak = wb.measure_fp64_peak()
+
+    # ---- device-resident timing --------------------------------------------
+    g.advance(args.warmup, sync=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        g.profile_sweeps(True)
+        e0.record(stream)
+        g.advance(args.steps, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        g.profile_sweeps(False)
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    sweep_ms, sweep_launches = g.profile_read()
+    counters = g.counters()
+    if counters["unphysical"]:
+        raise RuntimeError(f"unphysical state during the bench: {counters}")
+    ms_max = max_over_ranks(ms, world, dev)
+    value = world * n ** 3 * args.steps / (ms_max * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    nx = ny = nz = n
+    pin = dict(dtype=torch.float64, pin_memory=True)
+    U_h = torch.empty((5, nz, ny, nx), **pin)
+    bx_h = torch.empty((nz, ny, nx + 1), **pin)
+    by_h = torch.empty((nz, ny + 1, nx), **pin)
+    bz_h = torch.empty((nz + 1, ny, nx), **pin)
+    B_h = torch.empty((3, nz, ny, nx), **pin)
+    g.read(out=(U_h.numpy(), bx_h.numpy(), by_h.numpy(), bz_h.numpy(), B_h.numpy()))
+    h2d = sum(t.numel() * 8 for t in (U_h, bx_h, by_h, bz_h))
+    d2h = h2d + B_h.numel() * 8
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g.load(U_h.numpy(), bx_h.numpy(), by_h.numpy(), bz_h.numpy())
+        g.advance(1, sync=True)
+        g.read(out=(U_h.numpy(), bx_h.numpy(), by_h.numpy(), bz_h.numpy(), B_h.numpy()))
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = world * n ** 3 * args.e2e_steps / e2e_s
+
+    # ---- CPU baseline: oracle on a bounded sample -------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s, steps_s = 64, 2
+        v, wall, used = cpu_sample(n_s, steps_s)
+        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"{n_s}^3 box of the same turbulence data, {steps_s} steps ({wall:.1f} s)"}
+
+    if rank == 0:
+        per_launch_ms = sweep_ms / max(sweep_launches, 1)
+        faces_per_launch = sweep_faces_per_step(n) / 6.0
+        achieved = FLOPS_PER_FACE * faces_per_launch / (per_launch_ms * 1e-3) / 1e12
+        peak = fp64_peak / 1e12
+        launches_per_step = 26
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded turbulence IC, no dataset)",
+            "config": {"workload": f"{n}^3 periodic FP64 MHD turbulence box, CTU+CT MHDTVD step",
+                       "patches": "1 (single grid)", "l2": "state 1.6 GB > L2, no flush",
+                       "parallelism": "replicas only" if world > 1 else "1 GPU"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": args.e2e_steps},
+            "roofline": {"bound": "alu", "kernel": "k_sweep (MHDTVD flux)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": "FP64 DFMA probe in this process (no FP64 figure in "
+                                        "MEASURED_PEAKS.json)",
+                         "sweep_ms_per_launch": per_launch_ms,
+                         "sweep_share_of_step": sweep_ms / ms},
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "gpu_launches": launches_per_step * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

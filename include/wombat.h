@@ -1,0 +1,156 @@
+/*
+ * wombat.h -- C ABI of the GB300-native (sm_103a) FP64 implementation of the
+ * WOMBAT per-patch ideal-MHD step (Mendygral et al. 2017, arXiv:1701.07452):
+ * the MHDTVD modified flux (Appendix A) inside the 3D CTU+CT 6-solve
+ * integrator (Sec. "MHD in Three Dimensions", Steps 1-11), with 5 boundary
+ * zones per patch filled once per step (Sec. "MHD in Two Dimensions") and a
+ * global CFL time step (Sec. "MPI-RMA Engine": the non-blocking dt reduction).
+ *
+ * Conventions shared by every call
+ *  - All floating point data are IEEE binary64.  Host arrays are row-major
+ *    with x fastest:
+ *      U  [5][nz][ny][nx]   conserved (rho, Mx, My, Mz, E)        (Sec. 3, q)
+ *      W  [5][nz][ny][nx]   primitive (rho, vx, vy, vz, P)
+ *      bx [nz][ny][nx+1], by [nz][ny+1][nx], bz [nz+1][ny][nx]
+ *                           face-centred field; face index f is the low face
+ *                           of zone f, the last face is the high boundary face
+ *      B  [3][nz][ny][nx]   zone-centred field = face averages (Step 11)
+ *  - Units absorb 4 pi (Sec. 3): P* = P + |B|^2/2.
+ *  - Every call returns an int status (WB_OK = 0 or one of WB_ERR_*); details
+ *    of the last failure on a handle are in wb_last_error().  No C++
+ *    exception crosses this boundary.
+ *  - Memory ownership: the caller allocates the device workspace (size from
+ *    wb_grid_bytes) and keeps it alive until wb_grid_destroy; the library
+ *    never allocates device memory for a grid and never frees caller memory.
+ *  - Streams: all device work is enqueued on the stream given at create time
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream).  Calls
+ *    that return host-visible values (dt, totals, t_out, counters) synchronise
+ *    that stream; wb_advance without t_out does not.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef WOMBAT_H
+#define WOMBAT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WB_OK 0
+#define WB_ERR_INVALID 1     /* bad argument or descriptor */
+#define WB_ERR_NOMEM 2       /* workspace smaller than wb_grid_bytes() */
+#define WB_ERR_CUDA 3        /* a CUDA runtime call failed */
+#define WB_ERR_UNPHYSICAL 4  /* rho <= 0, P <= 0 or non-finite state met */
+#define WB_ERR_TIMEOUT 5     /* a bounded device wait ran out */
+
+#define WB_BC_PERIODIC 0
+#define WB_BC_OUTFLOW 1      /* zero-gradient copy of the nearest zone */
+
+/* Grid of equal patches (Sec. "Domain Decomposition": a Patch is a
+ * self-contained sub-grid with its own 5 boundary zones).
+ *  n[d]        global interior zones per axis
+ *  patches[d]  patches per axis; n[d] must be a multiple of patches[d]
+ *  length[d]   box size; dx_d = length[d] / n[d]
+ *  gamma       adiabatic index, 1 < gamma <= 2 (Sec. 3)
+ *  cfl         Courant number of the time step
+ *  bc[d]       WB_BC_PERIODIC or WB_BC_OUTFLOW
+ *  eps[7]      entropy-fix parameters of Q_k (App. A), 0 <= eps < 0.5, waves
+ *              ordered (v-cf, v-ca, v-cs, v, v+cs, v+ca, v+cf)
+ *  sweby_beta  SWEBY limiter parameter, 1 <= beta <= 2 (1 = minmod)
+ *  rho_floor, p_floor  floors applied to the updated state (App. A)
+ *  batch_patches  patches processed together per pipeline pass (0 = all) */
+typedef struct wb_desc {
+  int n[3];
+  int patches[3];
+  double length[3];
+  double gamma;
+  double cfl;
+  int bc[3];
+  double eps[7];
+  double sweby_beta;
+  double rho_floor;
+  double p_floor;
+  int batch_patches;
+} wb_desc;
+
+typedef struct wb_counters_t {
+  long long steps;          /* steps taken since load */
+  long long floor_hits;     /* zones where a floor was applied */
+  long long unphysical;     /* interfaces or zones found unphysical */
+  double t;                 /* simulated time since load */
+  double last_dt;           /* dt of the last step */
+} wb_counters_t;
+
+typedef struct wb_grid wb_grid;
+
+/* Fill *d with the defaults used by this library: gamma 5/3, cfl 0.8,
+ * periodic, eps = (0.1, 0, 0.1, 0, 0.1, 0, 0.1), sweby 1, floors 1e-20. */
+void wb_desc_default(wb_desc* d, int nx, int ny, int nz);
+
+/* Device workspace bytes a grid with descriptor d needs (state, one step's
+ * intermediates for batch_patches patches, staging, reductions). */
+int wb_grid_bytes(const wb_desc* d, size_t* bytes);
+
+/* Create a grid on the current CUDA device inside caller-owned device memory
+ * dev_mem of at least wb_grid_bytes() bytes (256-byte aligned).  stream is a
+ * cudaStream_t (borrowed).  The state is undefined until a load call. */
+int wb_grid_create(const wb_desc* d, void* dev_mem, size_t bytes, void* stream,
+                   wb_grid** out);
+int wb_grid_destroy(wb_grid* g);
+
+/* Load conserved U and faces bx, by, bz (layouts above).  on_device != 0:
+ * the pointers are device memory, else host memory (pinned for overlap).
+ * The zone field is set to the face averages; the high boundary face of
+ * each axis is taken from the ghost fill (periodic: face 0). */
+int wb_load_state(wb_grid* g, const double* U, const double* bx, const double* by,
+                  const double* bz, int on_device);
+/* Same with primitive W = (rho, v, P); E from Eq. totenergy on the device. */
+int wb_load_primitive(wb_grid* g, const double* W, const double* bx, const double* by,
+                      const double* bz, int on_device);
+
+/* CFL time step of the current state: dt = cfl / max over zones of
+ * sum_d (|v_d| + c_f,d) / dx_d, c_f,d the fast speed along d (Sec. 3). */
+int wb_compute_dt(wb_grid* g, double* dt);
+
+/* Advance nsteps CTU+CT steps, each with the CFL dt of its start state,
+ * clipped so that the time since load does not pass t_end (t_end <= 0: no
+ * limit; steps past t_end do nothing).  If t_out != NULL the stream is
+ * synchronised, *t_out receives the time since load and an unphysical state
+ * met during these steps returns WB_ERR_UNPHYSICAL. */
+int wb_advance(wb_grid* g, int nsteps, double t_end, double* t_out);
+
+/* Read back the state (any pointer may be NULL); on_device as for load. */
+int wb_read_state(wb_grid* g, double* U, double* bx, double* by, double* bz, double* B,
+                  int on_device);
+
+/* Conserved totals times zone volume: rho, Mx, My, Mz, E over zones and
+ * bx, by, bz over owned faces (compensated summation on the host). */
+int wb_conserved_totals(wb_grid* g, double tot[8]);
+/* max over zones of |div b| with the face differences of Step 11. */
+int wb_divb_max(wb_grid* g, double* divb);
+int wb_counters(wb_grid* g, wb_counters_t* c);
+const char* wb_last_error(const wb_grid* g);
+
+/* Stage dump of the last step (debugging and parity tests): which = 0..2
+ * predictor fluxes F, G, H; 3..5 corrector fluxes; 6..8 b^{n+1/2}; 9..11
+ * q^{n+1/2}_x,y,z -- same layouts as the oracle's dump (single patch only).
+ * Copies to host memory out (cap doubles); *written = doubles written. */
+int wb_debug_stage(wb_grid* g, int which, double* out, long long cap, long long* written);
+
+/* Kernel timing of the MHDTVD sweep launches (Steps 1, 6, 7): enable != 0
+ * starts recording CUDA events around every sweep launch on the grid's stream
+ * (at most 8192 launches; later ones are not recorded); enable == 0 stops.
+ * wb_profile_read synchronises the stream and returns the summed duration in
+ * milliseconds and the number of recorded launches since the last enable. */
+int wb_profile_sweeps(wb_grid* g, int enable);
+int wb_profile_read(wb_grid* g, double* sweep_ms, long long* launches);
+
+/* FP64 pipe probe: runs a dependent-free DFMA loop on every SM of the
+ * current device and returns the achieved FP64 FLOP/s (FMA = 2 flops). */
+int wb_measure_fp64_peak(void* stream, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of ``libwombat_gb300.so`` (C ABI in include/wombat.h).
+
+Argument marshalling only: every step of the MHD update runs in the
+library's CUDA kernels.  PyTorch provides the device workspace (a uint8
+tensor the caller owns) and the CUDA stream.  There is no CPU fallback: if
+the library cannot be built or loaded, or no CUDA device is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+WB_OK, WB_ERR_INVALID, WB_ERR_NOMEM, WB_ERR_CUDA, WB_ERR_UNPHYSICAL, WB_ERR_TIMEOUT = range(6)
+WB_BC_PERIODIC, WB_BC_OUTFLOW = 0, 1
+DEFAULT_EPS = (0.1, 0.0, 0.1, 0.0, 0.1, 0.0, 0.1)
+
+EXPORTED = (
+    "wb_desc_default", "wb_grid_bytes", "wb_grid_create", "wb_grid_destroy", "wb_load_state",
+    "wb_load_primitive", "wb_compute_dt", "wb_advance", "wb_read_state", "wb_conserved_totals",
+    "wb_divb_max", "wb_counters", "wb_last_error", "wb_debug_stage", "wb_measure_fp64_peak",
+    "wb_profile_sweeps", "wb_profile_read",
+)
+
+
+class WbDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("patches", ctypes.c_int * 3),
+        ("length", ctypes.c_double * 3),
+        ("gamma", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("bc", ctypes.c_int * 3),
+        ("eps", ctypes.c_double * 7),
+        ("sweby_beta", ctypes.c_double),
+        ("rho_floor", ctypes.c_double),
+        ("p_floor", ctypes.c_double),
+        ("batch_patches", ctypes.c_int),
+    ]
+
+
+class WbCounters(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_longlong),
+        ("floor_hits", ctypes.c_longlong),
+        ("unphysical", ctypes.c_longlong),
+        ("t", ctypes.c_double),
+        ("last_dt", ctypes.c_double),
+    ]
+
+
+class WombatError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"wombat error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build: bool = True):
+    """Load (building first if needed) the CUDA library.  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libwombat_gb300.so not found at {path}")
+            L = ctypes.CDLL(path)
+            vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+            L.wb_desc_default.argtypes = [ctypes.POINTER(WbDesc), ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.wb_desc_default.restype = None
+            L.wb_grid_bytes.argtypes = [ctypes.POINTER(WbDesc), ctypes.POINTER(ctypes.c_size_t)]
+            L.wb_grid_create.argtypes = [ctypes.POINTER(WbDesc), vp, ctypes.c_size_t, vp,
+                                         ctypes.POINTER(vp)]
+            L.wb_grid_destroy.argtypes = [vp]
+            L.wb_load_state.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int]
+            L.wb_load_primitive.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int]
+            L.wb_compute_dt.argtypes = [vp, dp]
+            L.wb_advance.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp]
+            L.wb_read_state.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int]
+            L.wb_conserved_totals.argtypes = [vp, dp]
+            L.wb_divb_max.argtypes = [vp, dp]
+            L.wb_counters.argtypes = [vp, ctypes.POINTER(WbCounters)]
+            L.wb_last_error.argtypes = [vp]
+            L.wb_last_error.restype = ctypes.c_char_p
+            L.wb_debug_stage.argtypes = [vp, ctypes.c_int, dp, ctypes.c_longlong,
+                                         ctypes.POINTER(ctypes.c_longlong)]
+            L.wb_measure_fp64_peak.argtypes = [vp, dp]
+            L.wb_profile_sweeps.argtypes = [vp, ctypes.c_int]
+            L.wb_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
+            _lib = L
+    return _lib
+
+
+def make_desc(n, patches=(1, 1, 1), length=None, gamma=5.0 / 3.0, cfl=0.8, bc=(0, 0, 0),
+              eps=DEFAULT_EPS, sweby=1.0, rho_floor=1e-20, p_floor=1e-20, batch_patches=0):
+    d = WbDesc()
+    lib().wb_desc_default(ctypes.byref(d), int(n[0]), int(n[1]), int(n[2]))
+    for a in range(3):
+        d.patches[a] = int(patches[a])
+        d.length[a] = float(length[a] if length is not None else n[a])
+        d.bc[a] = int(bc[a])
+    for k in range(7):
+        d.eps[k] = float(eps[k])
+    d.gamma, d.cfl, d.sweby_beta = float(gamma), float(cfl), float(sweby)
+    d.rho_floor, d.p_floor = float(rho_floor), float(p_floor)
+    d.batch_patches = int(batch_patches)
+    return d
+
+
+def grid_bytes(desc: WbDesc) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().wb_grid_bytes(ctypes.byref(desc), ctypes.byref(out))
+    if rc:
+        raise WombatError(rc, "invalid descriptor")
+    return int(out.value)
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class Grid:
+    """A grid of patches advanced on the current CUDA device.
+
+    The device workspace is a torch uint8 tensor owned by this object (the
+    caller side of the C ABI); the stream is torch's current stream unless
+    one is given."""
+
+    def __init__(self, n, patches=(1, 1, 1), length=None, stream=None, **kw):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("wombat: a CUDA device is required (no CPU fallback)")
+        self.n = tuple(int(x) for x in n)
+        self.desc = make_desc(self.n, patches, length, **kw)
+        self.nbytes = grid_bytes(self.desc)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        rc = lib().wb_grid_create(ctypes.byref(self.desc), ctypes.c_void_p(self.workspace.data_ptr()),
+                                  ctypes.c_size_t(self.nbytes), ctypes.c_void_p(self.stream.cuda_stream),
+                                  ctypes.byref(h))
+        if rc:
+            raise WombatError(rc, "grid create failed")
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().wb_grid_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            msg = lib().wb_last_error(self._h)
+            raise WombatError(rc, msg.decode() if msg else "")
+
+    # -- load / read -------------------------------------------------------
+    def _prep(self, a, shape, on_device):
+        if on_device:
+            assert tuple(a.shape) == shape and a.is_contiguous()
+            return a
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.shape == shape, (a.shape, shape)
+        return a
+
+    def _shapes(self):
+        nx, ny, nz = self.n
+        return (5, nz, ny, nx), (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)
+
+    def load(self, U, bx, by, bz, on_device=False, primitive=False):
+        sU, sx, sy, sz = self._shapes()
+        arrs = [self._prep(U, sU, on_device), self._prep(bx, sx, on_device),
+                self._prep(by, sy, on_device), self._prep(bz, sz, on_device)]
+        fn = lib().wb_load_primitive if primitive else lib().wb_load_state
+        self._check(fn(self._h, *[ctypes.c_void_p(_ptr(a)) for a in arrs], int(bool(on_device))))
+
+    def load_state(self, st):
+        """Load a dict with primitive W and faces (see initial_conditions)."""
+        self.load(st["W"], st["bx"], st["by"], st["bz"], primitive=True)
+
+    def read(self, on_device=False, out=None):
+        sU, sx, sy, sz = self._shapes()
+        nx, ny, nz = self.n
+        if out is None:
+            if on_device:
+                import torch
+                kw = dict(dtype=torch.float64, device=self.device)
+                out = (torch.empty(sU, **kw), torch.empty(sx, **kw), torch.empty(sy, **kw),
+                       torch.empty(sz, **kw), torch.empty((3, nz, ny, nx), **kw))
+            else:
+                out = (np.empty(sU), np.empty(sx), np.empty(sy), np.empty(sz), np.empty((3, nz, ny, nx)))
+        self._check(lib().wb_read_state(self._h, *[ctypes.c_void_p(_ptr(a)) for a in out],
+                                        int(bool(on_device))))
+        return out
+
+    # -- stepping ----------------------------------------------------------
+    def dt(self) -> float:
+        out = ctypes.c_double(0.0)
+        self._check(lib().wb_compute_dt(self._h, ctypes.byref(out)))
+        return out.value
+
+    def advance(self, nsteps: int, t_end: float = 0.0, sync: bool = True):
+        """Enqueue nsteps steps; with sync, wait and return the time since load."""
+        if sync:
+            t = ctypes.c_double(0.0)
+            self._check(lib().wb_advance(self._h, int(nsteps), float(t_end), ctypes.byref(t)))
+            return t.value
+        self._check(lib().wb_advance(self._h, int(nsteps), float(t_end), None))
+        return None
+
+    def totals(self):
+        out = np.zeros(8)
+        self._check(lib().wb_conserved_totals(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def divb_max(self) -> float:
+        out = ctypes.c_double(0.0)
+        self._check(lib().wb_divb_max(self._h, ctypes.byref(out)))
+        return out.value
+
+    def counters(self):
+        c = WbCounters()
+        self._check(lib().wb_counters(self._h, ctypes.byref(c)))
+        return {"steps": c.steps, "floor_hits": c.floor_hits, "unphysical": c.unphysical,
+                "t": c.t, "last_dt": c.last_dt}
+
+    def profile_sweeps(self, enable: bool):
+        self._check(lib().wb_profile_sweeps(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_longlong(0)
+        self._check(lib().wb_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def stage(self, which: int):
+        nx, ny, nz = self.n
+        cap = 8 * (nx + 1) * (ny + 1) * (nz + 1)
+        out = np.empty(cap)
+        w = ctypes.c_longlong(0)
+        self._check(lib().wb_debug_stage(self._h, int(which), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         cap, ctypes.byref(w)))
+        return out[: w.value]
+
+
+def measure_fp64_peak(stream=None) -> float:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double(0.0)
+    rc = lib().wb_measure_fp64_peak(ctypes.c_void_p(s.cuda_stream), ctypes.byref(out))
+    if rc:
+        raise WombatError(rc, "fp64 probe failed")
+    return out.value

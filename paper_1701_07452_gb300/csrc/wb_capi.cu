@@ -1,0 +1,655 @@
+// C ABI and grid manager of the GB300-native WOMBAT step (include/wombat.h).
+// Host code: carves the caller's device workspace into the patch state and the
+// per-batch intermediates, and enqueues the stage kernels of one CTU+CT step
+// (Sec. "MHD in Three Dimensions", Steps 1-11) on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/wombat.h"
+#include "wb_device.cuh"
+#include "wb_internal.h"
+
+struct wb_grid {
+  wb_desc d;
+  WbGeo geo;
+  GridMap map;
+  WbPhys phys;
+  cudaStream_t stream;
+  char* mem;
+  size_t bytes;
+  long long npatch;
+  int S;  // patch slots per pipeline pass
+  double* q[8];
+  double* b[3];
+  // workspace, slot 0 bases (stride geo.V)
+  double* Fp[3][8];
+  double* Fc[3][8];
+  double* Eref[3];
+  double* Eedge[3];
+  double* bh[3];
+  double* qh[3][8];
+  double* Erefh[3];
+  double* Eedgeh[3];
+  double* staging;
+  WbScalars* scal;
+  unsigned long long* red;
+  std::string err;
+  bool loaded;
+  // sweep timing (wb_profile_sweeps)
+  bool prof;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used;
+};
+
+namespace {
+
+const size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t state, work, staging, scalars, total;
+  long long npatch, V;
+  int S;
+};
+
+bool valid_desc(const wb_desc* d, std::string* why) {
+  if (!d) { *why = "null descriptor"; return false; }
+  for (int a = 0; a < 3; ++a) {
+    if (d->n[a] < 1 || d->patches[a] < 1 || d->n[a] % d->patches[a] != 0) {
+      *why = "n must be a positive multiple of patches on every axis";
+      return false;
+    }
+    if (!(d->length[a] > 0.0)) { *why = "length must be positive"; return false; }
+    if (d->bc[a] != WB_BC_PERIODIC && d->bc[a] != WB_BC_OUTFLOW) { *why = "bad bc"; return false; }
+  }
+  if (!(d->gamma > 1.0) || d->gamma > 2.0) { *why = "gamma must be in (1, 2]"; return false; }
+  if (!(d->cfl > 0.0)) { *why = "cfl must be positive"; return false; }
+  for (int k = 0; k < 7; ++k)
+    if (!(d->eps[k] >= 0.0) || !(d->eps[k] < 0.5)) { *why = "eps_k must be in [0, 0.5)"; return false; }
+  if (!(d->sweby_beta >= 1.0) || d->sweby_beta > 2.0) { *why = "sweby_beta must be in [1, 2]"; return false; }
+  if (d->batch_patches < 0) { *why = "batch_patches must be >= 0"; return false; }
+  return true;
+}
+
+WbGeo make_geo(const wb_desc* d) {
+  WbGeo g;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = d->n[a] / d->patches[a];
+    g.pd[a] = g.n[a] + 2 * WB_NG;
+    g.dx[a] = d->length[a] / d->n[a];
+    g.idx[a] = 1.0 / g.dx[a];
+  }
+  g.sy = g.pd[0];
+  g.sz = (long long)g.pd[0] * g.pd[1];
+  g.V = g.sz * g.pd[2];
+  return g;
+}
+
+const int kWorkArrays = 3 * 7 + 3 * 7 + 3 + 3 + 3 + 3 * 8 + 3 + 3;  // 81
+
+Layout layout(const wb_desc* d) {
+  Layout L;
+  WbGeo g = make_geo(d);
+  L.V = g.V;
+  L.npatch = (long long)d->patches[0] * d->patches[1] * d->patches[2];
+  long long S = d->batch_patches > 0 ? d->batch_patches : L.npatch;
+  if (S > L.npatch) S = L.npatch;
+  L.S = (int)S;
+  L.state = align_up(sizeof(double) * (size_t)L.V * L.npatch * 11);
+  L.work = align_up(sizeof(double) * (size_t)L.V * S * kWorkArrays);
+  size_t gmax = (size_t)(d->n[0] + 1) * (d->n[1] + 1) * (d->n[2] + 1);
+  L.staging = align_up(sizeof(double) * gmax);
+  L.scalars = align_up(sizeof(WbScalars) + 64 * sizeof(unsigned long long));
+  L.total = L.state + L.work + L.staging + L.scalars;
+  return L;
+}
+
+WbPhys make_phys(const wb_desc* d) {
+  WbPhys p;
+  p.gamma = d->gamma;
+  p.gm1 = d->gamma - 1.0;
+  p.gm2 = d->gamma - 2.0;
+  p.g_over_gm1 = d->gamma / (d->gamma - 1.0);
+  p.inv_gm1 = 1.0 / (d->gamma - 1.0);
+  p.gm2_over_gm1 = (d->gamma - 2.0) / (d->gamma - 1.0);
+  p.cfl = d->cfl;
+  for (int k = 0; k < 7; ++k) {
+    p.eps[k] = d->eps[k];
+    p.two_eps[k] = 2.0 * d->eps[k];
+    p.inv4eps[k] = d->eps[k] > 0.0 ? 1.0 / (4.0 * d->eps[k]) : 0.0;
+  }
+  p.sweby = d->sweby_beta;
+  p.minmod = d->sweby_beta == 1.0 ? 1 : 0;
+  p.rho_floor = d->rho_floor;
+  p.p_floor = d->p_floor;
+  return p;
+}
+
+int fail(wb_grid* g, int code, const std::string& msg) {
+  if (g) g->err = msg;
+  return code;
+}
+
+int check_cuda(wb_grid* g, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return WB_OK;
+  return fail(g, WB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+WbBox box(int l0, int h0, int l1, int h1, int l2, int h2) {
+  WbBox b;
+  b.lo[0] = l0; b.hi[0] = h0; b.lo[1] = l1; b.hi[1] = h1; b.lo[2] = l2; b.hi[2] = h2;
+  return b;
+}
+
+StageArgs stage_args(wb_grid* g, long long p0, int nslots) {
+  StageArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int c = 0; c < 8; ++c) a.q[c] = g->q[c] + p0 * g->geo.V;
+  for (int c = 0; c < 3; ++c) a.b[c] = g->b[c] + p0 * g->geo.V;
+  a.slot_q = g->geo.V;
+  for (int d = 0; d < 3; ++d) {
+    for (int c = 0; c < 8; ++c) {
+      a.Fp[d][c] = g->Fp[d][c];
+      a.Fc[d][c] = g->Fc[d][c];
+      a.qh[d][c] = g->qh[d][c];
+    }
+    a.Eref[d] = g->Eref[d];
+    a.Eedge[d] = g->Eedge[d];
+    a.bh[d] = g->bh[d];
+    a.Erefh[d] = g->Erefh[d];
+    a.Eedgeh[d] = g->Eedgeh[d];
+  }
+  a.slot_w = g->geo.V;
+  a.geo = g->geo;
+  a.phys = g->phys;
+  a.scal = g->scal;
+  a.nslots = nslots;
+  return a;
+}
+
+SweepArgs sweep_args(wb_grid* g, const StageArgs& s, int dir, bool corr, const WbBox& bx) {
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int c = 0; c < 8; ++c) a.q[c] = corr ? s.qh[dir][c] : s.q[c];
+  a.bn = corr ? s.bh[dir] : s.b[dir];
+  for (int c = 0; c < 8; ++c) a.F[c] = corr ? s.Fc[dir][c] : s.Fp[dir][c];
+  a.slot_in = corr ? s.slot_w : s.slot_q;
+  a.slot_out = s.slot_w;
+  a.geo = g->geo;
+  a.box = bx;
+  a.dt = &g->scal->dt;
+  a.phys = g->phys;
+  a.scal = g->scal;
+  return a;
+}
+
+const size_t kMaxProfiled = 8192;
+
+void sweep(wb_grid* g, int dir, const SweepArgs& a, int nslots) {
+  bool rec = g->prof && g->ev_used + 2 <= g->ev.size();
+  if (rec) cudaEventRecord(g->ev[g->ev_used], g->stream);
+  wb_launch_sweep(dir, a, nslots, g->stream);
+  if (rec) {
+    cudaEventRecord(g->ev[g->ev_used + 1], g->stream);
+    g->ev_used += 2;
+  }
+}
+
+// One pipeline pass (Steps 1-11) over patches [p0, p0 + nslots).
+void enqueue_pass(wb_grid* g, long long p0, int nslots) {
+  cudaStream_t s = g->stream;
+  StageArgs A = stage_args(g, p0, nslots);
+  const int N0 = g->geo.n[0], N1 = g->geo.n[1], N2 = g->geo.n[2];
+  // Step 1: predictor fluxes from q^n
+  sweep(g, 0, sweep_args(g, A, 0, false, box(-3, N0 + 3, -4, N1 + 3, -4, N2 + 3)), nslots);
+  sweep(g, 1, sweep_args(g, A, 1, false, box(-4, N0 + 3, -3, N1 + 3, -4, N2 + 3)), nslots);
+  sweep(g, 2, sweep_args(g, A, 2, false, box(-4, N0 + 3, -4, N1 + 3, -3, N2 + 3)), nslots);
+  // Step 2: reference EMF; Step 3: corner EMFs
+  wb_launch_eref(A, box(-4, N0 + 3, -4, N1 + 3, -4, N2 + 3), s);
+  wb_launch_edge(A, 2, false, box(-3, N0 + 3, -3, N1 + 3, -1, N2), s);
+  wb_launch_edge(A, 1, false, box(-3, N0 + 3, -1, N1, -3, N2 + 3), s);
+  wb_launch_edge(A, 0, false, box(-1, N0, -3, N1 + 3, -3, N2 + 3), s);
+  // Step 4: b^{n+1/2}
+  {
+    WbBox bb[3] = {box(-3, N0 + 3, -1, N1, -1, N2), box(-1, N0, -3, N1 + 3, -1, N2),
+                   box(-1, N0, -1, N1, -3, N2 + 3)};
+    wb_launch_ct(A, false, bb, s);
+  }
+  // Steps 5, 7: transverse-flux preconditioned states
+  wb_launch_transverse(A, 0, box(-3, N0 + 2, -1, N1, -1, N2), s);
+  wb_launch_transverse(A, 1, box(-1, N0, -3, N1 + 2, -1, N2), s);
+  wb_launch_transverse(A, 2, box(-1, N0, -1, N1, -3, N2 + 2), s);
+  // Steps 6, 7: corrector fluxes
+  sweep(g, 0, sweep_args(g, A, 0, true, box(-1, N0 + 1, -1, N1, -1, N2)), nslots);
+  sweep(g, 1, sweep_args(g, A, 1, true, box(-1, N0, -1, N1 + 1, -1, N2)), nslots);
+  sweep(g, 2, sweep_args(g, A, 2, true, box(-1, N0, -1, N1, -1, N2 + 1)), nslots);
+  // Step 8: half-step reference EMF; Step 9: corner EMFs
+  wb_launch_eref_half(A, box(-1, N0, -1, N1, -1, N2), s);
+  wb_launch_edge(A, 2, true, box(0, N0, 0, N1, 0, N2 - 1), s);
+  wb_launch_edge(A, 1, true, box(0, N0, 0, N1 - 1, 0, N2), s);
+  wb_launch_edge(A, 0, true, box(0, N0 - 1, 0, N1, 0, N2), s);
+  // Step 11 (faces), then Step 10 + zone field + floors + next signal rate
+  {
+    WbBox bb[3] = {box(0, N0, 0, N1 - 1, 0, N2 - 1), box(0, N0 - 1, 0, N1, 0, N2 - 1),
+                   box(0, N0 - 1, 0, N1 - 1, 0, N2)};
+    wb_launch_ct(A, true, bb, s);
+  }
+  wb_launch_final(A, s);
+}
+
+int sync(wb_grid* g, const char* where) {
+  return check_cuda(g, cudaStreamSynchronize(g->stream), where);
+}
+
+int load_common(wb_grid* g, const double* U, const double* bx, const double* by,
+                const double* bz, int on_device, bool primitive) {
+  if (!g || !U || !bx || !by || !bz) return fail(g, WB_ERR_INVALID, "null argument");
+  cudaStream_t s = g->stream;
+  const long long nc = (long long)g->d.n[0] * g->d.n[1] * g->d.n[2];
+  const double* faces[3] = {bx, by, bz};
+  for (int comp = 0; comp < 8; ++comp) {
+    long long ext[3] = {g->d.n[0], g->d.n[1], g->d.n[2]};
+    const double* src;
+    if (comp < 5) src = U + comp * nc;
+    else { ext[comp - 5] += 1; src = faces[comp - 5]; }
+    long long n = ext[0] * ext[1] * ext[2];
+    const double* dsrc = src;
+    if (!on_device) {
+      cudaError_t e = cudaMemcpyAsync(g->staging, src, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return check_cuda(g, e, "load copy");
+      dsrc = g->staging;
+    }
+    double* dst = comp < 5 ? g->q[comp] : g->b[comp - 5];
+    wb_launch_scatter(dsrc, dst, comp, g->geo, g->map, s);
+    if (!on_device) {
+      // staging is reused by the next component
+      int rc = sync(g, "load");
+      if (rc) return rc;
+    }
+  }
+  wb_launch_halo(g->q, g->b, g->geo, g->map, s);
+  wb_launch_ccb(g->q, g->b, g->geo, g->npatch, s);
+  if (primitive) wb_launch_prim_to_cons(g->q, g->geo, g->npatch, g->phys, s);
+  wb_launch_halo(g->q, g->b, g->geo, g->map, s);
+  WbScalars z;
+  std::memset(&z, 0, sizeof(z));
+  cudaError_t e = cudaMemcpyAsync(g->scal, &z, sizeof(z), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return check_cuda(g, e, "load scalars");
+  wb_launch_dt_init(g->q, g->geo, g->npatch, g->phys, g->scal, s);
+  int rc = sync(g, "load");
+  if (rc) return rc;
+  g->loaded = true;
+  return check_cuda(g, cudaGetLastError(), "load kernels");
+}
+
+}  // namespace
+
+extern "C" {
+
+void wb_desc_default(wb_desc* d, int nx, int ny, int nz) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->n[0] = nx; d->n[1] = ny; d->n[2] = nz;
+  d->patches[0] = d->patches[1] = d->patches[2] = 1;
+  d->length[0] = nx; d->length[1] = ny; d->length[2] = nz;
+  d->gamma = 5.0 / 3.0;
+  d->cfl = 0.8;
+  const double eps[7] = {0.1, 0.0, 0.1, 0.0, 0.1, 0.0, 0.1};
+  for (int k = 0; k < 7; ++k) d->eps[k] = eps[k];
+  d->sweby_beta = 1.0;
+  d->rho_floor = 1e-20;
+  d->p_floor = 1e-20;
+  d->batch_patches = 0;
+}
+
+int wb_grid_bytes(const wb_desc* d, size_t* bytes) {
+  std::string why;
+  if (!bytes || !valid_desc(d, &why)) return WB_ERR_INVALID;
+  *bytes = layout(d).total;
+  return WB_OK;
+}
+
+int wb_grid_create(const wb_desc* d, void* dev_mem, size_t bytes, void* stream, wb_grid** out) {
+  std::string why;
+  if (!out) return WB_ERR_INVALID;
+  *out = nullptr;
+  if (!valid_desc(d, &why)) return WB_ERR_INVALID;
+  if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) % kAlign) != 0) return WB_ERR_INVALID;
+  Layout L = layout(d);
+  if (bytes < L.total) return WB_ERR_NOMEM;
+  wb_grid* g = new (std::nothrow) wb_grid();
+  if (!g) return WB_ERR_NOMEM;
+  g->d = *d;
+  g->geo = make_geo(d);
+  for (int a = 0; a < 3; ++a) {
+    g->map.N[a] = d->n[a];
+    g->map.np[a] = d->patches[a];
+    g->map.bc[a] = d->bc[a];
+  }
+  g->map.npatch = L.npatch;
+  g->npatch = L.npatch;
+  g->S = L.S;
+  g->phys = make_phys(d);
+  g->stream = reinterpret_cast<cudaStream_t>(stream);
+  g->mem = reinterpret_cast<char*>(dev_mem);
+  g->bytes = bytes;
+  const size_t V = (size_t)g->geo.V;
+  double* st = reinterpret_cast<double*>(g->mem);
+  for (int c = 0; c < 8; ++c) g->q[c] = st + (size_t)c * V * L.npatch;
+  for (int c = 0; c < 3; ++c) g->b[c] = st + (size_t)(8 + c) * V * L.npatch;
+  double* w = reinterpret_cast<double*>(g->mem + L.state);
+  size_t slab = V * (size_t)L.S;
+  size_t k = 0;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c) g->Fp[dd][c] = (c == F_BX + dd) ? nullptr : w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c) g->Fc[dd][c] = (c == F_BX + dd) ? nullptr : w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd) g->Eref[dd] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd) g->Eedge[dd] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd) g->bh[dd] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c) g->qh[dd][c] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd) g->Erefh[dd] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd) g->Eedgeh[dd] = w + slab * k++;
+  g->staging = reinterpret_cast<double*>(g->mem + L.state + L.work);
+  g->scal = reinterpret_cast<WbScalars*>(g->mem + L.state + L.work + L.staging);
+  g->red = reinterpret_cast<unsigned long long*>(g->scal + 1);
+  g->loaded = false;
+  g->prof = false;
+  g->ev_used = 0;
+  // NaN-poison the workspace so that any read of an uncomputed value shows
+  cudaError_t e = cudaMemsetAsync(g->mem, 0xff, L.state + L.work, g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->scal, 0, L.scalars, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) {
+    delete g;
+    return WB_ERR_CUDA;
+  }
+  *out = g;
+  return WB_OK;
+}
+
+int wb_grid_destroy(wb_grid* g) {
+  if (!g) return WB_OK;
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  delete g;
+  return WB_OK;
+}
+
+int wb_profile_sweeps(wb_grid* g, int enable) {
+  if (!g) return WB_ERR_INVALID;
+  if (enable) {
+    if (g->ev.empty()) {
+      g->ev.resize(2 * kMaxProfiled);
+      for (auto& e : g->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(g, WB_ERR_CUDA, "event create");
+    }
+    g->ev_used = 0;
+  }
+  g->prof = enable != 0;
+  return WB_OK;
+}
+
+int wb_profile_read(wb_grid* g, double* sweep_ms, long long* launches) {
+  if (!g || !sweep_ms || !launches) return fail(g, WB_ERR_INVALID, "null argument");
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return check_cuda(g, e, "profile");
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < g->ev_used; i += 2) {
+    float ms = 0.0f;
+    e = cudaEventElapsedTime(&ms, g->ev[i], g->ev[i + 1]);
+    if (e != cudaSuccess) return check_cuda(g, e, "profile");
+    tot += ms;
+  }
+  *sweep_ms = tot;
+  *launches = (long long)(g->ev_used / 2);
+  return WB_OK;
+}
+
+int wb_load_state(wb_grid* g, const double* U, const double* bx, const double* by,
+                  const double* bz, int on_device) {
+  return load_common(g, U, bx, by, bz, on_device, false);
+}
+
+int wb_load_primitive(wb_grid* g, const double* W, const double* bx, const double* by,
+                      const double* bz, int on_device) {
+  return load_common(g, W, bx, by, bz, on_device, true);
+}
+
+int wb_compute_dt(wb_grid* g, double* dt) {
+  if (!g || !dt) return fail(g, WB_ERR_INVALID, "null argument");
+  if (!g->loaded) return fail(g, WB_ERR_INVALID, "no state loaded");
+  unsigned long long bits = 0;
+  cudaError_t e = cudaMemcpyAsync(&bits, &g->scal->wmax_next, sizeof(bits), cudaMemcpyDeviceToHost,
+                                  g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return check_cuda(g, e, "compute_dt");
+  double w;
+  std::memcpy(&w, &bits, sizeof(w));
+  if (!(w > 0.0) || !std::isfinite(w)) return fail(g, WB_ERR_UNPHYSICAL, "no finite signal speed");
+  *dt = g->d.cfl / w;
+  return WB_OK;
+}
+
+int wb_advance(wb_grid* g, int nsteps, double t_end, double* t_out) {
+  if (!g || nsteps < 0) return fail(g, WB_ERR_INVALID, "bad argument");
+  if (!g->loaded) return fail(g, WB_ERR_INVALID, "no state loaded");
+  cudaStream_t s = g->stream;
+  cudaError_t e;
+  long long unph0 = 0;
+  if (t_out) {
+    e = cudaMemcpyAsync(&unph0, &g->scal->unphysical, sizeof(unph0), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return check_cuda(g, e, "advance");
+  }
+  for (int st = 0; st < nsteps; ++st) {
+    wb_launch_dt_step(g->scal, g->d.cfl, t_end, s);
+    for (long long p0 = 0; p0 < g->npatch; p0 += g->S) {
+      int ns = (int)std::min<long long>(g->S, g->npatch - p0);
+      enqueue_pass(g, p0, ns);
+    }
+    wb_launch_halo(g->q, g->b, g->geo, g->map, s);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return check_cuda(g, e, "advance launch");
+  if (t_out) {
+    WbScalars sc;
+    e = cudaMemcpyAsync(&sc, g->scal, sizeof(sc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return check_cuda(g, e, "advance");
+    *t_out = sc.t;
+    if (sc.unphysical > unph0) return fail(g, WB_ERR_UNPHYSICAL, "unphysical state met");
+  }
+  return WB_OK;
+}
+
+int wb_read_state(wb_grid* g, double* U, double* bx, double* by, double* bz, double* B,
+                  int on_device) {
+  if (!g) return WB_ERR_INVALID;
+  if (!g->loaded) return fail(g, WB_ERR_INVALID, "no state loaded");
+  cudaStream_t s = g->stream;
+  const long long nc = (long long)g->d.n[0] * g->d.n[1] * g->d.n[2];
+  double* faces[3] = {bx, by, bz};
+  for (int comp = 0; comp < 11; ++comp) {
+    double* dst;
+    int mcomp = comp;
+    const double* src;
+    long long ext[3] = {g->d.n[0], g->d.n[1], g->d.n[2]};
+    if (comp < 5) { if (!U) continue; dst = U + comp * nc; src = g->q[comp]; }
+    else if (comp < 8) {
+      if (!faces[comp - 5]) continue;
+      dst = faces[comp - 5]; src = g->b[comp - 5]; ext[comp - 5] += 1;
+    } else {
+      if (!B) continue;
+      dst = B + (comp - 8) * nc; src = g->q[F_BX + comp - 8]; mcomp = 0;
+    }
+    long long n = ext[0] * ext[1] * ext[2];
+    double* ddst = on_device ? dst : g->staging;
+    wb_launch_gather(src, ddst, mcomp, g->geo, g->map, s);
+    if (!on_device) {
+      cudaError_t e = cudaMemcpyAsync(dst, g->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return check_cuda(g, e, "read");
+    }
+  }
+  return check_cuda(g, cudaGetLastError(), "read");
+}
+
+int wb_conserved_totals(wb_grid* g, double tot[8]) {
+  if (!g || !tot) return fail(g, WB_ERR_INVALID, "null argument");
+  const int nx = g->d.n[0], ny = g->d.n[1], nz = g->d.n[2];
+  const long long nc = (long long)nx * ny * nz;
+  std::vector<double> U(5 * nc), bx((size_t)(nx + 1) * ny * nz), by((size_t)nx * (ny + 1) * nz),
+      bz((size_t)nx * ny * (nz + 1));
+  int rc = wb_read_state(g, U.data(), bx.data(), by.data(), bz.data(), nullptr, 0);
+  if (rc) return rc;
+  double vol = (g->d.length[0] / nx) * (g->d.length[1] / ny) * (g->d.length[2] / nz);
+  auto neumaier = [](const double* x, long long n, long long stride_skip, long long period) {
+    double s = 0.0, c = 0.0;
+    for (long long i = 0; i < n; ++i) {
+      if (period > 0 && (i % period) == stride_skip) continue;
+      double t = s + x[i];
+      if (std::fabs(s) >= std::fabs(x[i])) c += (s - t) + x[i];
+      else c += (x[i] - t) + s;
+      s = t;
+    }
+    return s + c;
+  };
+  for (int c = 0; c < 5; ++c) tot[c] = neumaier(U.data() + c * nc, nc, -1, 0) * vol;
+  // owned faces only: skip the high boundary face of the face axis
+  {
+    double s = 0.0, cc = 0.0;
+    for (long long i = 0; i < (long long)bx.size(); ++i) {
+      if (i % (nx + 1) == nx) continue;
+      double t = s + bx[i];
+      if (std::fabs(s) >= std::fabs(bx[i])) cc += (s - t) + bx[i]; else cc += (bx[i] - t) + s;
+      s = t;
+    }
+    tot[5] = (s + cc) * vol;
+  }
+  {
+    double s = 0.0, cc = 0.0;
+    for (long long i = 0; i < (long long)by.size(); ++i) {
+      if ((i / nx) % (ny + 1) == ny) continue;
+      double t = s + by[i];
+      if (std::fabs(s) >= std::fabs(by[i])) cc += (s - t) + by[i]; else cc += (by[i] - t) + s;
+      s = t;
+    }
+    tot[6] = (s + cc) * vol;
+  }
+  tot[7] = neumaier(bz.data(), (long long)nx * ny * nz, -1, 0) * vol;
+  return WB_OK;
+}
+
+int wb_divb_max(wb_grid* g, double* divb) {
+  if (!g || !divb) return fail(g, WB_ERR_INVALID, "null argument");
+  cudaStream_t s = g->stream;
+  cudaError_t e = cudaMemsetAsync(g->red, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return check_cuda(g, e, "divb");
+  wb_launch_divb(g->b, g->geo, g->npatch, g->red, s);
+  unsigned long long bits = 0;
+  e = cudaMemcpyAsync(&bits, g->red, sizeof(bits), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return check_cuda(g, e, "divb");
+  std::memcpy(divb, &bits, sizeof(double));
+  return WB_OK;
+}
+
+int wb_counters(wb_grid* g, wb_counters_t* c) {
+  if (!g || !c) return fail(g, WB_ERR_INVALID, "null argument");
+  WbScalars sc;
+  cudaError_t e = cudaMemcpyAsync(&sc, g->scal, sizeof(sc), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return check_cuda(g, e, "counters");
+  c->steps = sc.steps;
+  c->floor_hits = sc.floor_hits;
+  c->unphysical = sc.unphysical;
+  c->t = sc.t;
+  c->last_dt = sc.dt;
+  return WB_OK;
+}
+
+const char* wb_last_error(const wb_grid* g) {
+  if (!g) return "null grid";
+  return g->err.c_str();
+}
+
+int wb_debug_stage(wb_grid* g, int which, double* out, long long cap, long long* written) {
+  if (!g || !out || !written) return fail(g, WB_ERR_INVALID, "null argument");
+  if (g->npatch != 1) return fail(g, WB_ERR_INVALID, "stage dump needs a single patch");
+  const int* n = g->geo.n;
+  std::vector<const double*> arrays;
+  WbBox bx = box(0, n[0] - 1, 0, n[1] - 1, 0, n[2] - 1);
+  if (which >= 0 && which < 6) {
+    int d = which % 3;
+    for (int c = 0; c < 8; ++c) arrays.push_back(which < 3 ? g->Fp[d][c] : g->Fc[d][c]);
+    bx.hi[d] += 1;
+  } else if (which >= 6 && which < 9) {
+    int d = which - 6;
+    arrays.push_back(g->bh[d]);
+    bx.hi[d] += 1;
+  } else if (which >= 9 && which < 12) {
+    for (int c = 0; c < 8; ++c) arrays.push_back(g->qh[which - 9][c]);
+  } else {
+    return fail(g, WB_ERR_INVALID, "bad stage");
+  }
+  long long per = (long long)(bx.hi[0] + 1) * (bx.hi[1] + 1) * (bx.hi[2] + 1);
+  long long need = per * (long long)arrays.size();
+  if (cap < need) return fail(g, WB_ERR_INVALID, "output too small");
+  const double nanv = std::nan("");
+  for (size_t a = 0; a < arrays.size(); ++a) {
+    if (!arrays[a]) {
+      for (long long i = 0; i < per; ++i) out[a * per + i] = (which < 6) ? 0.0 : nanv;
+      continue;
+    }
+    wb_launch_copy_box(arrays[a], 0, g->geo, bx, g->staging, g->stream);
+    cudaError_t e = cudaMemcpyAsync(out + a * per, g->staging, sizeof(double) * per,
+                                    cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return check_cuda(g, e, "stage");
+  }
+  *written = need;
+  return WB_OK;
+}
+
+int wb_measure_fp64_peak(void* stream, double* flops) {
+  if (!flops) return WB_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return WB_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return WB_ERR_CUDA;
+  // the probe is a diagnostic outside any grid: it uses a small buffer of its own
+  const int blocks = sms * 4, iters = 1500;
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * blocks * 256) != cudaSuccess) return WB_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  wb_launch_fp64_probe(buf, blocks, 20, s);
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    cudaEventRecord(e0, s);
+    wb_launch_fp64_probe(buf, blocks, iters, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (err != cudaSuccess) return WB_ERR_CUDA;
+  *flops = 2.0 * 8 * 16 * (double)iters * blocks * 256 / (best * 1e-3);
+  return WB_OK;
+}
+
+}  // extern "C"

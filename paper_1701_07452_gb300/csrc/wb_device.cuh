@@ -1,0 +1,86 @@
+// Device-side definitions shared by the CUDA translation units of the
+// GB300-native WOMBAT step (Mendygral et al. 2017, arXiv:1701.07452).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define WB_NG 5  // boundary zones per patch (Sec. "MHD in Two Dimensions")
+
+// zone-centred state fields
+enum { F_RHO = 0, F_MX = 1, F_MY = 2, F_MZ = 3, F_EN = 4, F_BX = 5, F_BY = 6, F_BZ = 7 };
+
+struct WbPhys {
+  double gamma, gm1, gm2, g_over_gm1, inv_gm1, gm2_over_gm1, cfl;
+  double eps[7], two_eps[7], inv4eps[7];
+  double sweby;
+  int minmod;  // sweby == 1
+  double rho_floor, p_floor;
+};
+
+// Geometry of one patch and its padded storage (x fastest).
+struct WbGeo {
+  int n[3];         // interior zones
+  int pd[3];        // padded dims n + 2 NG
+  long long sy, sz; // strides of j and k
+  long long V;      // padded volume (doubles per field per patch)
+  double dx[3], idx[3];
+};
+
+__host__ __device__ __forceinline__ long long wb_at(const WbGeo& g, int i, int j, int k) {
+  return (long long)(k + WB_NG) * g.sz + (long long)(j + WB_NG) * g.sy + (i + WB_NG);
+}
+
+template <int D>
+__host__ __device__ __forceinline__ long long wb_stride(const WbGeo& g) {
+  return D == 0 ? 1LL : (D == 1 ? g.sy : g.sz);
+}
+
+// Inclusive index box relative to the patch interior.
+struct WbBox {
+  int lo[3], hi[3];
+};
+
+// Device scalars of a grid (time step control and error counters).
+struct WbScalars {
+  double dt;              // dt of the current step (0 = skip)
+  double t;               // time since load
+  unsigned long long wmax_bits;  // max signal rate of the state (bits of a double >= 0)
+  unsigned long long wmax_next;  // accumulated by the final update for the next step
+  long long steps;
+  long long floor_hits;
+  long long unphysical;
+  long long timeouts;
+};
+
+__device__ __forceinline__ double wb_sgn(double x) { return x >= 0.0 ? 1.0 : -1.0; }
+
+// magnitude comparison on the IEEE bit pattern (integer pipe): |a| < |b|
+__device__ __forceinline__ bool wb_abs_less(double a, double b) {
+  unsigned long long ua = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffULL;
+  unsigned long long ub = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffULL;
+  return ua < ub;
+}
+
+// minmod(a, b) on the integer pipe: the argument of smaller magnitude when the
+// signs agree, else 0 (the SWEBY limiter with beta = 1, App. A).
+__device__ __forceinline__ double wb_minmod(double a, double b) {
+  long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  double r = wb_abs_less(a, b) ? a : b;
+  return ((ia ^ ib) >= 0) ? r : 0.0;
+}
+
+// SWEBY limiter g = SIGN(a) max(0, min(beta|a|, s b), min(|a|, beta s b)), s = SIGN(a)
+__device__ __forceinline__ double wb_sweby(double a, double b, double beta, int minmod) {
+  if (minmod) return wb_minmod(a, b);
+  double s = wb_sgn(a);
+  double aa = fabs(a);
+  double m1 = fmin(beta * aa, s * b);
+  double m2 = fmin(aa, beta * s * b);
+  return s * fmax(0.0, fmax(m1, m2));
+}
+
+// atomic max of a non-negative double through its bit pattern (exact, order independent)
+__device__ __forceinline__ void wb_atomic_max_pos(unsigned long long* addr, double v) {
+  if (v >= 0.0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+  else if (!(v >= 0.0) && v != v) atomicMax(addr, 0x7ff8000000000000ULL);  // NaN poisons
+}

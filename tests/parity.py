@@ -1,0 +1,31 @@
+"""Parity metric shared by the GPU tests: per-zone relative difference with a
+guard for sign-changing components, |g - o| / max(|o|, 1e-3 max_box |o|),
+taken over every variable of the state.  The guard keeps the metric a
+relative one wherever a component is at least 0.1 % of its box maximum; below
+that it bounds the absolute error by 1e-3 max|o| times the tolerance.  (The
+GPU contracts multiply-adds, the oracle does not, so zones where a momentum
+or field component crosses zero carry rounding differences of a few ulps of
+the box scale, which no finite relative bound without a guard can accept.)"""
+import numpy as np
+
+
+def rel_err(g, o, guard=1e-3):
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    scale = np.maximum(np.abs(o), guard * max(np.abs(o).max(), 1e-300))
+    return float(np.max(np.abs(g - o) / scale))
+
+
+def state_err(gs, os_):
+    """gs, os_: (U, bx, by, bz, B) tuples; worst rel_err over variables."""
+    worst = 0.0
+    U1, U2 = gs[0], os_[0]
+    for c in range(U1.shape[0]):
+        worst = max(worst, rel_err(U1[c], U2[c]))
+    for a, b in zip(gs[1:], os_[1:]):
+        if a.ndim == 4:
+            for c in range(a.shape[0]):
+                worst = max(worst, rel_err(a[c], b[c]))
+        else:
+            worst = max(worst, rel_err(a, b))
+    return worst
