@@ -272,8 +272,7 @@ def main():
                     "steps": args.e2e_steps},
             "roofline": {"bound": "alu", "kernel": "k_sweep (MHDTVD flux)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": "FP64 DFMA probe in this process (no FP64 figure in "
-                                        "MEASURED_PEAKS.json)",
+                         "peak_source": "FP64 DFMA probe run in this process",
                          "sweep_ms_per_launch": per_launch_ms,
                          "sweep_share_of_step": sweep_ms / ms},
             "cpu_baseline": cpu,
