@@ -146,6 +146,36 @@ int wb_debug_stage(wb_grid* g, int which, double* out, long long cap, long long*
 int wb_profile_sweeps(wb_grid* g, int enable);
 int wb_profile_read(wb_grid* g, double* sweep_ms, long long* launches);
 
+/* One CTU+CT step of a single small box that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (code running while a stream is being captured into
+ * a CUDA graph, allocator-restricted plug-ins, or hosts that hand over only
+ * device buffers), so it cannot size a wb_grid workspace for them.  Its
+ * intermediates live in a static device array of 24 MiB inside this library
+ * (held by every GPU that loads the library until process exit).  A box
+ * needs about 736 (nx+10)(ny+10)(nz+10) + 8 (nx+1)(ny+1)(nz+1) bytes of it
+ * (state, one step's intermediates, reductions), so cubes up to 22^3
+ * interior zones fit; larger boxes return WB_ERR_INVALID with a message in
+ * wb_noalloc_last_error().
+ *  d        descriptor of one box: patches must be (1,1,1); batch_patches is
+ *           ignored
+ *  U, bx, by, bz          device input state (layouts above)
+ *  U_out, bx_out, by_out, bz_out   device outputs after one step with the
+ *           CFL dt of the input (same layouts; may alias nothing else)
+ *  dt_out   device double receiving the dt used (may be NULL)
+ *  stream   cudaStream_t on which the work is enqueued; the call does not
+ *           synchronise and does not report unphysical states (they show as
+ *           non-finite outputs).
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call on a device shares the one array: calls whose GPU work overlaps
+ * (other streams, other threads) race and corrupt each other's results, so
+ * serialise them on one stream. */
+int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const double* by,
+                    const double* bz, double* U_out, double* bx_out, double* by_out,
+                    double* bz_out, double* dt_out, void* stream);
+const char* wb_noalloc_last_error(void);
+
 /* FP64 pipe probe: runs a dependent-free DFMA loop on every SM of the
  * current device and returns the achieved FP64 FLOP/s (FMA = 2 flops). */
 int wb_measure_fp64_peak(void* stream, double* flops);

@@ -24,7 +24,7 @@ EXPORTED = (
     "wb_desc_default", "wb_grid_bytes", "wb_grid_create", "wb_grid_destroy", "wb_load_state",
     "wb_load_primitive", "wb_compute_dt", "wb_advance", "wb_read_state", "wb_conserved_totals",
     "wb_divb_max", "wb_counters", "wb_last_error", "wb_debug_stage", "wb_measure_fp64_peak",
-    "wb_profile_sweeps", "wb_profile_read",
+    "wb_profile_sweeps", "wb_profile_read", "wb_step_noalloc", "wb_noalloc_last_error",
 )
 
 
@@ -99,6 +99,9 @@ def lib(build: bool = True):
             L.wb_measure_fp64_peak.argtypes = [vp, dp]
             L.wb_profile_sweeps.argtypes = [vp, ctypes.c_int]
             L.wb_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
+            L.wb_step_noalloc.argtypes = [ctypes.POINTER(WbDesc)] + [vp] * 10
+            L.wb_noalloc_last_error.argtypes = []
+            L.wb_noalloc_last_error.restype = ctypes.c_char_p
             _lib = L
     return _lib
 
@@ -266,6 +269,19 @@ class Grid:
         self._check(lib().wb_debug_stage(self._h, int(which), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          cap, ctypes.byref(w)))
         return out[: w.value]
+
+
+def step_noalloc(desc: WbDesc, U, bx, by, bz, U_out, bx_out, by_out, bz_out, dt_out=None,
+                 stream=None):
+    """One step of a small single box through wb_step_noalloc (device tensors
+    in and out; no device memory is allocated by the library)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    args = [U, bx, by, bz, U_out, bx_out, by_out, bz_out, dt_out]
+    rc = lib().wb_step_noalloc(ctypes.byref(desc), *[ctypes.c_void_p(_ptr(a)) for a in args],
+                               ctypes.c_void_p(s.cuda_stream))
+    if rc:
+        raise WombatError(rc, lib().wb_noalloc_last_error().decode())
 
 
 def measure_fp64_peak(stream=None) -> float:

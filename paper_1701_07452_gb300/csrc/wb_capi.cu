@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -649,6 +650,143 @@ int wb_measure_fp64_peak(void* stream, double* flops) {
   cudaFree(buf);
   if (err != cudaSuccess) return WB_ERR_CUDA;
   *flops = 2.0 * 8 * 16 * (double)iters * blocks * 256 / (best * 1e-3);
+  return WB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// wb_step_noalloc: one step of a small single box with every intermediate in
+// a file-scope device array, for callers that cannot allocate device memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+const size_t kNoallocBytes = 24u << 20;  // 24 MiB
+static __device__ __align__(256) double wb_noalloc_scratch[kNoallocBytes / sizeof(double)];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256];  // device address of the array, per device ordinal
+std::string g_noalloc_err;
+
+int noalloc_fail(int code, const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  g_noalloc_err = msg;
+  return code;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wb_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
+
+int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const double* by,
+                    const double* bz, double* U_out, double* bx_out, double* by_out,
+                    double* bz_out, double* dt_out, void* stream) {
+  std::string why;
+  if (!valid_desc(d, &why)) return noalloc_fail(WB_ERR_INVALID, "invalid descriptor: " + why);
+  if (d->patches[0] != 1 || d->patches[1] != 1 || d->patches[2] != 1)
+    return noalloc_fail(WB_ERR_INVALID, "wb_step_noalloc takes a single box (patches = 1,1,1)");
+  if (!U || !bx || !by || !bz || !U_out || !bx_out || !by_out || !bz_out)
+    return noalloc_fail(WB_ERR_INVALID, "null state pointer");
+  wb_desc one = *d;
+  one.batch_patches = 0;
+  Layout L = layout(&one);
+  if (L.total > kNoallocBytes) {
+    char buf[200];
+    std::snprintf(buf, sizeof(buf),
+                  "box %dx%dx%d needs %zu bytes of scratch; the static limit is %zu bytes "
+                  "(24 MiB, cubes up to 22^3 zones)",
+                  d->n[0], d->n[1], d->n[2], L.total, kNoallocBytes);
+    return noalloc_fail(WB_ERR_INVALID, buf);
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
+    return noalloc_fail(WB_ERR_CUDA, "no current CUDA device");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, wb_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        g_noalloc_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return WB_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  // a grid object carved from the static array (no device allocation)
+  wb_grid g;
+  g.d = one;
+  g.geo = make_geo(&one);
+  for (int a = 0; a < 3; ++a) {
+    g.map.N[a] = one.n[a];
+    g.map.np[a] = 1;
+    g.map.bc[a] = one.bc[a];
+  }
+  g.map.npatch = 1;
+  g.npatch = 1;
+  g.S = 1;
+  g.phys = make_phys(&one);
+  g.stream = reinterpret_cast<cudaStream_t>(stream);
+  g.mem = reinterpret_cast<char*>(base);
+  g.bytes = kNoallocBytes;
+  const size_t V = (size_t)g.geo.V;
+  double* st = reinterpret_cast<double*>(g.mem);
+  for (int c = 0; c < 8; ++c) g.q[c] = st + (size_t)c * V;
+  for (int c = 0; c < 3; ++c) g.b[c] = st + (size_t)(8 + c) * V;
+  double* w = reinterpret_cast<double*>(g.mem + L.state);
+  size_t k = 0;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c) g.Fp[dd][c] = (c == F_BX + dd) ? nullptr : w + V * k++;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c) g.Fc[dd][c] = (c == F_BX + dd) ? nullptr : w + V * k++;
+  for (int dd = 0; dd < 3; ++dd) g.Eref[dd] = w + V * k++;
+  for (int dd = 0; dd < 3; ++dd) g.Eedge[dd] = w + V * k++;
+  for (int dd = 0; dd < 3; ++dd) g.bh[dd] = w + V * k++;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c) g.qh[dd][c] = w + V * k++;
+  for (int dd = 0; dd < 3; ++dd) g.Erefh[dd] = w + V * k++;
+  for (int dd = 0; dd < 3; ++dd) g.Eedgeh[dd] = w + V * k++;
+  g.staging = reinterpret_cast<double*>(g.mem + L.state + L.work);
+  g.scal = reinterpret_cast<WbScalars*>(g.mem + L.state + L.work + L.staging);
+  g.red = reinterpret_cast<unsigned long long*>(g.scal + 1);
+  g.loaded = true;
+  g.prof = false;
+  g.ev_used = 0;
+  cudaStream_t s = g.stream;
+  // the array keeps the previous call's contents: the scalars (time, dt,
+  // signal-rate accumulator, counters) must start at zero
+  cudaError_t e = cudaMemsetAsync(g.scal, 0, L.scalars, s);
+  if (e != cudaSuccess) return noalloc_fail(WB_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e));
+  const double* faces[3] = {bx, by, bz};
+  const long long nc = (long long)one.n[0] * one.n[1] * one.n[2];
+  for (int comp = 0; comp < 8; ++comp) {
+    const double* src = comp < 5 ? U + comp * nc : faces[comp - 5];
+    double* dst = comp < 5 ? g.q[comp] : g.b[comp - 5];
+    wb_launch_scatter(src, dst, comp, g.geo, g.map, s);
+  }
+  wb_launch_halo(g.q, g.b, g.geo, g.map, s);
+  wb_launch_ccb(g.q, g.b, g.geo, 1, s);
+  wb_launch_halo(g.q, g.b, g.geo, g.map, s);
+  wb_launch_dt_init(g.q, g.geo, 1, g.phys, g.scal, s);
+  wb_launch_dt_step(g.scal, one.cfl, 0.0, s);
+  enqueue_pass(&g, 0, 1);
+  wb_launch_halo(g.q, g.b, g.geo, g.map, s);
+  double* outs[3] = {bx_out, by_out, bz_out};
+  for (int comp = 0; comp < 8; ++comp) {
+    const double* src = comp < 5 ? g.q[comp] : g.b[comp - 5];
+    double* dst = comp < 5 ? U_out + comp * nc : outs[comp - 5];
+    wb_launch_gather(src, dst, comp, g.geo, g.map, s);
+  }
+  if (dt_out) {
+    e = cudaMemcpyAsync(dt_out, &g.scal->dt, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return noalloc_fail(WB_ERR_CUDA, std::string("dt copy: ") + cudaGetErrorString(e));
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(WB_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return WB_OK;
 }
 
