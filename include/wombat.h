@@ -176,6 +176,13 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
                     double* bz_out, double* dt_out, void* stream);
 const char* wb_noalloc_last_error(void);
 
+/* Self-test of the library's FP64 reciprocal and reciprocal-square-root
+ * helpers (PTX approximations refined by a third-order correction) against
+ * the CUDA library division and rsqrt on n inputs spread over [1e-40, 1e40]:
+ * worst[0] = max |rcp(x) x - 1|, worst[1] = max |rsqrt_ours / rsqrt_cuda - 1|.
+ * Uses the grid's reduction words; synchronises the grid's stream. */
+int wb_selftest_math(wb_grid* g, int n, double worst[2]);
+
 /* FP64 pipe probe: runs a dependent-free DFMA loop on every SM of the
  * current device and returns the achieved FP64 FLOP/s (FMA = 2 flops). */
 int wb_measure_fp64_peak(void* stream, double* flops);

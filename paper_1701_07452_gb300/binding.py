@@ -25,6 +25,7 @@ EXPORTED = (
     "wb_load_primitive", "wb_compute_dt", "wb_advance", "wb_read_state", "wb_conserved_totals",
     "wb_divb_max", "wb_counters", "wb_last_error", "wb_debug_stage", "wb_measure_fp64_peak",
     "wb_profile_sweeps", "wb_profile_read", "wb_step_noalloc", "wb_noalloc_last_error",
+    "wb_selftest_math",
 )
 
 
@@ -100,6 +101,7 @@ def lib(build: bool = True):
             L.wb_profile_sweeps.argtypes = [vp, ctypes.c_int]
             L.wb_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
             L.wb_step_noalloc.argtypes = [ctypes.POINTER(WbDesc)] + [vp] * 10
+            L.wb_selftest_math.argtypes = [vp, ctypes.c_int, dp]
             L.wb_noalloc_last_error.argtypes = []
             L.wb_noalloc_last_error.restype = ctypes.c_char_p
             _lib = L
@@ -260,6 +262,11 @@ class Grid:
         n = ctypes.c_longlong(0)
         self._check(lib().wb_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def selftest_math(self, n: int = 1 << 20):
+        out = np.zeros(2)
+        self._check(lib().wb_selftest_math(self._h, int(n), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return float(out[0]), float(out[1])
 
     def stage(self, which: int):
         nx, ny, nz = self.n

@@ -620,6 +620,19 @@ int wb_debug_stage(wb_grid* g, int which, double* out, long long cap, long long*
   return WB_OK;
 }
 
+int wb_selftest_math(wb_grid* g, int n, double worst[2]) {
+  if (!g || !worst || n < 1) return fail(g, WB_ERR_INVALID, "bad argument");
+  cudaError_t e = cudaMemsetAsync(g->red, 0, 2 * sizeof(unsigned long long), g->stream);
+  if (e != cudaSuccess) return check_cuda(g, e, "selftest");
+  wb_launch_math_selftest(n, g->red, g->stream);
+  unsigned long long bits[2] = {0, 0};
+  e = cudaMemcpyAsync(bits, g->red, sizeof(bits), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return check_cuda(g, e, "selftest");
+  std::memcpy(worst, bits, sizeof(bits));
+  return WB_OK;
+}
+
 int wb_measure_fp64_peak(void* stream, double* flops) {
   if (!flops) return WB_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

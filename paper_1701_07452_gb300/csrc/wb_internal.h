@@ -14,6 +14,8 @@ struct SweepArgs {
   const double* dt;
   WbPhys phys;
   WbScalars* scal;
+  int nseg;                // segments per pencil (0: chosen at launch)
+  int seg_len;             // faces per segment (set at launch)
 };
 
 // Pointers of one pipeline pass over a batch of patches.
@@ -75,3 +77,4 @@ void wb_launch_divb(double* const b[3], const WbGeo& geo, long long npatch,
 void wb_launch_copy_box(const double* src, long long slot, const WbGeo& geo, const WbBox& box,
                         double* dst, cudaStream_t s);
 void wb_launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
+void wb_launch_math_selftest(int n, unsigned long long* worst, cudaStream_t s);
