@@ -176,6 +176,45 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
                     double* bz_out, double* dt_out, void* stream);
 const char* wb_noalloc_last_error(void);
 
+/* ---- batching: many independent boxes in one persistent kernel ----
+ * A batch holds nbox independent single-patch boxes (sizes may differ; every
+ * box must share gamma, cfl, eps, sweby and floors).  One wb_batch_advance
+ * launches one persistent kernel that advances every box with steps left by
+ * up to nsteps CTU+CT steps, each box with its own CFL dt: thread blocks take
+ * chunks of work items (pencil segments, zones, faces, edges) of all boxes
+ * from a device work counter, and a bounded grid-wide barrier separates the
+ * stages of a step.  The state of all boxes stays resident; the step's
+ * intermediates are shared by workspace groups of boxes whose combined
+ * workspace fits work_budget bytes (0 = 64 GiB).  Boxes are periodic or
+ * outflow on their own; patches must be (1,1,1).
+ * wb_batch_bytes / wb_batch_create: caller-owned device memory as for grids.
+ * wb_batch_load: as wb_load_state / wb_load_primitive for one box.
+ * wb_batch_set_steps: steps left for one box (box = -1: all boxes); a box with
+ * no steps left is skipped by wb_batch_advance.
+ * wb_batch_advance: one persistent launch of nsteps steps; use_graph != 0
+ * replays it from a captured CUDA graph (captured on first use per nsteps).
+ * Synchronises the stream; returns WB_ERR_TIMEOUT if a barrier wait ran out.
+ * wb_batch_autotune: times trial_steps real steps per candidate segment
+ * length and blocks per SM, keeps the fastest (cached per box-size mix).
+ * wb_batch_config: set them explicitly (0 = keep); barrier_budget_cycles is
+ * the per-barrier wait limit in SM clock cycles (default 20 s worth). */
+typedef struct wb_batch wb_batch;
+int wb_batch_bytes(int nbox, const wb_desc* descs, size_t work_budget, size_t* bytes);
+int wb_batch_create(int nbox, const wb_desc* descs, size_t work_budget, void* dev_mem,
+                    size_t bytes, void* stream, wb_batch** out);
+int wb_batch_destroy(wb_batch* b);
+int wb_batch_load(wb_batch* b, int box, const double* U, const double* bx, const double* by,
+                  const double* bz, int on_device, int primitive);
+int wb_batch_set_steps(wb_batch* b, int box, int nsteps);
+int wb_batch_advance(wb_batch* b, int nsteps, int use_graph);
+int wb_batch_read(wb_batch* b, int box, double* U, double* bx, double* by, double* bz, double* B,
+                  int on_device);
+int wb_batch_counters(wb_batch* b, int box, wb_counters_t* c);
+int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms);
+int wb_batch_config(wb_batch* b, int seg_len, int blocks_per_sm, long long barrier_budget_cycles);
+int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* groups);
+const char* wb_batch_last_error(const wb_batch* b);
+
 /* Self-test of the library's FP64 reciprocal and reciprocal-square-root
  * helpers (PTX approximations refined by a third-order correction) against
  * the CUDA library division and rsqrt on n inputs spread over [1e-40, 1e40]:

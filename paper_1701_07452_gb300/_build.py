@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwombat_gb300.so")
-SOURCES = ["wb_sweep.cu", "wb_stages.cu", "wb_capi.cu"]
-HEADERS = ["wb_device.cuh", "wb_internal.h"]
+SOURCES = ["wb_sweep.cu", "wb_stages.cu", "wb_capi.cu", "wb_batch.cu"]
+HEADERS = ["wb_device.cuh", "wb_internal.h", "wb_units.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

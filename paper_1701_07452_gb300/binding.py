@@ -25,7 +25,9 @@ EXPORTED = (
     "wb_load_primitive", "wb_compute_dt", "wb_advance", "wb_read_state", "wb_conserved_totals",
     "wb_divb_max", "wb_counters", "wb_last_error", "wb_debug_stage", "wb_measure_fp64_peak",
     "wb_profile_sweeps", "wb_profile_read", "wb_step_noalloc", "wb_noalloc_last_error",
-    "wb_selftest_math",
+    "wb_selftest_math", "wb_batch_bytes", "wb_batch_create", "wb_batch_destroy", "wb_batch_load",
+    "wb_batch_set_steps", "wb_batch_advance", "wb_batch_read", "wb_batch_counters",
+    "wb_batch_autotune", "wb_batch_config", "wb_batch_get_config", "wb_batch_last_error",
 )
 
 
@@ -102,6 +104,22 @@ def lib(build: bool = True):
             L.wb_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
             L.wb_step_noalloc.argtypes = [ctypes.POINTER(WbDesc)] + [vp] * 10
             L.wb_selftest_math.argtypes = [vp, ctypes.c_int, dp]
+            L.wb_batch_bytes.argtypes = [ctypes.c_int, ctypes.POINTER(WbDesc), ctypes.c_size_t,
+                                         ctypes.POINTER(ctypes.c_size_t)]
+            L.wb_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(WbDesc), ctypes.c_size_t, vp,
+                                          ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+            L.wb_batch_destroy.argtypes = [vp]
+            L.wb_batch_load.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int]
+            L.wb_batch_set_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            L.wb_batch_advance.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            L.wb_batch_read.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_int]
+            L.wb_batch_counters.argtypes = [vp, ctypes.c_int, ctypes.POINTER(WbCounters)]
+            L.wb_batch_autotune.argtypes = [vp, ctypes.c_int, dp]
+            L.wb_batch_config.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
+            L.wb_batch_get_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]
+            L.wb_batch_last_error.argtypes = [vp]
+            L.wb_batch_last_error.restype = ctypes.c_char_p
             L.wb_noalloc_last_error.argtypes = []
             L.wb_noalloc_last_error.restype = ctypes.c_char_p
             _lib = L
@@ -276,6 +294,100 @@ class Grid:
         self._check(lib().wb_debug_stage(self._h, int(which), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          cap, ctypes.byref(w)))
         return out[: w.value]
+
+
+class Batch:
+    """Many independent single-patch boxes advanced by one persistent kernel
+    (wb_batch_* of the C ABI).  boxes: list of dicts with keys n, length and
+    optional bc; physics keywords are shared by every box."""
+
+    def __init__(self, boxes, work_budget=0, stream=None, **kw):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("wombat: a CUDA device is required (no CPU fallback)")
+        self.nbox = len(boxes)
+        self.n = [tuple(int(x) for x in b["n"]) for b in boxes]
+        arr = (WbDesc * self.nbox)()
+        for i, b in enumerate(boxes):
+            d = make_desc(b["n"], (1, 1, 1), b.get("length"), bc=b.get("bc", (0, 0, 0)), **kw)
+            arr[i] = d
+        self._descs = arr
+        nbytes = ctypes.c_size_t(0)
+        rc = lib().wb_batch_bytes(self.nbox, arr, ctypes.c_size_t(int(work_budget)), ctypes.byref(nbytes))
+        if rc:
+            raise WombatError(rc, "invalid batch description")
+        self.nbytes = int(nbytes.value)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        rc = lib().wb_batch_create(self.nbox, arr, ctypes.c_size_t(int(work_budget)),
+                                   ctypes.c_void_p(self.workspace.data_ptr()), ctypes.c_size_t(self.nbytes),
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc:
+            raise WombatError(rc, "batch create failed")
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().wb_batch_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            msg = lib().wb_batch_last_error(self._h)
+            raise WombatError(rc, msg.decode() if msg else "")
+
+    def load(self, box, U, bx, by, bz, primitive=False, on_device=False):
+        arrs = [U, bx, by, bz]
+        if not on_device:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        self._check(lib().wb_batch_load(self._h, int(box), *[ctypes.c_void_p(_ptr(a)) for a in arrs],
+                                        int(bool(on_device)), int(bool(primitive))))
+
+    def load_state(self, box, st):
+        self.load(box, st["W"], st["bx"], st["by"], st["bz"], primitive=True)
+
+    def set_steps(self, box, nsteps):
+        self._check(lib().wb_batch_set_steps(self._h, int(box), int(nsteps)))
+
+    def advance(self, nsteps, use_graph=True):
+        self._check(lib().wb_batch_advance(self._h, int(nsteps), int(bool(use_graph))))
+
+    def read(self, box):
+        nx, ny, nz = self.n[box]
+        out = (np.empty((5, nz, ny, nx)), np.empty((nz, ny, nx + 1)), np.empty((nz, ny + 1, nx)),
+               np.empty((nz + 1, ny, nx)), np.empty((3, nz, ny, nx)))
+        self._check(lib().wb_batch_read(self._h, int(box), *[ctypes.c_void_p(_ptr(a)) for a in out], 0))
+        return out
+
+    def counters(self, box):
+        c = WbCounters()
+        self._check(lib().wb_batch_counters(self._h, int(box), ctypes.byref(c)))
+        return {"steps": c.steps, "floor_hits": c.floor_hits, "unphysical": c.unphysical,
+                "t": c.t, "last_dt": c.last_dt}
+
+    def autotune(self, trial_steps=1):
+        ms = ctypes.c_double(0.0)
+        self._check(lib().wb_batch_autotune(self._h, int(trial_steps), ctypes.byref(ms)))
+        return ms.value
+
+    def config(self, seg_len=0, blocks_per_sm=0, barrier_budget_cycles=0):
+        self._check(lib().wb_batch_config(self._h, int(seg_len), int(blocks_per_sm),
+                                          ctypes.c_longlong(int(barrier_budget_cycles))))
+
+    def get_config(self):
+        a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        self._check(lib().wb_batch_get_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"seg_len": a.value, "blocks_per_sm": b.value, "groups": c.value}
 
 
 def step_noalloc(desc: WbDesc, U, bx, by, bz, U_out, bx_out, by_out, bz_out, dt_out=None,

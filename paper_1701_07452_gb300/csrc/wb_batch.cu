@@ -1,0 +1,947 @@
+// Batched advance of many independent boxes of uneven sizes in one persistent
+// kernel (the batching pattern built around the paper's Patch update engine,
+// Sec. "Update Engine": a work list of patch updates drained by all threads,
+// with dynamic -- GUIDED-like -- scheduling, Sec. "Thread Scheduling at Scale").
+//
+// One launch advances every active box by up to nsteps CTU+CT steps (Sec. "MHD
+// in Three Dimensions", Steps 1-11), each box with its own CFL dt.  Inside the
+// launch the stages of a step run one after another over all boxes of a
+// workspace group; within a stage, thread blocks take chunks of work items
+// (pencil segments, zones, faces, edges of some box) from an atomic counter,
+// and a grid-wide barrier separates stages.  The barrier waits are bounded:
+// a block that waits longer than the budget sets an error word and every
+// block returns, so a stalled launch ends with WB_ERR_TIMEOUT instead of a
+// hang.  The stage bodies are the same device functions the per-stage kernels
+// of a grid use (wb_units.cuh).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/wombat.h"
+#include "wb_device.cuh"
+#include "wb_internal.h"
+
+namespace {
+
+enum {
+  BS_DT = 0, BS_PRED, BS_EREF, BS_EDGE_P, BS_CT_H, BS_TRANS, BS_CORR, BS_EREF_H, BS_EDGE_C,
+  BS_CT_F, BS_FINAL, BS_HALO, BS_COUNT
+};
+
+constexpr int kB = wbu::kBlock;        // threads per block
+constexpr int kItemsPerThread = 8;     // items per thread in a chunk of a cheap stage
+
+__host__ __device__ inline WbBox bxx(int l0, int h0, int l1, int h1, int l2, int h2) {
+  WbBox b;
+  b.lo[0] = l0; b.hi[0] = h0; b.lo[1] = l1; b.hi[1] = h1; b.lo[2] = l2; b.hi[2] = h2;
+  return b;
+}
+
+__host__ __device__ inline int stage_nsub(int s) {
+  return (s == BS_PRED || s == BS_CORR || s == BS_EDGE_P || s == BS_EDGE_C || s == BS_CT_H ||
+          s == BS_CT_F || s == BS_TRANS) ? 3 : 1;
+}
+
+__host__ __device__ inline bool stage_is_sweep(int s) { return s == BS_PRED || s == BS_CORR; }
+
+// Index boxes of every stage (the same regions as the grid path, wb_capi.cu).
+__host__ __device__ inline WbBox stage_box(int s, int d, const int* n) {
+  const int N0 = n[0], N1 = n[1], N2 = n[2];
+  switch (s) {
+    case BS_PRED:
+      if (d == 0) return bxx(-3, N0 + 3, -4, N1 + 3, -4, N2 + 3);
+      if (d == 1) return bxx(-4, N0 + 3, -3, N1 + 3, -4, N2 + 3);
+      return bxx(-4, N0 + 3, -4, N1 + 3, -3, N2 + 3);
+    case BS_EREF: return bxx(-4, N0 + 3, -4, N1 + 3, -4, N2 + 3);
+    case BS_EDGE_P:
+      if (d == 0) return bxx(-1, N0, -3, N1 + 3, -3, N2 + 3);
+      if (d == 1) return bxx(-3, N0 + 3, -1, N1, -3, N2 + 3);
+      return bxx(-3, N0 + 3, -3, N1 + 3, -1, N2);
+    case BS_CT_H:
+      if (d == 0) return bxx(-3, N0 + 3, -1, N1, -1, N2);
+      if (d == 1) return bxx(-1, N0, -3, N1 + 3, -1, N2);
+      return bxx(-1, N0, -1, N1, -3, N2 + 3);
+    case BS_TRANS:
+      if (d == 0) return bxx(-3, N0 + 2, -1, N1, -1, N2);
+      if (d == 1) return bxx(-1, N0, -3, N1 + 2, -1, N2);
+      return bxx(-1, N0, -1, N1, -3, N2 + 2);
+    case BS_CORR:
+      if (d == 0) return bxx(-1, N0 + 1, -1, N1, -1, N2);
+      if (d == 1) return bxx(-1, N0, -1, N1 + 1, -1, N2);
+      return bxx(-1, N0, -1, N1, -1, N2 + 1);
+    case BS_EREF_H: return bxx(-1, N0, -1, N1, -1, N2);
+    case BS_EDGE_C:
+      if (d == 0) return bxx(0, N0 - 1, 0, N1, 0, N2);
+      if (d == 1) return bxx(0, N0, 0, N1 - 1, 0, N2);
+      return bxx(0, N0, 0, N1, 0, N2 - 1);
+    case BS_CT_F:
+      if (d == 0) return bxx(0, N0, 0, N1 - 1, 0, N2 - 1);
+      if (d == 1) return bxx(0, N0 - 1, 0, N1, 0, N2 - 1);
+      return bxx(0, N0 - 1, 0, N1 - 1, 0, N2);
+    case BS_FINAL: return bxx(0, N0 - 1, 0, N1 - 1, 0, N2 - 1);
+    case BS_HALO: return bxx(-WB_NG, N0 + WB_NG - 1, -WB_NG, N1 + WB_NG - 1, -WB_NG, N2 + WB_NG - 1);
+    default: return bxx(0, 0, 0, 0, 0, 0);
+  }
+}
+
+__host__ __device__ inline long long box_cnt(const WbBox& b) {
+  return (long long)(b.hi[0] - b.lo[0] + 1) * (b.hi[1] - b.lo[1] + 1) * (b.hi[2] - b.lo[2] + 1);
+}
+
+// sweep items: pencils x segments
+__host__ __device__ inline void sweep_shape(const WbBox& b, int d, int seg_len, long long* npen,
+                                            int* nseg) {
+  const int U = (d == 0) ? 1 : 0, W = (d == 2) ? 1 : 2;
+  *npen = (long long)(b.hi[U] - b.lo[U] + 1) * (b.hi[W] - b.lo[W] + 1);
+  const int len = b.hi[d] - b.lo[d] + 1;
+  *nseg = (len + seg_len - 1) / seg_len;
+}
+
+__host__ __device__ inline long long stage_items(int s, int d, const int* n, int seg_len) {
+  if (s == BS_DT) return 1;
+  WbBox b = stage_box(s, d, n);
+  if (stage_is_sweep(s)) {
+    long long np;
+    int ns;
+    sweep_shape(b, d, seg_len, &np, &ns);
+    return np * ns;
+  }
+  return box_cnt(b);
+}
+
+__host__ __device__ inline int items_per_chunk(int s) {
+  return (stage_is_sweep(s) || s == BS_DT) ? kB : kB * kItemsPerThread;
+}
+
+struct BoxInfo {
+  WbView v;
+  int bc[3];
+};
+
+struct BatchParams {
+  const BoxInfo* boxes;
+  WbScalars* scal;            // per box
+  int* steps_left;            // per box
+  const int* gbox;            // box ids of each group, concatenated
+  const int* gfirst;          // [ngroups + 1]
+  const long long* pre;       // chunk prefix sums per (group, stage): entries (box, sub)
+  const long long* pre_off;   // [ngroups * BS_COUNT] start of each prefix array in pre
+  int ngroups;
+  unsigned* sync;             // [0] arrivals, [1] generation, [2] error, [3..4] chunk counters
+  WbPhys phys;
+  double cfl;
+  int seg_len;
+  long long budget;           // barrier wait budget in SM clock cycles
+};
+
+// Grid-wide barrier with a bounded wait.  Returns false when the error word is
+// set (timeout here or elsewhere); every block then leaves the kernel.
+__device__ bool grid_barrier(const BatchParams& B, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = B.sync + 1;
+    volatile unsigned* err = B.sync + 2;
+    __threadfence();
+    const unsigned g = *gen;
+    const unsigned arrived = atomicAdd(B.sync, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(B.sync, 0u);
+      __threadfence();
+      atomicAdd((unsigned*)gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (*err) break;
+        if (clock64() - t0 > B.budget) {
+          atomicExch((unsigned*)err, 1u);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = (*err == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void warp_max_atomic(double w, unsigned long long* dst) {
+  unsigned long long bits = (w >= 0.0) ? (unsigned long long)__double_as_longlong(w)
+                                       : (w != w ? 0x7ff8000000000000ULL : 0ULL);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = other > bits ? other : bits;
+  }
+  if ((threadIdx.x & 31) == 0 && bits) atomicMax(dst, bits);
+}
+
+template <int D>
+__device__ __forceinline__ int sweep_item(const BoxInfo& bi, bool corr, const WbBox& b, long long item,
+                                          int seg_len, double dt, const WbPhys& P,
+                                          const wbu::Rec rec[2]) {
+  constexpr int U = (D == 0) ? 1 : 0, W = (D == 2) ? 1 : 2;
+  long long npen;
+  int nseg;
+  sweep_shape(b, D, seg_len, &npen, &nseg);
+  const int seg = (int)(item / npen);
+  const long long pen = item - seg * npen;
+  const int nu = b.hi[U] - b.lo[U] + 1;
+  const int fa = b.lo[D] + seg * seg_len;
+  int fb = fa + seg_len - 1;
+  if (fb > b.hi[D]) fb = b.hi[D];
+  const WbView& v = bi.v;
+  const double* const* q = corr ? v.qh[D] : v.q;
+  const double* bn = corr ? v.bh[D] : v.b[D];
+  double* const* F = corr ? v.Fc[D] : v.Fp[D];
+  return wbu::sweep_segment<D, false>(v.geo, q, bn, F, 0, 0, b.lo[U] + (int)(pen % nu), b.lo[W] + (int)(pen / nu),
+                               fa, fb, dt, P, rec);
+}
+
+__device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, int box,
+                                          const BoxInfo& bi, long long item, double dt,
+                                          const wbu::Rec rec[2], double* wmax, int* hits, int* bad) {
+  const WbView& v = bi.v;
+  const int* n = v.geo.n;
+  if (stage_is_sweep(s)) {
+    const WbBox b = stage_box(s, d, n);
+    const bool corr = s == BS_CORR;
+    if (d == 0) *bad += sweep_item<0>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    else if (d == 1) *bad += sweep_item<1>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    else *bad += sweep_item<2>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    return;
+  }
+  if (s == BS_HALO) {
+    wbu::halo_self(v, 0, bi.bc, item);
+    return;
+  }
+  const WbBox b = stage_box(s, d, n);
+  const int nx = b.hi[0] - b.lo[0] + 1, ny = b.hi[1] - b.lo[1] + 1;
+  const int i = b.lo[0] + (int)(item % nx);
+  const long long r = item / nx;
+  const int j = b.lo[1] + (int)(r % ny);
+  const int k = b.lo[2] + (int)(r / ny);
+  switch (s) {
+    case BS_EREF: wbu::eref(v, 0, 0, i, j, k); break;
+    case BS_EDGE_P:
+    case BS_EDGE_C: {
+      const bool corr = s == BS_EDGE_C;
+      if (d == 0) wbu::edge<0>(v, 0, corr, i, j, k);
+      else if (d == 1) wbu::edge<1>(v, 0, corr, i, j, k);
+      else wbu::edge<2>(v, 0, corr, i, j, k);
+      break;
+    }
+    case BS_CT_H:
+    case BS_CT_F: {
+      const bool fin = s == BS_CT_F;
+      if (d == 0) wbu::ct<0>(v, 0, 0, fin, dt, i, j, k);
+      else if (d == 1) wbu::ct<1>(v, 0, 0, fin, dt, i, j, k);
+      else wbu::ct<2>(v, 0, 0, fin, dt, i, j, k);
+      break;
+    }
+    case BS_TRANS:
+      if (d == 0) wbu::transverse<0>(v, 0, 0, dt, i, j, k);
+      else if (d == 1) wbu::transverse<1>(v, 0, 0, dt, i, j, k);
+      else wbu::transverse<2>(v, 0, 0, dt, i, j, k);
+      break;
+    case BS_EREF_H: wbu::eref_half(v, 0, 0, dt, i, j, k); break;
+    case BS_FINAL: {
+      const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, hits, bad);
+      *wmax = fmax(*wmax, w);
+      if (w != w) *wmax = w;
+      break;
+    }
+    default: break;
+  }
+  (void)box;
+}
+
+// dt of one box for the coming step (reading R3 of the design notes)
+__device__ void box_dt(const BatchParams& B, int box) {
+  WbScalars* s = B.scal + box;
+  if (B.steps_left[box] <= 0) { s->dt = 0.0; return; }
+  const double w = __longlong_as_double((long long)s->wmax_next);
+  const double dt = B.cfl / w;
+  if (!((w > 0.0) && isfinite(w) && isfinite(dt) && dt > 0.0)) {
+    s->dt = 0.0;
+    s->unphysical += 1;
+    B.steps_left[box] = 0;
+    return;
+  }
+  s->dt = dt;
+  s->t += dt;
+  s->steps += 1;
+  s->wmax_next = 0ULL;
+  B.steps_left[box] -= 1;
+}
+
+__global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nsteps) {
+  __shared__ double srec[2][wbu::R_WORDS][wbu::kBlock];
+  __shared__ long long s_chunk;
+  const wbu::Rec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
+  const unsigned nblocks = gridDim.x;
+  unsigned stage_seq = 0;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int grp = 0; grp < B.ngroups; ++grp) {
+      const int gb0 = B.gfirst[grp];
+      const int nbox = B.gfirst[grp + 1] - gb0;
+      for (int s = 0; s < BS_COUNT; ++s, ++stage_seq) {
+        unsigned* ctr = B.sync + 3 + (stage_seq & 1u);
+        // the other counter is idle during this stage: block 0 clears it
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(B.sync + 3 + ((stage_seq + 1) & 1u), 0u);
+        const long long* pre = B.pre + B.pre_off[grp * BS_COUNT + s];
+        const int nsub = stage_nsub(s);
+        const int nent = nbox * nsub;
+        const long long nchunks = pre[nent];
+        const int ipc = items_per_chunk(s);
+        for (;;) {
+          if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(ctr, 1u);
+          __syncthreads();
+          const long long c = s_chunk;
+          __syncthreads();
+          if (c >= nchunks) break;
+          // (box, sub) entry holding chunk c
+          int lo = 0, hi = nent - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= c) lo = mid; else hi = mid - 1;
+          }
+          const int box = B.gbox[gb0 + lo / nsub];
+          const int sub = lo % nsub;
+          if (s == BS_DT) {
+            if (threadIdx.x == 0) box_dt(B, box);
+            continue;
+          }
+          const double dt = *(volatile const double*)&B.scal[box].dt;
+          if (!(dt > 0.0)) continue;
+          const BoxInfo& bi = B.boxes[box];
+          const long long nitems = stage_items(s, sub, bi.v.geo.n, B.seg_len);
+          const long long i0 = (c - pre[lo]) * ipc;
+          long long i1 = i0 + ipc;
+          if (i1 > nitems) i1 = nitems;
+          double wmax = 0.0;
+          int hits = 0, bad = 0;
+          for (long long it = i0 + threadIdx.x; it < i1; it += kB)
+            unit_item(B, s, sub, box, bi, it, dt, rec, &wmax, &hits, &bad);
+          if (s == BS_FINAL) warp_max_atomic(wmax, &B.scal[box].wmax_next);
+          if (hits) atomicAdd((unsigned long long*)&B.scal[box].floor_hits, (unsigned long long)hits);
+          if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
+        }
+        if (!grid_barrier(B, nblocks)) return;
+      }
+    }
+  }
+}
+
+// initial signal rate of one box
+__global__ void k_box_rate(BoxInfo* boxes, WbScalars* scal, int box, WbPhys P) {
+  const WbView& v = boxes[box].v;
+  const WbGeo& g = v.geo;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  double w = 0.0;
+  if (t < nint) {
+    const int i = (int)(t % g.n[0]);
+    const int j = (int)((t / g.n[0]) % g.n[1]);
+    const int k = (int)(t / ((long long)g.n[0] * g.n[1]));
+    const long long o = wb_at(g, i, j, k);
+    w = wbu::signal_rate(v.q[0][o], v.q[1][o], v.q[2][o], v.q[3][o], v.q[4][o], v.q[5][o], v.q[6][o],
+                         v.q[7][o], P, g);
+  }
+  warp_max_atomic(w, &scal[box].wmax_next);
+}
+
+const int kWorkB = 3 * 7 + 3 + 3 + 3 + 3 * 8;  // 54: corrector fluxes, half-step EMFs alias
+
+struct TuneKey {
+  std::vector<int> sizes;
+  bool operator<(const TuneKey& o) const { return sizes < o.sizes; }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (seg_len, blocks per SM)
+
+}  // namespace
+
+struct wb_batch {
+  int nbox;
+  std::vector<wb_desc> d;
+  std::vector<WbGeo> geo;
+  WbPhys phys;
+  double cfl;
+  cudaStream_t stream;
+  char* mem;
+  size_t bytes;
+  // host copies
+  std::vector<BoxInfo> info;
+  std::vector<int> gbox, gfirst;
+  // device regions
+  BoxInfo* d_info;
+  WbScalars* d_scal;
+  int* d_steps;
+  int* d_gbox;
+  int* d_gfirst;
+  long long* d_pre;
+  long long* d_pre_off;
+  unsigned* d_sync;
+  double* staging;
+  size_t staging_elems;
+  size_t pre_cap;
+  // launch configuration
+  int seg_len;
+  int blocks_per_sm;
+  int max_blocks_per_sm;
+  int sms;
+  long long budget;
+  // graph
+  cudaGraphExec_t graph;
+  int graph_steps;
+  bool graph_ok;
+  std::string err;
+};
+
+namespace {
+
+int bfail(wb_batch* b, int code, const std::string& m) {
+  if (b) b->err = m;
+  return code;
+}
+
+int bcuda(wb_batch* b, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return WB_OK;
+  return bfail(b, WB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+WbGeo geo_of(const wb_desc& d) {
+  WbGeo g;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = d.n[a];
+    g.pd[a] = g.n[a] + 2 * WB_NG;
+    g.dx[a] = d.length[a] / d.n[a];
+    g.idx[a] = 1.0 / g.dx[a];
+  }
+  g.sy = g.pd[0];
+  g.sz = (long long)g.pd[0] * g.pd[1];
+  g.V = g.sz * g.pd[2];
+  return g;
+}
+
+bool same_physics(const wb_desc& a, const wb_desc& b) {
+  if (a.gamma != b.gamma || a.cfl != b.cfl || a.sweby_beta != b.sweby_beta ||
+      a.rho_floor != b.rho_floor || a.p_floor != b.p_floor)
+    return false;
+  for (int k = 0; k < 7; ++k)
+    if (a.eps[k] != b.eps[k]) return false;
+  return true;
+}
+
+struct BatchLayout {
+  size_t state, work, tables, staging, total;
+  std::vector<int> gbox, gfirst;
+  std::vector<size_t> state_off, work_off;  // per box, in doubles
+  size_t pre_cap;
+};
+
+// Boxes go to workspace groups in order until a group's intermediates would
+// exceed work_budget; the state of every box stays resident.
+BatchLayout plan(int nbox, const wb_desc* d, size_t work_budget) {
+  BatchLayout L;
+  L.state_off.resize(nbox);
+  L.work_off.resize(nbox);
+  size_t st = 0, maxg = 0, cur = 0, gmax = 0;
+  L.gfirst.push_back(0);
+  for (int b = 0; b < nbox; ++b) {
+    WbGeo g = geo_of(d[b]);
+    L.state_off[b] = st;
+    st += (size_t)g.V * 11;
+    size_t w = (size_t)g.V * kWorkB;
+    if (cur > 0 && (cur + w) * sizeof(double) > work_budget) {
+      L.gfirst.push_back((int)L.gbox.size());
+      cur = 0;
+    }
+    L.work_off[b] = cur;
+    cur += w;
+    if (cur > maxg) maxg = cur;
+    L.gbox.push_back(b);
+    size_t ge = (size_t)(d[b].n[0] + 1) * (d[b].n[1] + 1) * (d[b].n[2] + 1);
+    if (ge > gmax) gmax = ge;
+  }
+  L.gfirst.push_back((int)L.gbox.size());
+  const int ngroups = (int)L.gfirst.size() - 1;
+  L.state = al(st * sizeof(double));
+  L.work = al(maxg * sizeof(double));
+  L.pre_cap = (size_t)ngroups * BS_COUNT + (size_t)BS_COUNT * 3 * nbox + 16;
+  L.tables = al(sizeof(BoxInfo) * nbox) + al(sizeof(WbScalars) * nbox) + al(sizeof(int) * nbox) +
+             al(sizeof(int) * nbox) + al(sizeof(int) * (ngroups + 1)) +
+             al(sizeof(long long) * L.pre_cap) + al(sizeof(long long) * ngroups * BS_COUNT) +
+             al(sizeof(unsigned) * 8);
+  L.staging = al(sizeof(double) * gmax);
+  L.total = L.state + L.work + L.tables + L.staging;
+  return L;
+}
+
+// chunk prefix tables for the current seg_len
+void build_prefix(const wb_batch* b, std::vector<long long>& pre, std::vector<long long>& off) {
+  const int ngroups = (int)b->gfirst.size() - 1;
+  pre.clear();
+  off.assign((size_t)ngroups * BS_COUNT, 0);
+  for (int gi = 0; gi < ngroups; ++gi)
+    for (int s = 0; s < BS_COUNT; ++s) {
+      off[gi * BS_COUNT + s] = (long long)pre.size();
+      const int nsub = stage_nsub(s);
+      long long acc = 0;
+      for (int e = b->gfirst[gi]; e < b->gfirst[gi + 1]; ++e) {
+        const int box = b->gbox[e];
+        for (int sub = 0; sub < nsub; ++sub) {
+          pre.push_back(acc);
+          const long long items = stage_items(s, sub, b->geo[box].n, b->seg_len);
+          acc += (items + items_per_chunk(s) - 1) / items_per_chunk(s);
+        }
+      }
+      pre.push_back(acc);
+    }
+}
+
+int upload_tables(wb_batch* b) {
+  std::vector<long long> pre, off;
+  build_prefix(b, pre, off);
+  if (pre.size() > b->pre_cap) return bfail(b, WB_ERR_INVALID, "prefix table overflow");
+  cudaError_t e = cudaMemcpyAsync(b->d_pre, pre.data(), sizeof(long long) * pre.size(),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_pre_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return bcuda(b, e, "tables");
+}
+
+BatchParams params(const wb_batch* b) {
+  BatchParams p;
+  p.boxes = b->d_info;
+  p.scal = b->d_scal;
+  p.steps_left = b->d_steps;
+  p.gbox = b->d_gbox;
+  p.gfirst = b->d_gfirst;
+  p.pre = b->d_pre;
+  p.pre_off = b->d_pre_off;
+  p.ngroups = (int)b->gfirst.size() - 1;
+  p.sync = b->d_sync;
+  p.phys = b->phys;
+  p.cfl = b->cfl;
+  p.seg_len = b->seg_len;
+  p.budget = b->budget;
+  return p;
+}
+
+// enqueue one persistent launch of nsteps steps (no synchronisation)
+cudaError_t enqueue_advance(wb_batch* b, int nsteps) {
+  cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * 8, b->stream);
+  if (e != cudaSuccess) return e;
+  BatchParams p = params(b);
+  int nblocks = b->blocks_per_sm * b->sms;
+  void* args[] = {&p, &nsteps};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(kB);
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, (const void*)k_batch, args);
+}
+
+int read_sync_error(wb_batch* b) {
+  unsigned err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, b->d_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "batch sync");
+  if (err) return bfail(b, WB_ERR_TIMEOUT, "a grid barrier wait ran out of its budget");
+  return WB_OK;
+}
+
+void drop_graph(wb_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_steps = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wb_batch_bytes(int nbox, const wb_desc* descs, size_t work_budget, size_t* bytes) {
+  if (nbox < 1 || !descs || !bytes) return WB_ERR_INVALID;
+  for (int i = 0; i < nbox; ++i) {
+    const wb_desc& d = descs[i];
+    for (int a = 0; a < 3; ++a)
+      if (d.n[a] < 1 || d.patches[a] != 1 || !(d.length[a] > 0.0)) return WB_ERR_INVALID;
+    if (!same_physics(d, descs[0])) return WB_ERR_INVALID;
+  }
+  *bytes = plan(nbox, descs, work_budget > 0 ? work_budget : ((size_t)64 << 30)).total;
+  return WB_OK;
+}
+
+int wb_batch_create(int nbox, const wb_desc* descs, size_t work_budget, void* dev_mem, size_t bytes,
+                    void* stream, wb_batch** out) {
+  if (!out) return WB_ERR_INVALID;
+  *out = nullptr;
+  size_t need = 0;
+  int rc = wb_batch_bytes(nbox, descs, work_budget, &need);
+  if (rc) return rc;
+  if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 255u)) return WB_ERR_INVALID;
+  if (bytes < need) return WB_ERR_NOMEM;
+  const wb_desc& d0 = descs[0];
+  if (!(d0.gamma > 1.0) || d0.gamma > 2.0 || !(d0.cfl > 0.0)) return WB_ERR_INVALID;
+  wb_batch* b = new (std::nothrow) wb_batch();
+  if (!b) return WB_ERR_NOMEM;
+  BatchLayout L = plan(nbox, descs, work_budget > 0 ? work_budget : ((size_t)64 << 30));
+  b->nbox = nbox;
+  b->d.assign(descs, descs + nbox);
+  b->cfl = d0.cfl;
+  WbPhys& p = b->phys;
+  p.gamma = d0.gamma;
+  p.gm1 = d0.gamma - 1.0;
+  p.gm2 = d0.gamma - 2.0;
+  p.g_over_gm1 = d0.gamma / (d0.gamma - 1.0);
+  p.inv_gm1 = 1.0 / (d0.gamma - 1.0);
+  p.gm2_over_gm1 = (d0.gamma - 2.0) / (d0.gamma - 1.0);
+  p.cfl = d0.cfl;
+  for (int k = 0; k < 7; ++k) {
+    p.eps[k] = d0.eps[k];
+    p.two_eps[k] = 2.0 * d0.eps[k];
+    p.inv4eps[k] = d0.eps[k] > 0.0 ? 1.0 / (4.0 * d0.eps[k]) : 0.0;
+  }
+  p.sweby = d0.sweby_beta;
+  p.minmod = d0.sweby_beta == 1.0 ? 1 : 0;
+  p.rho_floor = d0.rho_floor;
+  p.p_floor = d0.p_floor;
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->mem = reinterpret_cast<char*>(dev_mem);
+  b->bytes = bytes;
+  b->gbox = L.gbox;
+  b->gfirst = L.gfirst;
+  b->pre_cap = L.pre_cap;
+  double* state = reinterpret_cast<double*>(b->mem);
+  double* work = reinterpret_cast<double*>(b->mem + L.state);
+  char* t = b->mem + L.state + L.work;
+  b->d_info = reinterpret_cast<BoxInfo*>(t); t += al(sizeof(BoxInfo) * nbox);
+  b->d_scal = reinterpret_cast<WbScalars*>(t); t += al(sizeof(WbScalars) * nbox);
+  b->d_steps = reinterpret_cast<int*>(t); t += al(sizeof(int) * nbox);
+  b->d_gbox = reinterpret_cast<int*>(t); t += al(sizeof(int) * nbox);
+  const int ngroups = (int)L.gfirst.size() - 1;
+  b->d_gfirst = reinterpret_cast<int*>(t); t += al(sizeof(int) * (ngroups + 1));
+  b->d_pre = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * L.pre_cap);
+  b->d_pre_off = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * ngroups * BS_COUNT);
+  b->d_sync = reinterpret_cast<unsigned*>(t); t += al(sizeof(unsigned) * 8);
+  b->staging = reinterpret_cast<double*>(b->mem + L.state + L.work + L.tables);
+  b->info.resize(nbox);
+  b->geo.resize(nbox);
+  for (int i = 0; i < nbox; ++i) {
+    BoxInfo& bi = b->info[i];
+    std::memset(&bi, 0, sizeof(bi));
+    WbGeo g = geo_of(descs[i]);
+    b->geo[i] = g;
+    bi.v.geo = g;
+    for (int a = 0; a < 3; ++a) bi.bc[a] = descs[i].bc[a];
+    double* s = state + L.state_off[i];
+    for (int c = 0; c < 8; ++c) bi.v.q[c] = s + (size_t)c * g.V;
+    for (int c = 0; c < 3; ++c) bi.v.b[c] = s + (size_t)(8 + c) * g.V;
+    double* w = work + L.work_off[i];
+    size_t k = 0;
+    for (int dd = 0; dd < 3; ++dd)
+      for (int c = 0; c < 8; ++c) {
+        double* f = (c == F_BX + dd) ? nullptr : w + (size_t)g.V * k++;
+        bi.v.Fp[dd][c] = f;
+        bi.v.Fc[dd][c] = f;  // corrector fluxes reuse the predictor flux arrays
+      }
+    for (int dd = 0; dd < 3; ++dd) { bi.v.Eref[dd] = w + (size_t)g.V * k; bi.v.Erefh[dd] = bi.v.Eref[dd]; ++k; }
+    for (int dd = 0; dd < 3; ++dd) { bi.v.Eedge[dd] = w + (size_t)g.V * k; bi.v.Eedgeh[dd] = bi.v.Eedge[dd]; ++k; }
+    for (int dd = 0; dd < 3; ++dd) bi.v.bh[dd] = w + (size_t)g.V * k++;
+    for (int dd = 0; dd < 3; ++dd)
+      for (int c = 0; c < 8; ++c) bi.v.qh[dd][c] = w + (size_t)g.V * k++;
+    bi.v.scal = b->d_scal + i;
+  }
+  // launch configuration
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch, kB, 0);
+  b->max_blocks_per_sm = nb > 0 ? nb : 1;
+  b->blocks_per_sm = b->max_blocks_per_sm;
+  b->seg_len = 32;
+  int clk_khz = 0;
+  cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+  b->budget = (long long)(clk_khz > 0 ? clk_khz : 2000000) * 1000LL * 20;  // 20 s of cycles
+  b->graph = nullptr;
+  b->graph_steps = 0;
+  b->graph_ok = true;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneKey key;
+    for (int i = 0; i < nbox; ++i) key.sizes.push_back(descs[i].n[0] * 1000000 + descs[i].n[1] * 1000 + descs[i].n[2]);
+    std::sort(key.sizes.begin(), key.sizes.end());
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      b->seg_len = it->second.first;
+      b->blocks_per_sm = std::min(it->second.second, b->max_blocks_per_sm);
+    }
+  }
+  cudaStream_t s = b->stream;
+  cudaError_t e = cudaMemsetAsync(b->mem, 0xff, L.state + L.work, s);  // NaN poison
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scal, 0, sizeof(WbScalars) * nbox, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_steps, 0, sizeof(int) * nbox, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_info, b->info.data(), sizeof(BoxInfo) * nbox, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_gbox, b->gbox.data(), sizeof(int) * nbox, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_gfirst, b->gfirst.data(), sizeof(int) * (ngroups + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete b;
+    return WB_ERR_CUDA;
+  }
+  if (upload_tables(b)) {
+    delete b;
+    return WB_ERR_CUDA;
+  }
+  *out = b;
+  return WB_OK;
+}
+
+int wb_batch_destroy(wb_batch* b) {
+  if (!b) return WB_OK;
+  drop_graph(b);
+  delete b;
+  return WB_OK;
+}
+
+int wb_batch_load(wb_batch* b, int box, const double* U, const double* bx, const double* by,
+                  const double* bz, int on_device, int primitive) {
+  if (!b || box < 0 || box >= b->nbox || !U || !bx || !by || !bz) return bfail(b, WB_ERR_INVALID, "bad argument");
+  const wb_desc& d = b->d[box];
+  const WbGeo& g = b->geo[box];
+  GridMap m;
+  for (int a = 0; a < 3; ++a) { m.N[a] = d.n[a]; m.np[a] = 1; m.bc[a] = d.bc[a]; }
+  m.npatch = 1;
+  const BoxInfo& bi = b->info[box];
+  cudaStream_t s = b->stream;
+  const long long nc = (long long)d.n[0] * d.n[1] * d.n[2];
+  const double* faces[3] = {bx, by, bz};
+  for (int comp = 0; comp < 8; ++comp) {
+    long long ext[3] = {d.n[0], d.n[1], d.n[2]};
+    const double* src;
+    if (comp < 5) src = U + comp * nc;
+    else { ext[comp - 5] += 1; src = faces[comp - 5]; }
+    const double* dsrc = src;
+    if (!on_device) {
+      cudaError_t e = cudaMemcpyAsync(b->staging, src, sizeof(double) * ext[0] * ext[1] * ext[2],
+                                      cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return bcuda(b, e, "batch load");
+      dsrc = b->staging;
+    }
+    double* dst = comp < 5 ? bi.v.q[comp] : bi.v.b[comp - 5];
+    wb_launch_scatter(dsrc, dst, comp, g, m, s);
+    if (!on_device) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return bcuda(b, e, "batch load");
+    }
+  }
+  double* q[8];
+  double* bb[3];
+  for (int c = 0; c < 8; ++c) q[c] = bi.v.q[c];
+  for (int c = 0; c < 3; ++c) bb[c] = bi.v.b[c];
+  wb_launch_halo(q, bb, g, m, s);
+  wb_launch_ccb(q, bb, g, 1, s);
+  if (primitive) wb_launch_prim_to_cons(q, g, 1, b->phys, s);
+  wb_launch_halo(q, bb, g, m, s);
+  cudaError_t e = cudaMemsetAsync(b->d_scal + box, 0, sizeof(WbScalars), s);
+  if (e != cudaSuccess) return bcuda(b, e, "batch load");
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  k_box_rate<<<(unsigned)((nint + 255) / 256), 256, 0, s>>>(b->d_info, b->d_scal, box, b->phys);
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return bcuda(b, e, "batch load");
+}
+
+int wb_batch_set_steps(wb_batch* b, int box, int nsteps) {
+  if (!b || box < -1 || box >= b->nbox || nsteps < 0) return bfail(b, WB_ERR_INVALID, "bad argument");
+  std::vector<int> v;
+  int first = box < 0 ? 0 : box, count = box < 0 ? b->nbox : 1;
+  v.assign(count, nsteps);
+  cudaError_t e = cudaMemcpyAsync(b->d_steps + first, v.data(), sizeof(int) * count, cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return bcuda(b, e, "set steps");
+}
+
+int wb_batch_advance(wb_batch* b, int nsteps, int use_graph) {
+  if (!b || nsteps < 0) return bfail(b, WB_ERR_INVALID, "bad argument");
+  if (nsteps == 0) return WB_OK;
+  cudaError_t e;
+  if (use_graph && b->graph_ok) {
+    if (!b->graph || b->graph_steps != nsteps) {
+      drop_graph(b);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t le = enqueue_advance(b, nsteps);
+        e = cudaStreamEndCapture(b->stream, &graph);
+        if (le != cudaSuccess) e = le;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph = nullptr;
+        b->graph_ok = false;  // fall back to direct launches
+      } else {
+        b->graph_steps = nsteps;
+      }
+    }
+    if (b->graph) {
+      e = cudaGraphLaunch(b->graph, b->stream);
+      if (e != cudaSuccess) return bcuda(b, e, "graph launch");
+      return read_sync_error(b);
+    }
+  }
+  e = enqueue_advance(b, nsteps);
+  if (e != cudaSuccess) return bcuda(b, e, "batch launch");
+  return read_sync_error(b);
+}
+
+int wb_batch_read(wb_batch* b, int box, double* U, double* bx, double* by, double* bz, double* B,
+                  int on_device) {
+  if (!b || box < 0 || box >= b->nbox) return bfail(b, WB_ERR_INVALID, "bad argument");
+  const wb_desc& d = b->d[box];
+  const WbGeo& g = b->geo[box];
+  GridMap m;
+  for (int a = 0; a < 3; ++a) { m.N[a] = d.n[a]; m.np[a] = 1; m.bc[a] = d.bc[a]; }
+  m.npatch = 1;
+  const BoxInfo& bi = b->info[box];
+  cudaStream_t s = b->stream;
+  const long long nc = (long long)d.n[0] * d.n[1] * d.n[2];
+  double* faces[3] = {bx, by, bz};
+  for (int comp = 0; comp < 11; ++comp) {
+    double* dst;
+    const double* src;
+    int mcomp = comp;
+    long long ext[3] = {d.n[0], d.n[1], d.n[2]};
+    if (comp < 5) { if (!U) continue; dst = U + comp * nc; src = bi.v.q[comp]; }
+    else if (comp < 8) {
+      if (!faces[comp - 5]) continue;
+      dst = faces[comp - 5]; src = bi.v.b[comp - 5]; ext[comp - 5] += 1;
+    } else {
+      if (!B) continue;
+      dst = B + (comp - 8) * nc; src = bi.v.q[F_BX + comp - 8]; mcomp = 0;
+    }
+    double* ddst = on_device ? dst : b->staging;
+    wb_launch_gather(src, ddst, mcomp, g, m, s);
+    if (!on_device) {
+      cudaError_t e = cudaMemcpyAsync(dst, b->staging, sizeof(double) * ext[0] * ext[1] * ext[2],
+                                      cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return bcuda(b, e, "batch read");
+    }
+  }
+  return bcuda(b, cudaGetLastError(), "batch read");
+}
+
+int wb_batch_counters(wb_batch* b, int box, wb_counters_t* c) {
+  if (!b || !c || box < 0 || box >= b->nbox) return bfail(b, WB_ERR_INVALID, "bad argument");
+  WbScalars sc;
+  cudaError_t e = cudaMemcpyAsync(&sc, b->d_scal + box, sizeof(sc), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "batch counters");
+  c->steps = sc.steps;
+  c->floor_hits = sc.floor_hits;
+  c->unphysical = sc.unphysical;
+  c->t = sc.t;
+  c->last_dt = sc.dt;
+  return WB_OK;
+}
+
+int wb_batch_config(wb_batch* b, int seg_len, int blocks_per_sm, long long barrier_budget_cycles) {
+  if (!b) return WB_ERR_INVALID;
+  if (seg_len > 0) b->seg_len = seg_len;
+  if (blocks_per_sm > 0) b->blocks_per_sm = std::min(blocks_per_sm, b->max_blocks_per_sm);
+  if (barrier_budget_cycles > 0) b->budget = barrier_budget_cycles;
+  drop_graph(b);
+  return upload_tables(b);
+}
+
+int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* groups) {
+  if (!b) return WB_ERR_INVALID;
+  if (seg_len) *seg_len = b->seg_len;
+  if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+  if (groups) *groups = (int)b->gfirst.size() - 1;
+  return WB_OK;
+}
+
+// Online autotuner: time trial_steps steps under each candidate segment
+// length, then each block count, keep the fastest.  The candidates change
+// only the work decomposition, so the trial steps are ordinary steps of the
+// simulation (results do not depend on the configuration).
+int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms) {
+  if (!b || trial_steps < 1) return bfail(b, WB_ERR_INVALID, "bad argument");
+  const int segs[] = {16, 24, 32, 48, 64, 96};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto trial = [&](int seg, int bps, float* ms) -> int {
+    int rc = wb_batch_config(b, seg, bps, 0);
+    if (rc) return rc;
+    cudaEventRecord(e0, b->stream);
+    cudaError_t e = enqueue_advance(b, trial_steps);
+    if (e != cudaSuccess) return bcuda(b, e, "autotune");
+    cudaEventRecord(e1, b->stream);
+    rc = read_sync_error(b);
+    if (rc) return rc;
+    cudaEventElapsedTime(ms, e0, e1);
+    return WB_OK;
+  };
+  int best_seg = b->seg_len, best_b = b->max_blocks_per_sm;
+  float best = 1e30f, ms = 0.f;
+  int rc = WB_OK;
+  for (int seg : segs) {
+    rc = trial(seg, b->max_blocks_per_sm, &ms);
+    if (rc) break;
+    if (ms < best) { best = ms; best_seg = seg; }
+  }
+  for (int bps = 1; rc == WB_OK && bps < b->max_blocks_per_sm; ++bps) {
+    rc = trial(best_seg, bps, &ms);
+    if (rc) break;
+    if (ms < best) { best = ms; best_b = bps; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = wb_batch_config(b, best_seg, best_b, 0);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneKey key;
+    for (int i = 0; i < b->nbox; ++i) key.sizes.push_back(b->d[i].n[0] * 1000000 + b->d[i].n[1] * 1000 + b->d[i].n[2]);
+    std::sort(key.sizes.begin(), key.sizes.end());
+    g_tune_cache[key] = {best_seg, best_b};
+  }
+  if (best_ms) *best_ms = best;
+  return WB_OK;
+}
+
+const char* wb_batch_last_error(const wb_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+}  // extern "C"

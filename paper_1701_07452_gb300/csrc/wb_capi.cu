@@ -152,25 +152,26 @@ WbBox box(int l0, int h0, int l1, int h1, int l2, int h2) {
 StageArgs stage_args(wb_grid* g, long long p0, int nslots) {
   StageArgs a;
   std::memset(&a, 0, sizeof(a));
-  for (int c = 0; c < 8; ++c) a.q[c] = g->q[c] + p0 * g->geo.V;
-  for (int c = 0; c < 3; ++c) a.b[c] = g->b[c] + p0 * g->geo.V;
+  WbView& v = a.v;
+  for (int c = 0; c < 8; ++c) v.q[c] = g->q[c] + p0 * g->geo.V;
+  for (int c = 0; c < 3; ++c) v.b[c] = g->b[c] + p0 * g->geo.V;
   a.slot_q = g->geo.V;
   for (int d = 0; d < 3; ++d) {
     for (int c = 0; c < 8; ++c) {
-      a.Fp[d][c] = g->Fp[d][c];
-      a.Fc[d][c] = g->Fc[d][c];
-      a.qh[d][c] = g->qh[d][c];
+      v.Fp[d][c] = g->Fp[d][c];
+      v.Fc[d][c] = g->Fc[d][c];
+      v.qh[d][c] = g->qh[d][c];
     }
-    a.Eref[d] = g->Eref[d];
-    a.Eedge[d] = g->Eedge[d];
-    a.bh[d] = g->bh[d];
-    a.Erefh[d] = g->Erefh[d];
-    a.Eedgeh[d] = g->Eedgeh[d];
+    v.Eref[d] = g->Eref[d];
+    v.Eedge[d] = g->Eedge[d];
+    v.bh[d] = g->bh[d];
+    v.Erefh[d] = g->Erefh[d];
+    v.Eedgeh[d] = g->Eedgeh[d];
   }
   a.slot_w = g->geo.V;
-  a.geo = g->geo;
+  v.geo = g->geo;
+  v.scal = g->scal;
   a.phys = g->phys;
-  a.scal = g->scal;
   a.nslots = nslots;
   return a;
 }
@@ -178,9 +179,9 @@ StageArgs stage_args(wb_grid* g, long long p0, int nslots) {
 SweepArgs sweep_args(wb_grid* g, const StageArgs& s, int dir, bool corr, const WbBox& bx) {
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
-  for (int c = 0; c < 8; ++c) a.q[c] = corr ? s.qh[dir][c] : s.q[c];
-  a.bn = corr ? s.bh[dir] : s.b[dir];
-  for (int c = 0; c < 8; ++c) a.F[c] = corr ? s.Fc[dir][c] : s.Fp[dir][c];
+  for (int c = 0; c < 8; ++c) a.q[c] = corr ? s.v.qh[dir][c] : s.v.q[c];
+  a.bn = corr ? s.v.bh[dir] : s.v.b[dir];
+  for (int c = 0; c < 8; ++c) a.F[c] = corr ? s.v.Fc[dir][c] : s.v.Fp[dir][c];
   a.slot_in = corr ? s.slot_w : s.slot_q;
   a.slot_out = s.slot_w;
   a.geo = g->geo;
@@ -214,9 +215,11 @@ void enqueue_pass(wb_grid* g, long long p0, int nslots) {
   sweep(g, 2, sweep_args(g, A, 2, false, box(-4, N0 + 3, -4, N1 + 3, -3, N2 + 3)), nslots);
   // Step 2: reference EMF; Step 3: corner EMFs
   wb_launch_eref(A, box(-4, N0 + 3, -4, N1 + 3, -4, N2 + 3), s);
-  wb_launch_edge(A, 2, false, box(-3, N0 + 3, -3, N1 + 3, -1, N2), s);
-  wb_launch_edge(A, 1, false, box(-3, N0 + 3, -1, N1, -3, N2 + 3), s);
-  wb_launch_edge(A, 0, false, box(-1, N0, -3, N1 + 3, -3, N2 + 3), s);
+  {
+    WbBox eb[3] = {box(-1, N0, -3, N1 + 3, -3, N2 + 3), box(-3, N0 + 3, -1, N1, -3, N2 + 3),
+                   box(-3, N0 + 3, -3, N1 + 3, -1, N2)};
+    wb_launch_edges(A, false, eb, s);
+  }
   // Step 4: b^{n+1/2}
   {
     WbBox bb[3] = {box(-3, N0 + 3, -1, N1, -1, N2), box(-1, N0, -3, N1 + 3, -1, N2),
@@ -224,18 +227,22 @@ void enqueue_pass(wb_grid* g, long long p0, int nslots) {
     wb_launch_ct(A, false, bb, s);
   }
   // Steps 5, 7: transverse-flux preconditioned states
-  wb_launch_transverse(A, 0, box(-3, N0 + 2, -1, N1, -1, N2), s);
-  wb_launch_transverse(A, 1, box(-1, N0, -3, N1 + 2, -1, N2), s);
-  wb_launch_transverse(A, 2, box(-1, N0, -1, N1, -3, N2 + 2), s);
+  {
+    WbBox tb[3] = {box(-3, N0 + 2, -1, N1, -1, N2), box(-1, N0, -3, N1 + 2, -1, N2),
+                   box(-1, N0, -1, N1, -3, N2 + 2)};
+    wb_launch_transverse(A, tb, s);
+  }
   // Steps 6, 7: corrector fluxes
   sweep(g, 0, sweep_args(g, A, 0, true, box(-1, N0 + 1, -1, N1, -1, N2)), nslots);
   sweep(g, 1, sweep_args(g, A, 1, true, box(-1, N0, -1, N1 + 1, -1, N2)), nslots);
   sweep(g, 2, sweep_args(g, A, 2, true, box(-1, N0, -1, N1, -1, N2 + 1)), nslots);
   // Step 8: half-step reference EMF; Step 9: corner EMFs
   wb_launch_eref_half(A, box(-1, N0, -1, N1, -1, N2), s);
-  wb_launch_edge(A, 2, true, box(0, N0, 0, N1, 0, N2 - 1), s);
-  wb_launch_edge(A, 1, true, box(0, N0, 0, N1 - 1, 0, N2), s);
-  wb_launch_edge(A, 0, true, box(0, N0 - 1, 0, N1, 0, N2), s);
+  {
+    WbBox eb[3] = {box(0, N0 - 1, 0, N1, 0, N2), box(0, N0, 0, N1 - 1, 0, N2),
+                   box(0, N0, 0, N1, 0, N2 - 1)};
+    wb_launch_edges(A, true, eb, s);
+  }
   // Step 11 (faces), then Step 10 + zone field + floors + next signal rate
   {
     WbBox bb[3] = {box(0, N0, 0, N1 - 1, 0, N2 - 1), box(0, N0 - 1, 0, N1, 0, N2 - 1),

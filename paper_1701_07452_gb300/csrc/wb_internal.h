@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "wb_device.cuh"
+#include "wb_units.cuh"
 
 struct SweepArgs {
   const double* q[8];      // input zone fields (slot 0)
@@ -18,25 +19,13 @@ struct SweepArgs {
   int seg_len;             // faces per segment (set at launch)
 };
 
-// Pointers of one pipeline pass over a batch of patches.
+// Pointers of one pipeline pass over a batch of patches: the view holds the
+// slot-0 pointers; slot s of the state is at +s*slot_q, of the workspace at
+// +s*slot_w.
 struct StageArgs {
-  // state of the batch (slot 0 = first patch of the batch), stride slot_q
-  double* q[8];
-  double* b[3];
-  long long slot_q;
-  // workspace (stride slot_w)
-  double* Fp[3][8];
-  double* Fc[3][8];
-  double* Eref[3];
-  double* Eedge[3];
-  double* bh[3];
-  double* qh[3][8];
-  double* Erefh[3];
-  double* Eedgeh[3];
-  long long slot_w;
-  WbGeo geo;
+  WbView v;
+  long long slot_q, slot_w;
   WbPhys phys;
-  WbScalars* scal;
   int nslots;
 };
 
@@ -51,10 +40,9 @@ struct GridMap {
 void wb_launch_sweep(int dir, const SweepArgs& a, int nslots, cudaStream_t s);
 
 void wb_launch_eref(const StageArgs& a, const WbBox& box, cudaStream_t s);
-void wb_launch_edge(const StageArgs& a, int axis, bool corrector, const WbBox& box,
-                    cudaStream_t s);
+void wb_launch_edges(const StageArgs& a, bool corrector, const WbBox box[3], cudaStream_t s);
 void wb_launch_ct(const StageArgs& a, bool final_step, const WbBox box[3], cudaStream_t s);
-void wb_launch_transverse(const StageArgs& a, int dir, const WbBox& box, cudaStream_t s);
+void wb_launch_transverse(const StageArgs& a, const WbBox box[3], cudaStream_t s);
 void wb_launch_eref_half(const StageArgs& a, const WbBox& box, cudaStream_t s);
 void wb_launch_final(const StageArgs& a, cudaStream_t s);
 

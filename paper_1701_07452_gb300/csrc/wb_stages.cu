@@ -4,6 +4,7 @@
 // one patch slot (blockIdx.y); all arrays share the padded patch geometry.
 #include "wb_device.cuh"
 #include "wb_internal.h"
+#include <cstring>
 
 namespace {
 
@@ -25,185 +26,72 @@ inline dim3 grid_for(long long n, int nslots, int bs) {
   return dim3((unsigned)((n + bs - 1) / bs), (unsigned)nslots);
 }
 
-// Step 2: zone-centred reference EMF E = -v x B from q^n.
+// Step 2: zone-centred reference EMF from q^n.
 __global__ void k_eref(StageArgs A, WbBox box) {
-  if (!(A.scal->dt > 0.0)) return;
+  if (!(A.v.scal->dt > 0.0)) return;
   int i, j, k;
   if (!box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  const long long o = blockIdx.y * A.slot_q + wb_at(A.geo, i, j, k);
-  const long long w = blockIdx.y * A.slot_w + wb_at(A.geo, i, j, k);
-  double ir = 1.0 / A.q[F_RHO][o];
-  double vx = A.q[F_MX][o] * ir, vy = A.q[F_MY][o] * ir, vz = A.q[F_MZ][o] * ir;
-  double bx = A.q[F_BX][o], by = A.q[F_BY][o], bz = A.q[F_BZ][o];
-  A.Eref[0][w] = vz * by - vy * bz;
-  A.Eref[1][w] = vx * bz - vz * bx;
-  A.Eref[2][w] = vy * bx - vx * by;
+  wbu::eref(A.v, blockIdx.y * A.slot_q, blockIdx.y * A.slot_w, i, j, k);
 }
 
-// Steps 3 and 9: upwinded corner EMF (GS05 "CT-contact" form).  Edge along
-// axis C at the low faces of axes a = C+1 and b = C+2 (cyclic).  Face EMFs
-// E^a = -F_a[B_b], E^b = +F_b[B_a]; the corner value is their average plus
-// one quarter of [(dE/db) at -3/4 minus (dE/db) at -1/4] and the same along
-// a, each derivative taken from the zone upwind of the mass flux through the
-// face it sits on (the mean of both zones when that flux is zero).
-template <int C>
-__global__ void k_edge(StageArgs A, bool corr, WbBox box) {
-  if (!(A.scal->dt > 0.0)) return;
-  constexpr int a = (C + 1) % 3, b = (C + 2) % 3;
+inline WbBox box_union(const WbBox b[3]) {
+  WbBox u = b[0];
+  for (int n = 1; n < 3; ++n)
+    for (int d = 0; d < 3; ++d) {
+      u.lo[d] = b[n].lo[d] < u.lo[d] ? b[n].lo[d] : u.lo[d];
+      u.hi[d] = b[n].hi[d] > u.hi[d] ? b[n].hi[d] : u.hi[d];
+    }
+  return u;
+}
+
+struct Boxes3 {
+  WbBox b[3];
+  WbBox u;
+};
+
+// Steps 3 and 9: the three corner-EMF components, one thread per index of
+// the union of their boxes.
+__global__ void k_edges(StageArgs A, bool corr, Boxes3 B) {
+  if (!(A.v.scal->dt > 0.0)) return;
   int i, j, k;
-  if (!box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  const WbGeo& g = A.geo;
-  const long long o = blockIdx.y * A.slot_w + wb_at(g, i, j, k);
-  const long long sa = a == 0 ? 1 : (a == 1 ? g.sy : g.sz);
-  const long long sb = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
-  double* const* Fa = corr ? A.Fc[a] : A.Fp[a];
-  double* const* Fb = corr ? A.Fc[b] : A.Fp[b];
-  const double* Er = corr ? A.Erefh[C] : A.Eref[C];
-  const double Ea_0 = -Fa[F_BX + b][o];
-  const double Ea_m = -Fa[F_BX + b][o - sb];
-  const double Eb_0 = Fb[F_BX + a][o];
-  const double Eb_m = Fb[F_BX + a][o - sa];
-  const double ma_0 = Fa[F_RHO][o], ma_m = Fa[F_RHO][o - sb];
-  const double mb_0 = Fb[F_RHO][o], mb_m = Fb[F_RHO][o - sa];
-  const double R00 = Er[o], Rm0 = Er[o - sa], R0m = Er[o - sb], Rmm = Er[o - sa - sb];
-  double db_hi_m = Rm0 - Eb_m, db_hi_0 = R00 - Eb_0;
-  double db_hi = ma_0 > 0.0 ? db_hi_m : (ma_0 < 0.0 ? db_hi_0 : 0.5 * (db_hi_m + db_hi_0));
-  double db_lo_m = Eb_m - Rmm, db_lo_0 = Eb_0 - R0m;
-  double db_lo = ma_m > 0.0 ? db_lo_m : (ma_m < 0.0 ? db_lo_0 : 0.5 * (db_lo_m + db_lo_0));
-  double da_hi_m = R0m - Ea_m, da_hi_0 = R00 - Ea_0;
-  double da_hi = mb_0 > 0.0 ? da_hi_m : (mb_0 < 0.0 ? da_hi_0 : 0.5 * (da_hi_m + da_hi_0));
-  double da_lo_m = Ea_m - Rmm, da_lo_0 = Ea_0 - Rm0;
-  double da_lo = mb_m > 0.0 ? da_lo_m : (mb_m < 0.0 ? da_lo_0 : 0.5 * (da_lo_m + da_lo_0));
-  double* out = corr ? A.Eedgeh[C] : A.Eedge[C];
-  out[o] = 0.25 * (Ea_0 + Ea_m + Eb_0 + Eb_m) + 0.25 * (db_lo - db_hi) + 0.25 * (da_lo - da_hi);
+  if (!box_index(B.u, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long wo = blockIdx.y * A.slot_w;
+  if (wbu::in_box(B.b[0], i, j, k)) wbu::edge<0>(A.v, wo, corr, i, j, k);
+  if (wbu::in_box(B.b[1], i, j, k)) wbu::edge<1>(A.v, wo, corr, i, j, k);
+  if (wbu::in_box(B.b[2], i, j, k)) wbu::edge<2>(A.v, wo, corr, i, j, k);
 }
 
-// Steps 4 and 11: b_out = b_in - tau curl E on the faces normal to D.
-template <int D>
-__global__ void k_ct(StageArgs A, bool fin, WbBox box) {
-  const double dt = A.scal->dt;
+// Steps 4 and 11: constrained transport of the three face components.
+__global__ void k_ct(StageArgs A, bool fin, Boxes3 B) {
+  const double dt = A.v.scal->dt;
   if (!(dt > 0.0)) return;
-  constexpr int a = (D + 1) % 3, b = (D + 2) % 3;
   int i, j, k;
-  if (!box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  const WbGeo& g = A.geo;
-  const long long w = blockIdx.y * A.slot_w + wb_at(g, i, j, k);
-  const long long q = blockIdx.y * A.slot_q + wb_at(g, i, j, k);
-  const long long sa = a == 0 ? 1 : (a == 1 ? g.sy : g.sz);
-  const long long sb = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
-  const double* Eb = fin ? A.Eedgeh[b] : A.Eedge[b];
-  const double* Ea = fin ? A.Eedgeh[a] : A.Eedge[a];
-  const double tau = fin ? dt : 0.5 * dt;
-  double curl = (Eb[w + sa] - Eb[w]) * g.idx[a] - (Ea[w + sb] - Ea[w]) * g.idx[b];
-  double bn = A.b[D][q] - tau * curl;
-  if (fin) A.b[D][q] = bn;
-  else A.bh[D][w] = bn;
+  if (!box_index(B.u, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long qo = blockIdx.y * A.slot_q, wo = blockIdx.y * A.slot_w;
+  if (wbu::in_box(B.b[0], i, j, k)) wbu::ct<0>(A.v, qo, wo, fin, dt, i, j, k);
+  if (wbu::in_box(B.b[1], i, j, k)) wbu::ct<1>(A.v, qo, wo, fin, dt, i, j, k);
+  if (wbu::in_box(B.b[2], i, j, k)) wbu::ct<2>(A.v, qo, wo, fin, dt, i, j, k);
 }
 
-__device__ __forceinline__ double minmod_src(double x, double y) {
-  if (x > 0.0 && y > 0.0) return fmin(x, y);
-  if (x < 0.0 && y < 0.0) return fmax(x, y);
-  return 0.0;
-}
-
-// Steps 5 and 7: q^{n+1/2}_D = q^n - dt/2 (transverse flux divergence)
-// + dt/2 S_D, zone B_D := mean of b_D^{n+1/2}, with the GS08-type div B
-// source S_D built from face differences of b^n and minmod pairings.
-template <int D>
-__global__ void k_transverse(StageArgs A, WbBox box) {
-  const double dt = A.scal->dt;
+// Steps 5 and 7: the three transverse-flux preconditioned states.
+__global__ void k_transverse(StageArgs A, Boxes3 B) {
+  const double dt = A.v.scal->dt;
   if (!(dt > 0.0)) return;
-  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
   int i, j, k;
-  if (!box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  const WbGeo& g = A.geo;
-  const long long q = blockIdx.y * A.slot_q + wb_at(g, i, j, k);
-  const long long w = blockIdx.y * A.slot_w + wb_at(g, i, j, k);
-  const long long s[3] = {1, g.sy, g.sz};
-  const double hdt = 0.5 * dt;
-  double ir = 1.0 / A.q[F_RHO][q];
-  double v[3], B[3], db[3];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    v[e] = A.q[F_MX + e][q] * ir;
-    B[e] = A.q[F_BX + e][q];
-    db[e] = (A.b[e][q + s[e]] - A.b[e][q]) * g.idx[e];
-  }
-  double m2 = minmod_src(db[D], -db[t1]);  // for the t2 field component
-  double m1 = minmod_src(db[D], -db[t2]);  // for the t1 field component
-  double S[8];
-  S[F_RHO] = 0.0;
-#pragma unroll
-  for (int e = 0; e < 3; ++e) S[F_MX + e] = B[e] * db[D];
-  S[F_EN] = B[D] * v[D] * db[D] + B[t1] * v[t1] * m1 + B[t2] * v[t2] * m2;
-  S[F_BX + D] = 0.0;
-  S[F_BX + t1] = v[t1] * m1;
-  S[F_BX + t2] = v[t2] * m2;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    if (c == F_BX + D) continue;
-    // normal-field fluxes of a sweep vanish (F_d[B_d] = 0)
-    double d1 = (c == F_BX + t1) ? 0.0 : (A.Fp[t1][c][w + s[t1]] - A.Fp[t1][c][w]) * g.idx[t1];
-    double d2 = (c == F_BX + t2) ? 0.0 : (A.Fp[t2][c][w + s[t2]] - A.Fp[t2][c][w]) * g.idx[t2];
-    A.qh[D][c][w] = A.q[c][q] - hdt * (d1 + d2) + hdt * S[c];
-  }
-  A.qh[D][F_BX + D][w] = 0.5 * (A.bh[D][w] + A.bh[D][w + s[D]]);
+  if (!box_index(B.u, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+  const long long qo = blockIdx.y * A.slot_q, wo = blockIdx.y * A.slot_w;
+  if (wbu::in_box(B.b[0], i, j, k)) wbu::transverse<0>(A.v, qo, wo, dt, i, j, k);
+  if (wbu::in_box(B.b[1], i, j, k)) wbu::transverse<1>(A.v, qo, wo, dt, i, j, k);
+  if (wbu::in_box(B.b[2], i, j, k)) wbu::transverse<2>(A.v, qo, wo, dt, i, j, k);
 }
 
-// Step 8: reference EMF at n+1/2 from v of q^n - dt/2 div F* and B = mean of
-// b^{n+1/2}.
+// Step 8: half-step reference EMF.
 __global__ void k_eref_half(StageArgs A, WbBox box) {
-  const double dt = A.scal->dt;
+  const double dt = A.v.scal->dt;
   if (!(dt > 0.0)) return;
   int i, j, k;
   if (!box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  const WbGeo& g = A.geo;
-  const long long q = blockIdx.y * A.slot_q + wb_at(g, i, j, k);
-  const long long w = blockIdx.y * A.slot_w + wb_at(g, i, j, k);
-  const long long s[3] = {1, g.sy, g.sz};
-  const double hdt = 0.5 * dt;
-  double u[4];
-  const int comps[4] = {F_RHO, F_MX, F_MY, F_MZ};
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    double div = 0.0;
-#pragma unroll
-    for (int e = 0; e < 3; ++e)
-      div += (A.Fc[e][comps[c]][w + s[e]] - A.Fc[e][comps[c]][w]) * g.idx[e];
-    u[c] = A.q[comps[c]][q] - hdt * div;
-  }
-  double ir = 1.0 / u[0];
-  double vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
-  double B[3];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) B[e] = 0.5 * (A.bh[e][w] + A.bh[e][w + s[e]]);
-  A.Erefh[0][w] = vz * B[1] - vy * B[2];
-  A.Erefh[1][w] = vx * B[2] - vz * B[0];
-  A.Erefh[2][w] = vy * B[0] - vx * B[1];
-}
-
-// CFL signal rate sum_d (|v_d| + c_f,d)/dx_d of one zone (Sec. 3 fast speed).
-__device__ __forceinline__ double signal_rate(double rho, double mx, double my, double mz, double e,
-                                              double bx, double by, double bz, const WbPhys& P,
-                                              const WbGeo& g) {
-  double ir = 1.0 / rho;
-  double v[3] = {mx * ir, my * ir, mz * ir};
-  double B[3] = {bx, by, bz};
-  double ke = 0.5 * (mx * v[0] + my * v[1] + mz * v[2]);
-  double bb = bx * bx + by * by + bz * bz;
-  double p = P.gm1 * (e - ke - 0.5 * bb);
-  double a2 = P.gamma * p * ir;
-  double w = 0.0;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    double cn2 = B[d] * B[d] * ir;
-    double ct2 = (bb - B[d] * B[d]) * ir;
-    double dd = a2 - cn2;
-    double disc = dd * dd + ct2 * (ct2 + 2.0 * (a2 + cn2));
-    double cf = sqrt(0.5 * (a2 + cn2 + ct2 + sqrt(disc)));
-    w += (fabs(v[d]) + cf) * g.idx[d];
-  }
-  return w;
+  wbu::eref_half(A.v, blockIdx.y * A.slot_q, blockIdx.y * A.slot_w, dt, i, j, k);
 }
 
 __device__ __forceinline__ void block_max_atomic(double w, unsigned long long* dst) {
@@ -218,61 +106,28 @@ __device__ __forceinline__ void block_max_atomic(double w, unsigned long long* d
   if ((threadIdx.x & 31) == 0 && bits) atomicMax(dst, bits);
 }
 
-// Step 10 (+ the zone field of Step 11, floors and the next step's signal
-// rate): U^{n+1} = ((U^n - dt/dx dF*) - dt/dy dG*) - dt/dz dH* on interior
-// zones, zone B = mean of b^{n+1}.
+// Step 10 (+ zone field of Step 11, floors, next signal rate) on interior zones.
 __global__ void k_final(StageArgs A) {
-  const double dt = A.scal->dt;
+  const double dt = A.v.scal->dt;
   if (!(dt > 0.0)) return;
-  const WbGeo& g = A.geo;
+  const WbGeo& g = A.v.geo;
   WbBox box = {{0, 0, 0}, {g.n[0] - 1, g.n[1] - 1, g.n[2] - 1}};
   int i, j, k;
-  bool ok = box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k);
+  const bool ok = box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k);
   double w = 0.0;
-  if (ok) {
-    const long long q = blockIdx.y * A.slot_q + wb_at(g, i, j, k);
-    const long long wi = blockIdx.y * A.slot_w + wb_at(g, i, j, k);
-    const long long s[3] = {1, g.sy, g.sz};
-    const WbPhys& P = A.phys;
-    double cx = dt * g.idx[0], cy = dt * g.idx[1], cz = dt * g.idx[2];
-    double u[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double x = A.q[c][q];
-      x = x - cx * (A.Fc[0][c][wi + 1] - A.Fc[0][c][wi]);
-      x = x - cy * (A.Fc[1][c][wi + s[1]] - A.Fc[1][c][wi]);
-      x = x - cz * (A.Fc[2][c][wi + s[2]] - A.Fc[2][c][wi]);
-      u[c] = x;
-    }
-    double B[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      B[e] = 0.5 * (A.b[e][q] + A.b[e][q + s[e]]);
-      A.q[F_BX + e][q] = B[e];
-    }
-    long long hits = 0;
-    if (u[0] < P.rho_floor) { u[0] = P.rho_floor; ++hits; }
-    double ke = 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0];
-    double me = 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
-    double p = P.gm1 * (u[4] - ke - me);
-    if (p < P.p_floor) { u[4] = P.p_floor * P.inv_gm1 + ke + me; ++hits; }
-    bool fin = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]) &&
-               isfinite(u[4]) && u[0] > 0.0 && isfinite(p);
-#pragma unroll
-    for (int c = 0; c < 5; ++c) A.q[c][q] = u[c];
-    if (hits) atomicAdd((unsigned long long*)&A.scal->floor_hits, (unsigned long long)hits);
-    if (!fin) atomicAdd((unsigned long long*)&A.scal->unphysical, 1ULL);
-    w = signal_rate(u[0], u[1], u[2], u[3], u[4], B[0], B[1], B[2], P, g);
-    if (!fin) w = __longlong_as_double(0x7ff8000000000000LL);
-  }
-  block_max_atomic(w, &A.scal->wmax_next);
+  int hits = 0, bad = 0;
+  if (ok) w = wbu::final_update(A.v, blockIdx.y * A.slot_q, blockIdx.y * A.slot_w, dt, A.phys, i, j, k,
+                                &hits, &bad);
+  if (hits) atomicAdd((unsigned long long*)&A.v.scal->floor_hits, (unsigned long long)hits);
+  if (bad) atomicAdd((unsigned long long*)&A.v.scal->unphysical, (unsigned long long)bad);
+  block_max_atomic(w, &A.v.scal->wmax_next);
 }
 
 // Ghost fill of every patch: zone (i,j,k) outside the interior copies the
 // zone of the same global position wrapped (periodic) or clamped (outflow)
 // into the domain; face arrays use the same rule on their face index.
 __global__ void k_halo(StageArgs A, GridMap m) {
-  const WbGeo& g = A.geo;
+  const WbGeo& g = A.v.geo;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= g.V) return;
   long long p = blockIdx.y;
@@ -304,13 +159,13 @@ __global__ void k_halo(StageArgs A, GridMap m) {
   const long long dst = p * g.V + t;
   const long long src = src_patch * g.V + wb_at(g, sl[0], sl[1], sl[2]);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) A.q[c][dst] = A.q[c][src];
+  for (int c = 0; c < 8; ++c) A.v.q[c][dst] = A.v.q[c][src];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) A.b[c][dst] = A.b[c][src];
+  for (int c = 0; c < 3; ++c) A.v.b[c][dst] = A.v.b[c][src];
 }
 
 __global__ void k_dt_init(StageArgs A, long long npatch) {
-  const WbGeo& g = A.geo;
+  const WbGeo& g = A.v.geo;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
   double w = 0.0;
@@ -320,11 +175,11 @@ __global__ void k_dt_init(StageArgs A, long long npatch) {
     int j = (int)((r / g.n[0]) % g.n[1]);
     int k = (int)(r / ((long long)g.n[0] * g.n[1]));
     long long o = p * g.V + wb_at(g, i, j, k);
-    w = signal_rate(A.q[0][o], A.q[1][o], A.q[2][o], A.q[3][o], A.q[4][o], A.q[5][o], A.q[6][o],
-                    A.q[7][o], A.phys, g);
+    w = wbu::signal_rate(A.v.q[0][o], A.v.q[1][o], A.v.q[2][o], A.v.q[3][o], A.v.q[4][o], A.v.q[5][o], A.v.q[6][o],
+                    A.v.q[7][o], A.phys, g);
     if (!(w >= 0.0)) w = __longlong_as_double(0x7ff8000000000000LL);
   }
-  block_max_atomic(w, &A.scal->wmax_next);
+  block_max_atomic(w, &A.v.scal->wmax_next);
 }
 
 // dt of the next step from the signal rate of its start state (reading R3)
@@ -349,7 +204,7 @@ __global__ void k_dt_step(WbScalars* s, double cfl, double t_end) {
 }
 
 __global__ void k_ccb(StageArgs A, long long npatch) {
-  const WbGeo& g = A.geo;
+  const WbGeo& g = A.v.geo;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
   if (t >= nint * npatch) return;
@@ -360,12 +215,12 @@ __global__ void k_ccb(StageArgs A, long long npatch) {
   long long o = p * g.V + wb_at(g, i, j, k);
   const long long s[3] = {1, g.sy, g.sz};
 #pragma unroll
-  for (int e = 0; e < 3; ++e) A.q[F_BX + e][o] = 0.5 * (A.b[e][o] + A.b[e][o + s[e]]);
+  for (int e = 0; e < 3; ++e) A.v.q[F_BX + e][o] = 0.5 * (A.v.b[e][o] + A.v.b[e][o + s[e]]);
 }
 
 // primitive (rho, v, P) in fields 0..4 -> conserved, with the zone field (Eq. totenergy)
 __global__ void k_prim_to_cons(StageArgs A, long long npatch) {
-  const WbGeo& g = A.geo;
+  const WbGeo& g = A.v.geo;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
   if (t >= nint * npatch) return;
@@ -374,12 +229,12 @@ __global__ void k_prim_to_cons(StageArgs A, long long npatch) {
   int j = (int)((r / g.n[0]) % g.n[1]);
   int k = (int)(r / ((long long)g.n[0] * g.n[1]));
   long long o = p * g.V + wb_at(g, i, j, k);
-  double rho = A.q[0][o], vx = A.q[1][o], vy = A.q[2][o], vz = A.q[3][o], pr = A.q[4][o];
-  double bx = A.q[5][o], by = A.q[6][o], bz = A.q[7][o];
-  A.q[1][o] = rho * vx;
-  A.q[2][o] = rho * vy;
-  A.q[3][o] = rho * vz;
-  A.q[4][o] = pr * A.phys.inv_gm1 + 0.5 * rho * (vx * vx + vy * vy + vz * vz) +
+  double rho = A.v.q[0][o], vx = A.v.q[1][o], vy = A.v.q[2][o], vz = A.v.q[3][o], pr = A.v.q[4][o];
+  double bx = A.v.q[5][o], by = A.v.q[6][o], bz = A.v.q[7][o];
+  A.v.q[1][o] = rho * vx;
+  A.v.q[2][o] = rho * vy;
+  A.v.q[3][o] = rho * vz;
+  A.v.q[4][o] = pr * A.phys.inv_gm1 + 0.5 * rho * (vx * vx + vy * vy + vz * vz) +
               0.5 * (bx * bx + by * by + bz * bz);
 }
 
@@ -416,7 +271,7 @@ __global__ void k_move(const double* src, double* dst, int comp, WbGeo g, GridMa
 }
 
 __global__ void k_divb(StageArgs A, long long npatch, unsigned long long* out) {
-  const WbGeo& g = A.geo;
+  const WbGeo& g = A.v.geo;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
   double w = 0.0;
@@ -426,8 +281,8 @@ __global__ void k_divb(StageArgs A, long long npatch, unsigned long long* out) {
     int j = (int)((r / g.n[0]) % g.n[1]);
     int k = (int)(r / ((long long)g.n[0] * g.n[1]));
     long long o = p * g.V + wb_at(g, i, j, k);
-    double dv = (A.b[0][o + 1] - A.b[0][o]) * g.idx[0] + (A.b[1][o + g.sy] - A.b[1][o]) * g.idx[1] +
-                (A.b[2][o + g.sz] - A.b[2][o]) * g.idx[2];
+    double dv = (A.v.b[0][o + 1] - A.v.b[0][o]) * g.idx[0] + (A.v.b[1][o + g.sy] - A.v.b[1][o]) * g.idx[1] +
+                (A.v.b[2][o + g.sz] - A.v.b[2][o]) * g.idx[2];
     w = fabs(dv);
   }
   block_max_atomic(w, out);
@@ -455,12 +310,20 @@ __global__ void k_fp64_probe(double* out, int iters) {
 }
 
 StageArgs mini_args(double* const q[8], double* const b[3], const WbGeo& geo) {
-  StageArgs a = {};
-  for (int c = 0; c < 8; ++c) a.q[c] = q[c];
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int c = 0; c < 8; ++c) a.v.q[c] = q[c];
   if (b)
-    for (int c = 0; c < 3; ++c) a.b[c] = b[c];
-  a.geo = geo;
+    for (int c = 0; c < 3; ++c) a.v.b[c] = b[c];
+  a.v.geo = geo;
   return a;
+}
+
+Boxes3 boxes3(const WbBox b[3]) {
+  Boxes3 B;
+  for (int n = 0; n < 3; ++n) B.b[n] = b[n];
+  B.u = box_union(b);
+  return B;
 }
 
 }  // namespace
@@ -469,24 +332,19 @@ void wb_launch_eref(const StageArgs& a, const WbBox& box, cudaStream_t s) {
   k_eref<<<grid_for(box_count(box), a.nslots, 256), 256, 0, s>>>(a, box);
 }
 
-void wb_launch_edge(const StageArgs& a, int axis, bool corr, const WbBox& box, cudaStream_t s) {
-  dim3 gr = grid_for(box_count(box), a.nslots, 256);
-  if (axis == 0) k_edge<0><<<gr, 256, 0, s>>>(a, corr, box);
-  else if (axis == 1) k_edge<1><<<gr, 256, 0, s>>>(a, corr, box);
-  else k_edge<2><<<gr, 256, 0, s>>>(a, corr, box);
+void wb_launch_edges(const StageArgs& a, bool corr, const WbBox box[3], cudaStream_t s) {
+  Boxes3 B = boxes3(box);
+  k_edges<<<grid_for(box_count(B.u), a.nslots, 256), 256, 0, s>>>(a, corr, B);
 }
 
 void wb_launch_ct(const StageArgs& a, bool fin, const WbBox box[3], cudaStream_t s) {
-  k_ct<0><<<grid_for(box_count(box[0]), a.nslots, 256), 256, 0, s>>>(a, fin, box[0]);
-  k_ct<1><<<grid_for(box_count(box[1]), a.nslots, 256), 256, 0, s>>>(a, fin, box[1]);
-  k_ct<2><<<grid_for(box_count(box[2]), a.nslots, 256), 256, 0, s>>>(a, fin, box[2]);
+  Boxes3 B = boxes3(box);
+  k_ct<<<grid_for(box_count(B.u), a.nslots, 256), 256, 0, s>>>(a, fin, B);
 }
 
-void wb_launch_transverse(const StageArgs& a, int dir, const WbBox& box, cudaStream_t s) {
-  dim3 gr = grid_for(box_count(box), a.nslots, 128);
-  if (dir == 0) k_transverse<0><<<gr, 128, 0, s>>>(a, box);
-  else if (dir == 1) k_transverse<1><<<gr, 128, 0, s>>>(a, box);
-  else k_transverse<2><<<gr, 128, 0, s>>>(a, box);
+void wb_launch_transverse(const StageArgs& a, const WbBox box[3], cudaStream_t s) {
+  Boxes3 B = boxes3(box);
+  k_transverse<<<grid_for(box_count(B.u), a.nslots, 128), 128, 0, s>>>(a, B);
 }
 
 void wb_launch_eref_half(const StageArgs& a, const WbBox& box, cudaStream_t s) {
@@ -494,7 +352,7 @@ void wb_launch_eref_half(const StageArgs& a, const WbBox& box, cudaStream_t s) {
 }
 
 void wb_launch_final(const StageArgs& a, cudaStream_t s) {
-  long long n = (long long)a.geo.n[0] * a.geo.n[1] * a.geo.n[2];
+  long long n = (long long)a.v.geo.n[0] * a.v.geo.n[1] * a.v.geo.n[2];
   k_final<<<grid_for(n, a.nslots, 256), 256, 0, s>>>(a);
 }
 
@@ -508,7 +366,7 @@ void wb_launch_dt_init(double* const q[8], const WbGeo& geo, long long npatch, c
                        WbScalars* scal, cudaStream_t s) {
   StageArgs a = mini_args(q, nullptr, geo);
   a.phys = ph;
-  a.scal = scal;
+  a.v.scal = scal;
   long long n = (long long)geo.n[0] * geo.n[1] * geo.n[2] * npatch;
   k_dt_init<<<grid_for(n, 1, 256), 256, 0, s>>>(a, npatch);
 }

@@ -1,0 +1,112 @@
+"""Batching pattern: many independent boxes of uneven sizes advanced by one
+persistent kernel with per-box dt (wb_batch_*), compared with the single-box
+grid path, alone vs in the mix, graph vs direct launch, after autotuning, and
+with a barrier wait forced to run out (error status, context still usable)."""
+import numpy as np
+import pytest
+
+from parity import state_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_07452_gb300 import binding
+    binding.lib()
+    return binding
+
+
+SIZES = [(8, 8, 8), (12, 10, 9), (16, 16, 16), (10, 14, 12), (6, 6, 6)]
+
+
+def boxes_and_states(sizes, seed0=100):
+    from paper_1701_07452_gb300.initial_conditions import random_box
+    boxes, states = [], []
+    for i, n in enumerate(sizes):
+        st = random_box(n, seed=seed0 + i)
+        boxes.append({"n": n, "length": st["length"]})
+        states.append(st)
+    return boxes, states
+
+
+def test_batch_matches_single_box_grids(wb):
+    boxes, states = boxes_and_states(SIZES)
+    bt = wb.Batch(boxes)
+    for i, st in enumerate(states):
+        bt.load_state(i, st)
+    bt.set_steps(-1, 4)
+    bt.advance(4)
+    for i, st in enumerate(states):
+        g = wb.Grid(boxes[i]["n"], length=boxes[i]["length"])
+        g.load_state(st)
+        g.advance(4)
+        assert state_err(bt.read(i), g.read()) < 1e-11, i
+        c = bt.counters(i)
+        assert c["steps"] == 4 and c["unphysical"] == 0
+        assert abs(c["t"] - g.counters()["t"]) <= 1e-13 * c["t"]
+
+
+def test_alone_and_in_the_mix_are_bit_identical(wb):
+    boxes, states = boxes_and_states(SIZES)
+    mix = wb.Batch(boxes, work_budget=8 << 20)  # several workspace groups
+    for i, st in enumerate(states):
+        mix.load_state(i, st)
+    mix.set_steps(-1, 3)
+    mix.set_steps(1, 2)  # a box that stops early
+    mix.advance(3)
+    for i in (0, 1, 2):
+        alone = wb.Batch([boxes[i]])
+        alone.load_state(0, states[i])
+        alone.set_steps(0, 2 if i == 1 else 3)
+        alone.advance(3)
+        for a, b in zip(alone.read(0), mix.read(i)):
+            assert np.array_equal(a, b), i
+    assert mix.counters(1)["steps"] == 2 and mix.counters(0)["steps"] == 3
+
+
+def test_graph_direct_and_autotuned_runs_agree(wb):
+    boxes, states = boxes_and_states(SIZES[:4], seed0=200)
+    runs = []
+    for mode in ("graph", "direct", "tuned"):
+        bt = wb.Batch(boxes)
+        for i, st in enumerate(states):
+            bt.load_state(i, st)
+        if mode == "tuned":
+            bt.set_steps(-1, 1000)
+            bt.autotune(trial_steps=1)          # real steps, any configuration
+            done = bt.counters(0)["steps"]
+            bt.set_steps(-1, 12 - done)
+            bt.advance(12 - done)
+        else:
+            bt.set_steps(-1, 12)
+            for _ in range(3):
+                bt.advance(4, use_graph=(mode == "graph"))
+        runs.append([bt.read(i) for i in range(len(boxes))])
+        assert all(bt.counters(i)["steps"] == 12 for i in range(len(boxes)))
+    for other in runs[1:]:
+        for ra, rb in zip(runs[0], other):
+            for a, b in zip(ra, rb):
+                assert np.array_equal(a, b)
+
+
+def test_barrier_timeout_returns_status_and_context_survives(wb):
+    boxes, states = boxes_and_states(SIZES[:3], seed0=300)
+    bt = wb.Batch(boxes)
+    for i, st in enumerate(states):
+        bt.load_state(i, st)
+    bt.set_steps(-1, 2)
+    bt.config(barrier_budget_cycles=1)     # every barrier wait runs out at once
+    with pytest.raises(wb.WombatError) as ei:
+        bt.advance(2, use_graph=False)
+    assert ei.value.code == wb.WB_ERR_TIMEOUT
+    # the context still works: a fresh batch advances normally
+    ok = wb.Batch(boxes)
+    for i, st in enumerate(states):
+        ok.load_state(i, st)
+    ok.set_steps(-1, 2)
+    ok.advance(2)
+    assert ok.counters(0)["steps"] == 2
