@@ -174,6 +174,141 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_mode(args):
+    """Secondary workloads, one JSON line each (not the headline line)."""
+    import numpy as np
+    import torch
+
+    from paper_1701_07452_gb300 import binding as wb
+    from paper_1701_07452_gb300 import serve as sv
+    from paper_1701_07452_gb300.initial_conditions import (random_box, turbulence_box,
+                                                           turbulence_box_device)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    if args.mode == "batch":
+        # ensemble: boxes of edge drawn from {16,...,128} (seed 4), data seed 4000+b
+        rng = np.random.default_rng(4)
+        edges = rng.choice([16, 24, 32, 48, 64, 96, 128], size=args.nbox)
+        states = [random_box(int(e), seed=4000 + b) for b, e in enumerate(edges)]
+        boxes = [{"n": (int(e),) * 3, "length": st["length"]} for e, st in zip(edges, states)]
+        steps = args.steps
+        tune = wb.Batch(boxes)
+        for i, st in enumerate(states):
+            tune.load_state(i, st)
+        tune.set_steps(-1, 1000)
+        tune.autotune(trial_steps=1)
+        cfg = tune.get_config()
+        del tune
+        bt = wb.Batch(boxes)
+        for i, st in enumerate(states):
+            bt.load_state(i, st)
+        bt.set_steps(-1, steps)
+        bt.advance(1, use_graph=True)       # capture + warm-up step
+        bt.set_steps(-1, steps)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        bt.advance(steps, use_graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = e0.elapsed_time(e1) * 1e-3
+        # the plain path: one box at a time through the single-grid API
+        t_plain = 0.0
+        worst = 0.0
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from parity import state_err
+        for i, (b, st) in enumerate(zip(boxes, states)):
+            g = wb.Grid(b["n"], length=b["length"])
+            g.load_state(st)
+            g.advance(1)
+            g.load_state(st)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            g.advance(steps + 1, sync=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_plain += e0.elapsed_time(e1) * 1e-3 * steps / (steps + 1)
+            if i < 8:
+                ref = wb.Batch([b])
+                ref.load_state(0, st)
+                ref.set_steps(0, steps + 1)
+                ref.advance(steps + 1)
+                worst = max(worst, state_err(ref.read(0), g.read()))
+            del g
+        cells = float(sum(int(e) ** 3 for e in edges)) * steps
+        line = {"metric": "solves/s (batched vs one box at a time)", "mode": "batch",
+                "value": args.nbox / t_batch, "unit": "solves/s", "higher_is_better": True,
+                "plain_solves_per_s": args.nbox / t_plain, "speedup": t_plain / t_batch,
+                "batched_cell_updates_per_s": cells / t_batch, "plain_cell_updates_per_s": cells / t_plain,
+                "steps": steps, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"{args.nbox} periodic boxes, edges from {{16..128}} (seed 4), "
+                                       f"random data seed 4000+b, {steps} steps each (solve = one box x "
+                                       f"{steps} steps)", "autotuned": cfg},
+                "batch_vs_grid_max_rel_err": worst}
+        print(json.dumps(line), flush=True)
+        return 0
+    if args.mode == "serve":
+        rng = np.random.default_rng(5)
+        gaps = rng.exponential(1.0 / 50.0, size=args.requests)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        ns = np.rint(np.exp(rng.uniform(np.log(32), np.log(192), size=args.requests))).astype(int)
+        nsteps = np.maximum(1, np.rint(rng.integers(50, 501, size=args.requests) * args.steps_scale)).astype(int)
+        reqs = []
+        for r in range(args.requests):
+            st = turbulence_box_device(int(ns[r]), 5000 + r, dev)
+            st = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in st.items()}
+            reqs.append(sv.Request(r, float(arrivals[r]), (int(ns[r]),) * 3, int(nsteps[r]), st))
+        srv = sv.Server(state_bytes=150 << 30, work_bytes=40 << 30, max_boxes=args.requests,
+                        max_n=int(ns.max()), tick_steps=5)
+        recs = srv.run(reqs)
+        summ = sv.summarize(recs)
+        line = {"metric": "serving p50/p99 completion latency and cell-updates/s", "mode": "serve",
+                "value": summ["cell_updates_per_s"], "unit": "cell-updates/s", "higher_is_better": True,
+                "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "solves_per_s": summ["solves_per_s"],
+                "wall_s": summ["wall_s"], "ticks": srv.ticks, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"{args.requests} requests, Poisson 50/s (seed 5), edge "
+                                       f"log-uniform 32..192, steps U{{50..500}} x {args.steps_scale}, "
+                                       "turbulence data seed 5000+r, 150 GB state budget, 5 steps per tick"}}
+        print(json.dumps(line), flush=True)
+        return 0
+    if args.mode in ("patches", "big"):
+        n, p = (512, 8) if args.mode == "patches" else (768, 12)
+        st = turbulence_box_device(n, SEED, dev)
+        def run(patches, batch):
+            g = wb.Grid((n, n, n), patches=(patches,) * 3, length=st["length"], batch_patches=batch)
+            g.load(st["W"], st["bx"], st["by"], st["bz"], on_device=True, primitive=True)
+            g.advance(1)
+            g.load(st["W"], st["bx"], st["by"], st["bz"], on_device=True, primitive=True)
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            g.advance(args.steps, sync=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out = g.read(on_device=True)
+            assert g.counters()["unphysical"] == 0
+            del g
+            torch.cuda.empty_cache()
+            return ms, out
+        ms_p, out_p = run(p, 152)
+        line = {"metric": METRIC, "mode": args.mode, "value": n ** 3 * args.steps / (ms_p * 1e-3),
+                "unit": UNIT, "higher_is_better": True, "steps": args.steps, "dtype": "f64",
+                "ms_per_step": ms_p / args.steps, "data": "synthetic",
+                "config": {"workload": f"{n}^3 periodic turbulence box in {p}^3 patches of {n // p}^3, "
+                                       "152 patches per pipeline pass"}}
+        if args.mode == "patches":
+            ms_s, out_s = run(1, 0)
+            same = all(bool(torch.equal(a, b)) for a, b in zip(out_p, out_s))
+            line["single_grid_value"] = n ** 3 * args.steps / (ms_s * 1e-3)
+            line["bit_exact_vs_single_grid"] = same
+        print(json.dumps(line), flush=True)
+        return 0
+    return 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,10 +318,19 @@ def main():
     ap.add_argument("--n", type=int, default=N_BOX)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--mode", default="box", choices=["box", "batch", "serve", "patches", "big"],
+                    help="box: the 256^3 box (default line); batch: ensemble of boxes, batched vs "
+                         "one at a time; serve: request stream; patches: 512^3 in 64^3 patches vs "
+                         "the single grid; big: 768^3 in 12^3 patches")
+    ap.add_argument("--nbox", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--steps-scale", type=float, default=0.1)
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.mode != "box":
+        return run_mode(args)
 
     import numpy as np
     import torch

@@ -215,6 +215,27 @@ int wb_batch_config(wb_batch* b, int seg_len, int blocks_per_sm, long long barri
 int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* groups);
 const char* wb_batch_last_error(const wb_batch* b);
 
+/* ---- serving: a batch as a pool boxes join and leave between launches ----
+ * wb_pool_create makes an empty batch with a state region of state_bytes
+ * (the HBM budget for resident runs), a shared workspace of work_bytes, up to
+ * max_boxes boxes and box edges up to max_n; physics (gamma, cfl, eps, sweby,
+ * floors) come from *physics and every admitted box must match them.
+ * wb_pool_admit places one box (state allocated first-fit in the region) and
+ * returns its slot in *box, or WB_ERR_NOMEM when the state region, the
+ * workspace or the slots cannot hold it; wb_pool_release frees a slot.  The
+ * wb_batch_* calls (load, set_steps, advance, read, counters) work on slots;
+ * workspace groups are rebuilt before the next advance after any change.
+ * wb_batch_steps_left copies the steps left of every slot (max_boxes ints).
+ * wb_pool_free_bytes reports the largest free block and the total free state
+ * bytes. */
+int wb_pool_bytes(size_t state_bytes, size_t work_bytes, int max_boxes, int max_n, size_t* bytes);
+int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes, int max_boxes,
+                   int max_n, void* dev_mem, size_t bytes, void* stream, wb_batch** out);
+int wb_pool_admit(wb_batch* b, const wb_desc* d, int* box);
+int wb_pool_release(wb_batch* b, int box);
+int wb_pool_free_bytes(wb_batch* b, size_t* largest, size_t* total);
+int wb_batch_steps_left(wb_batch* b, int* out);
+
 /* Self-test of the library's FP64 reciprocal and reciprocal-square-root
  * helpers (PTX approximations refined by a third-order correction) against
  * the CUDA library division and rsqrt on n inputs spread over [1e-40, 1e40]:

@@ -28,6 +28,8 @@ EXPORTED = (
     "wb_selftest_math", "wb_batch_bytes", "wb_batch_create", "wb_batch_destroy", "wb_batch_load",
     "wb_batch_set_steps", "wb_batch_advance", "wb_batch_read", "wb_batch_counters",
     "wb_batch_autotune", "wb_batch_config", "wb_batch_get_config", "wb_batch_last_error",
+    "wb_pool_bytes", "wb_pool_create", "wb_pool_admit", "wb_pool_release", "wb_pool_free_bytes",
+    "wb_batch_steps_left",
 )
 
 
@@ -120,6 +122,14 @@ def lib(build: bool = True):
                                               ctypes.POINTER(ctypes.c_int)]
             L.wb_batch_last_error.argtypes = [vp]
             L.wb_batch_last_error.restype = ctypes.c_char_p
+            L.wb_pool_bytes.argtypes = [ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_size_t)]
+            L.wb_pool_create.argtypes = [ctypes.POINTER(WbDesc), ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int,
+                                         ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+            L.wb_pool_admit.argtypes = [vp, ctypes.POINTER(WbDesc), ctypes.POINTER(ctypes.c_int)]
+            L.wb_pool_release.argtypes = [vp, ctypes.c_int]
+            L.wb_pool_free_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+            L.wb_batch_steps_left.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
             L.wb_noalloc_last_error.argtypes = []
             L.wb_noalloc_last_error.restype = ctypes.c_char_p
             _lib = L
@@ -306,6 +316,7 @@ class Batch:
 
         if not torch.cuda.is_available():
             raise RuntimeError("wombat: a CUDA device is required (no CPU fallback)")
+        self.phys_kw = kw
         self.nbox = len(boxes)
         self.n = [tuple(int(x) for x in b["n"]) for b in boxes]
         arr = (WbDesc * self.nbox)()
@@ -364,6 +375,9 @@ class Batch:
 
     def read(self, box):
         nx, ny, nz = self.n[box]
+        return self._read(box, nx, ny, nz)
+
+    def _read(self, box, nx, ny, nz):
         out = (np.empty((5, nz, ny, nx)), np.empty((nz, ny, nx + 1)), np.empty((nz, ny + 1, nx)),
                np.empty((nz + 1, ny, nx)), np.empty((3, nz, ny, nx)))
         self._check(lib().wb_batch_read(self._h, int(box), *[ctypes.c_void_p(_ptr(a)) for a in out], 0))
@@ -388,6 +402,63 @@ class Batch:
         a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
         self._check(lib().wb_batch_get_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"seg_len": a.value, "blocks_per_sm": b.value, "groups": c.value}
+
+
+class Pool(Batch):
+    """A batch whose boxes join and leave between launches (wb_pool_*): the
+    state region is the HBM budget of resident runs."""
+
+    def __init__(self, state_bytes, work_bytes, max_boxes=256, max_n=256, stream=None, **kw):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("wombat: a CUDA device is required (no CPU fallback)")
+        self.phys_kw = kw
+        self.physics = make_desc((8, 8, 8), **kw)
+        self.max_boxes = int(max_boxes)
+        nbytes = ctypes.c_size_t(0)
+        rc = lib().wb_pool_bytes(ctypes.c_size_t(int(state_bytes)), ctypes.c_size_t(int(work_bytes)),
+                                 self.max_boxes, int(max_n), ctypes.byref(nbytes))
+        if rc:
+            raise WombatError(rc, "invalid pool description")
+        self.nbytes = int(nbytes.value)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        rc = lib().wb_pool_create(ctypes.byref(self.physics), ctypes.c_size_t(int(state_bytes)),
+                                  ctypes.c_size_t(int(work_bytes)), self.max_boxes, int(max_n),
+                                  ctypes.c_void_p(self.workspace.data_ptr()), ctypes.c_size_t(self.nbytes),
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc:
+            raise WombatError(rc, "pool create failed")
+        self._h = h
+        self.n = {}
+
+    def admit(self, n, length=None, bc=(0, 0, 0)):
+        """Slot of a newly admitted box, or None when it does not fit now."""
+        d = make_desc(n, (1, 1, 1), length, bc=bc, **self.phys_kw)
+        slot = ctypes.c_int(-1)
+        rc = lib().wb_pool_admit(self._h, ctypes.byref(d), ctypes.byref(slot))
+        if rc == WB_ERR_NOMEM:
+            return None
+        self._check(rc)
+        self.n[slot.value] = tuple(int(x) for x in n)
+        return slot.value
+
+    def release(self, box):
+        self._check(lib().wb_pool_release(self._h, int(box)))
+        self.n.pop(box, None)
+
+    def steps_left(self):
+        out = (ctypes.c_int * self.max_boxes)()
+        self._check(lib().wb_batch_steps_left(self._h, out))
+        return list(out)
+
+    def free_bytes(self):
+        a, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        self._check(lib().wb_pool_free_bytes(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
 
 def step_noalloc(desc: WbDesc, U, bx, by, bz, U_out, bx_out, by_out, bz_out, dt_out=None,

@@ -342,9 +342,9 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
   }
 }
 
-// initial signal rate of one box
-__global__ void k_box_rate(BoxInfo* boxes, WbScalars* scal, int box, WbPhys P) {
-  const WbView& v = boxes[box].v;
+// initial signal rate of one box (the view is passed by value: the device box
+// table is only uploaded before the next launch of k_batch)
+__global__ void k_box_rate(WbView v, WbScalars* scal, WbPhys P) {
   const WbGeo& g = v.geo;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -357,7 +357,7 @@ __global__ void k_box_rate(BoxInfo* boxes, WbScalars* scal, int box, WbPhys P) {
     w = wbu::signal_rate(v.q[0][o], v.q[1][o], v.q[2][o], v.q[3][o], v.q[4][o], v.q[5][o], v.q[6][o],
                          v.q[7][o], P, g);
   }
-  warp_max_atomic(w, &scal[box].wmax_next);
+  warp_max_atomic(w, &scal->wmax_next);
 }
 
 const int kWorkB = 3 * 7 + 3 + 3 + 3 + 3 * 8;  // 54: corrector fluxes, half-step EMFs alias
@@ -371,19 +371,30 @@ std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (seg_len, blocks per
 
 }  // namespace
 
+// A batch is a pool: a state region shared by the resident boxes (first-fit
+// allocation on the host side), a workspace region shared by workspace groups
+// of the resident boxes, and device tables sized for max_boxes slots.
 struct wb_batch {
-  int nbox;
+  int cap;
+  std::vector<char> alive;
   std::vector<wb_desc> d;
   std::vector<WbGeo> geo;
+  std::vector<BoxInfo> info;
+  std::vector<size_t> state_off;              // doubles from the state base
+  std::map<size_t, size_t> free_;             // free state blocks: offset -> length (doubles)
+  size_t state_cap, work_cap, staging_elems;  // doubles
+  int max_n;
+  wb_desc phys_desc;
   WbPhys phys;
   double cfl;
   cudaStream_t stream;
   char* mem;
   size_t bytes;
-  // host copies
-  std::vector<BoxInfo> info;
+  double* state_base;
+  double* work_base;
   std::vector<int> gbox, gfirst;
-  // device regions
+  bool dirty;
+  // device tables
   BoxInfo* d_info;
   WbScalars* d_scal;
   int* d_steps;
@@ -393,7 +404,6 @@ struct wb_batch {
   long long* d_pre_off;
   unsigned* d_sync;
   double* staging;
-  size_t staging_elems;
   size_t pre_cap;
   // launch configuration
   int seg_len;
@@ -406,6 +416,7 @@ struct wb_batch {
   int graph_steps;
   bool graph_ok;
   std::string err;
+  int nbox;  // slots in use (highest alive slot + 1)
 };
 
 namespace {
@@ -445,52 +456,36 @@ bool same_physics(const wb_desc& a, const wb_desc& b) {
   return true;
 }
 
-struct BatchLayout {
-  size_t state, work, tables, staging, total;
-  std::vector<int> gbox, gfirst;
-  std::vector<size_t> state_off, work_off;  // per box, in doubles
-  size_t pre_cap;
-};
-
-// Boxes go to workspace groups in order until a group's intermediates would
-// exceed work_budget; the state of every box stays resident.
-BatchLayout plan(int nbox, const wb_desc* d, size_t work_budget) {
-  BatchLayout L;
-  L.state_off.resize(nbox);
-  L.work_off.resize(nbox);
-  size_t st = 0, maxg = 0, cur = 0, gmax = 0;
-  L.gfirst.push_back(0);
-  for (int b = 0; b < nbox; ++b) {
-    WbGeo g = geo_of(d[b]);
-    L.state_off[b] = st;
-    st += (size_t)g.V * 11;
-    size_t w = (size_t)g.V * kWorkB;
-    if (cur > 0 && (cur + w) * sizeof(double) > work_budget) {
-      L.gfirst.push_back((int)L.gbox.size());
-      cur = 0;
-    }
-    L.work_off[b] = cur;
-    cur += w;
-    if (cur > maxg) maxg = cur;
-    L.gbox.push_back(b);
-    size_t ge = (size_t)(d[b].n[0] + 1) * (d[b].n[1] + 1) * (d[b].n[2] + 1);
-    if (ge > gmax) gmax = ge;
-  }
-  L.gfirst.push_back((int)L.gbox.size());
-  const int ngroups = (int)L.gfirst.size() - 1;
-  L.state = al(st * sizeof(double));
-  L.work = al(maxg * sizeof(double));
-  L.pre_cap = (size_t)ngroups * BS_COUNT + (size_t)BS_COUNT * 3 * nbox + 16;
-  L.tables = al(sizeof(BoxInfo) * nbox) + al(sizeof(WbScalars) * nbox) + al(sizeof(int) * nbox) +
-             al(sizeof(int) * nbox) + al(sizeof(int) * (ngroups + 1)) +
-             al(sizeof(long long) * L.pre_cap) + al(sizeof(long long) * ngroups * BS_COUNT) +
-             al(sizeof(unsigned) * 8);
-  L.staging = al(sizeof(double) * gmax);
-  L.total = L.state + L.work + L.tables + L.staging;
-  return L;
+bool box_ok(const wb_desc& d) {
+  for (int a = 0; a < 3; ++a)
+    if (d.n[a] < 1 || d.patches[a] != 1 || !(d.length[a] > 0.0) ||
+        (d.bc[a] != WB_BC_PERIODIC && d.bc[a] != WB_BC_OUTFLOW))
+      return false;
+  return true;
 }
 
-// chunk prefix tables for the current seg_len
+// state doubles of a box (rounded to 256 bytes so every field stays aligned)
+size_t state_doubles(const WbGeo& g) { return al((size_t)g.V * 11 * sizeof(double)) / sizeof(double); }
+size_t work_doubles(const WbGeo& g) { return al((size_t)g.V * kWorkB * sizeof(double)) / sizeof(double); }
+
+struct PoolSizes {
+  size_t state, work, tables, staging, total, pre_cap;
+};
+
+PoolSizes pool_sizes(size_t state_bytes, size_t work_bytes, int cap, int max_n) {
+  PoolSizes P;
+  P.state = al(state_bytes);
+  P.work = al(work_bytes);
+  P.pre_cap = (size_t)BS_COUNT * (4 * (size_t)cap + 2) + 16;
+  P.tables = al(sizeof(BoxInfo) * cap) + al(sizeof(WbScalars) * cap) + al(sizeof(int) * cap) +
+             al(sizeof(int) * cap) + al(sizeof(int) * (cap + 1)) + al(sizeof(long long) * P.pre_cap) +
+             al(sizeof(long long) * (size_t)cap * BS_COUNT) + al(sizeof(unsigned) * 8);
+  P.staging = al(sizeof(double) * (size_t)(max_n + 1) * (max_n + 1) * (max_n + 1));
+  P.total = P.state + P.work + P.tables + P.staging;
+  return P;
+}
+
+// chunk prefix tables for the current groups and seg_len
 void build_prefix(const wb_batch* b, std::vector<long long>& pre, std::vector<long long>& off) {
   const int ngroups = (int)b->gfirst.size() - 1;
   pre.clear();
@@ -512,17 +507,70 @@ void build_prefix(const wb_batch* b, std::vector<long long>& pre, std::vector<lo
     }
 }
 
-int upload_tables(wb_batch* b) {
+// Regroup the resident boxes (in slot order) into workspace groups, point
+// their workspace views into the shared region and upload every table.
+int rebuild(wb_batch* b) {
+  b->gbox.clear();
+  b->gfirst.assign(1, 0);
+  size_t cur = 0;
+  double* work = b->work_base;
+  b->nbox = 0;
+  for (int i = 0; i < b->cap; ++i) {
+    if (!b->alive[i]) continue;
+    b->nbox = i + 1;
+    const WbGeo& g = b->geo[i];
+    const size_t w = work_doubles(g);
+    if (cur > 0 && cur + w > b->work_cap) {
+      b->gfirst.push_back((int)b->gbox.size());
+      cur = 0;
+    }
+    BoxInfo& bi = b->info[i];
+    double* base = work + cur;
+    size_t k = 0;
+    for (int dd = 0; dd < 3; ++dd)
+      for (int c = 0; c < 8; ++c) {
+        double* f = (c == F_BX + dd) ? nullptr : base + (size_t)g.V * k++;
+        bi.v.Fp[dd][c] = f;
+        bi.v.Fc[dd][c] = f;  // corrector fluxes reuse the predictor flux arrays
+      }
+    for (int dd = 0; dd < 3; ++dd) { bi.v.Eref[dd] = base + (size_t)g.V * k; bi.v.Erefh[dd] = bi.v.Eref[dd]; ++k; }
+    for (int dd = 0; dd < 3; ++dd) { bi.v.Eedge[dd] = base + (size_t)g.V * k; bi.v.Eedgeh[dd] = bi.v.Eedge[dd]; ++k; }
+    for (int dd = 0; dd < 3; ++dd) bi.v.bh[dd] = base + (size_t)g.V * k++;
+    for (int dd = 0; dd < 3; ++dd)
+      for (int c = 0; c < 8; ++c) bi.v.qh[dd][c] = base + (size_t)g.V * k++;
+    cur += w;
+    b->gbox.push_back(i);
+  }
+  if (b->gbox.empty()) b->gfirst.clear();
+  b->gfirst.push_back((int)b->gbox.size());
+  if (b->gfirst.size() >= 2 && b->gfirst[b->gfirst.size() - 2] == b->gfirst.back() && b->gbox.size() > 0)
+    b->gfirst.pop_back();
+  if (b->gbox.empty()) b->gfirst.assign(1, 0);
   std::vector<long long> pre, off;
   build_prefix(b, pre, off);
   if (pre.size() > b->pre_cap) return bfail(b, WB_ERR_INVALID, "prefix table overflow");
-  cudaError_t e = cudaMemcpyAsync(b->d_pre, pre.data(), sizeof(long long) * pre.size(),
-                                  cudaMemcpyHostToDevice, b->stream);
+  cudaStream_t s = b->stream;
+  cudaError_t e = cudaMemcpyAsync(b->d_info, b->info.data(), sizeof(BoxInfo) * b->cap, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !b->gbox.empty())
+    e = cudaMemcpyAsync(b->d_gbox, b->gbox.data(), sizeof(int) * b->gbox.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_pre_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice,
-                        b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  return bcuda(b, e, "tables");
+    e = cudaMemcpyAsync(b->d_gfirst, b->gfirst.data(), sizeof(int) * b->gfirst.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !pre.empty())
+    e = cudaMemcpyAsync(b->d_pre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !off.empty())
+    e = cudaMemcpyAsync(b->d_pre_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bcuda(b, e, "batch tables");
+  b->dirty = false;
+  return WB_OK;
+}
+
+int ensure_built(wb_batch* b) {
+  if (!b->dirty) return WB_OK;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_steps = 0;
+  return rebuild(b);
 }
 
 BatchParams params(const wb_batch* b) {
@@ -548,6 +596,7 @@ cudaError_t enqueue_advance(wb_batch* b, int nsteps) {
   cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * 8, b->stream);
   if (e != cudaSuccess) return e;
   BatchParams p = params(b);
+  if (p.ngroups <= 0) return cudaSuccess;
   int nblocks = b->blocks_per_sm * b->sms;
   void* args[] = {&p, &nsteps};
   cudaLaunchConfig_t cfg = {};
@@ -577,40 +626,8 @@ void drop_graph(wb_batch* b) {
   b->graph_steps = 0;
 }
 
-}  // namespace
-
-extern "C" {
-
-int wb_batch_bytes(int nbox, const wb_desc* descs, size_t work_budget, size_t* bytes) {
-  if (nbox < 1 || !descs || !bytes) return WB_ERR_INVALID;
-  for (int i = 0; i < nbox; ++i) {
-    const wb_desc& d = descs[i];
-    for (int a = 0; a < 3; ++a)
-      if (d.n[a] < 1 || d.patches[a] != 1 || !(d.length[a] > 0.0)) return WB_ERR_INVALID;
-    if (!same_physics(d, descs[0])) return WB_ERR_INVALID;
-  }
-  *bytes = plan(nbox, descs, work_budget > 0 ? work_budget : ((size_t)64 << 30)).total;
-  return WB_OK;
-}
-
-int wb_batch_create(int nbox, const wb_desc* descs, size_t work_budget, void* dev_mem, size_t bytes,
-                    void* stream, wb_batch** out) {
-  if (!out) return WB_ERR_INVALID;
-  *out = nullptr;
-  size_t need = 0;
-  int rc = wb_batch_bytes(nbox, descs, work_budget, &need);
-  if (rc) return rc;
-  if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 255u)) return WB_ERR_INVALID;
-  if (bytes < need) return WB_ERR_NOMEM;
-  const wb_desc& d0 = descs[0];
-  if (!(d0.gamma > 1.0) || d0.gamma > 2.0 || !(d0.cfl > 0.0)) return WB_ERR_INVALID;
-  wb_batch* b = new (std::nothrow) wb_batch();
-  if (!b) return WB_ERR_NOMEM;
-  BatchLayout L = plan(nbox, descs, work_budget > 0 ? work_budget : ((size_t)64 << 30));
-  b->nbox = nbox;
-  b->d.assign(descs, descs + nbox);
-  b->cfl = d0.cfl;
-  WbPhys& p = b->phys;
+WbPhys phys_of(const wb_desc& d0) {
+  WbPhys p;
   p.gamma = d0.gamma;
   p.gm1 = d0.gamma - 1.0;
   p.gm2 = d0.gamma - 2.0;
@@ -627,53 +644,83 @@ int wb_batch_create(int nbox, const wb_desc* descs, size_t work_budget, void* de
   p.minmod = d0.sweby_beta == 1.0 ? 1 : 0;
   p.rho_floor = d0.rho_floor;
   p.p_floor = d0.p_floor;
+  return p;
+}
+
+bool phys_ok(const wb_desc& d) {
+  if (!(d.gamma > 1.0) || d.gamma > 2.0 || !(d.cfl > 0.0)) return false;
+  for (int k = 0; k < 7; ++k)
+    if (!(d.eps[k] >= 0.0) || !(d.eps[k] < 0.5)) return false;
+  return d.sweby_beta >= 1.0 && d.sweby_beta <= 2.0;
+}
+
+void apply_tune_cache(wb_batch* b) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  TuneKey key;
+  for (int i = 0; i < b->cap; ++i)
+    if (b->alive[i]) key.sizes.push_back(b->d[i].n[0] * 1000000 + b->d[i].n[1] * 1000 + b->d[i].n[2]);
+  std::sort(key.sizes.begin(), key.sizes.end());
+  auto it = g_tune_cache.find(key);
+  if (it != g_tune_cache.end()) {
+    b->seg_len = it->second.first;
+    b->blocks_per_sm = std::min(it->second.second, b->max_blocks_per_sm);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int wb_pool_bytes(size_t state_bytes, size_t work_bytes, int max_boxes, int max_n, size_t* bytes) {
+  if (!bytes || max_boxes < 1 || max_n < 1 || state_bytes == 0 || work_bytes == 0) return WB_ERR_INVALID;
+  *bytes = pool_sizes(state_bytes, work_bytes, max_boxes, max_n).total;
+  return WB_OK;
+}
+
+int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes, int max_boxes,
+                   int max_n, void* dev_mem, size_t bytes, void* stream, wb_batch** out) {
+  if (!out || !physics) return WB_ERR_INVALID;
+  *out = nullptr;
+  size_t need = 0;
+  int rc = wb_pool_bytes(state_bytes, work_bytes, max_boxes, max_n, &need);
+  if (rc) return rc;
+  if (!phys_ok(*physics)) return WB_ERR_INVALID;
+  if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 255u)) return WB_ERR_INVALID;
+  if (bytes < need) return WB_ERR_NOMEM;
+  wb_batch* b = new (std::nothrow) wb_batch();
+  if (!b) return WB_ERR_NOMEM;
+  PoolSizes P = pool_sizes(state_bytes, work_bytes, max_boxes, max_n);
+  b->cap = max_boxes;
+  b->alive.assign(max_boxes, 0);
+  b->d.resize(max_boxes);
+  b->geo.resize(max_boxes);
+  b->info.resize(max_boxes);
+  std::memset(b->info.data(), 0, sizeof(BoxInfo) * max_boxes);
+  b->state_off.assign(max_boxes, 0);
+  b->state_cap = P.state / sizeof(double);
+  b->work_cap = P.work / sizeof(double);
+  b->free_[0] = b->state_cap;
+  b->max_n = max_n;
+  b->phys_desc = *physics;
+  b->phys = phys_of(*physics);
+  b->cfl = physics->cfl;
   b->stream = reinterpret_cast<cudaStream_t>(stream);
   b->mem = reinterpret_cast<char*>(dev_mem);
   b->bytes = bytes;
-  b->gbox = L.gbox;
-  b->gfirst = L.gfirst;
-  b->pre_cap = L.pre_cap;
-  double* state = reinterpret_cast<double*>(b->mem);
-  double* work = reinterpret_cast<double*>(b->mem + L.state);
-  char* t = b->mem + L.state + L.work;
-  b->d_info = reinterpret_cast<BoxInfo*>(t); t += al(sizeof(BoxInfo) * nbox);
-  b->d_scal = reinterpret_cast<WbScalars*>(t); t += al(sizeof(WbScalars) * nbox);
-  b->d_steps = reinterpret_cast<int*>(t); t += al(sizeof(int) * nbox);
-  b->d_gbox = reinterpret_cast<int*>(t); t += al(sizeof(int) * nbox);
-  const int ngroups = (int)L.gfirst.size() - 1;
-  b->d_gfirst = reinterpret_cast<int*>(t); t += al(sizeof(int) * (ngroups + 1));
-  b->d_pre = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * L.pre_cap);
-  b->d_pre_off = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * ngroups * BS_COUNT);
+  b->state_base = reinterpret_cast<double*>(b->mem);
+  b->work_base = reinterpret_cast<double*>(b->mem + P.state);
+  char* t = b->mem + P.state + P.work;
+  b->d_info = reinterpret_cast<BoxInfo*>(t); t += al(sizeof(BoxInfo) * max_boxes);
+  b->d_scal = reinterpret_cast<WbScalars*>(t); t += al(sizeof(WbScalars) * max_boxes);
+  b->d_steps = reinterpret_cast<int*>(t); t += al(sizeof(int) * max_boxes);
+  b->d_gbox = reinterpret_cast<int*>(t); t += al(sizeof(int) * max_boxes);
+  b->d_gfirst = reinterpret_cast<int*>(t); t += al(sizeof(int) * (max_boxes + 1));
+  b->pre_cap = P.pre_cap;
+  b->d_pre = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * P.pre_cap);
+  b->d_pre_off = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * (size_t)max_boxes * BS_COUNT);
   b->d_sync = reinterpret_cast<unsigned*>(t); t += al(sizeof(unsigned) * 8);
-  b->staging = reinterpret_cast<double*>(b->mem + L.state + L.work + L.tables);
-  b->info.resize(nbox);
-  b->geo.resize(nbox);
-  for (int i = 0; i < nbox; ++i) {
-    BoxInfo& bi = b->info[i];
-    std::memset(&bi, 0, sizeof(bi));
-    WbGeo g = geo_of(descs[i]);
-    b->geo[i] = g;
-    bi.v.geo = g;
-    for (int a = 0; a < 3; ++a) bi.bc[a] = descs[i].bc[a];
-    double* s = state + L.state_off[i];
-    for (int c = 0; c < 8; ++c) bi.v.q[c] = s + (size_t)c * g.V;
-    for (int c = 0; c < 3; ++c) bi.v.b[c] = s + (size_t)(8 + c) * g.V;
-    double* w = work + L.work_off[i];
-    size_t k = 0;
-    for (int dd = 0; dd < 3; ++dd)
-      for (int c = 0; c < 8; ++c) {
-        double* f = (c == F_BX + dd) ? nullptr : w + (size_t)g.V * k++;
-        bi.v.Fp[dd][c] = f;
-        bi.v.Fc[dd][c] = f;  // corrector fluxes reuse the predictor flux arrays
-      }
-    for (int dd = 0; dd < 3; ++dd) { bi.v.Eref[dd] = w + (size_t)g.V * k; bi.v.Erefh[dd] = bi.v.Eref[dd]; ++k; }
-    for (int dd = 0; dd < 3; ++dd) { bi.v.Eedge[dd] = w + (size_t)g.V * k; bi.v.Eedgeh[dd] = bi.v.Eedge[dd]; ++k; }
-    for (int dd = 0; dd < 3; ++dd) bi.v.bh[dd] = w + (size_t)g.V * k++;
-    for (int dd = 0; dd < 3; ++dd)
-      for (int c = 0; c < 8; ++c) bi.v.qh[dd][c] = w + (size_t)g.V * k++;
-    bi.v.scal = b->d_scal + i;
-  }
-  // launch configuration
+  b->staging = reinterpret_cast<double*>(b->mem + P.state + P.work + P.tables);
+  b->staging_elems = P.staging / sizeof(double);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -688,35 +735,158 @@ int wb_batch_create(int nbox, const wb_desc* descs, size_t work_budget, void* de
   b->graph = nullptr;
   b->graph_steps = 0;
   b->graph_ok = true;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    TuneKey key;
-    for (int i = 0; i < nbox; ++i) key.sizes.push_back(descs[i].n[0] * 1000000 + descs[i].n[1] * 1000 + descs[i].n[2]);
-    std::sort(key.sizes.begin(), key.sizes.end());
-    auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) {
-      b->seg_len = it->second.first;
-      b->blocks_per_sm = std::min(it->second.second, b->max_blocks_per_sm);
-    }
-  }
+  b->dirty = true;
+  b->nbox = 0;
   cudaStream_t s = b->stream;
-  cudaError_t e = cudaMemsetAsync(b->mem, 0xff, L.state + L.work, s);  // NaN poison
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scal, 0, sizeof(WbScalars) * nbox, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_steps, 0, sizeof(int) * nbox, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_info, b->info.data(), sizeof(BoxInfo) * nbox, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_gbox, b->gbox.data(), sizeof(int) * nbox, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_gfirst, b->gfirst.data(), sizeof(int) * (ngroups + 1), cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemsetAsync(b->mem, 0xff, P.state + P.work, s);  // NaN poison
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scal, 0, sizeof(WbScalars) * max_boxes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_steps, 0, sizeof(int) * max_boxes, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     delete b;
     return WB_ERR_CUDA;
   }
-  if (upload_tables(b)) {
+  *out = b;
+  return WB_OK;
+}
+
+int wb_pool_admit(wb_batch* b, const wb_desc* d, int* box) {
+  if (!b || !d || !box) return bfail(b, WB_ERR_INVALID, "null argument");
+  *box = -1;
+  if (!box_ok(*d)) return bfail(b, WB_ERR_INVALID, "a batch box needs patches = 1 and valid sizes");
+  if (!same_physics(*d, b->phys_desc)) return bfail(b, WB_ERR_INVALID, "physics differ from the pool's");
+  if (d->n[0] > b->max_n || d->n[1] > b->max_n || d->n[2] > b->max_n)
+    return bfail(b, WB_ERR_INVALID, "box larger than the pool's max_n");
+  const WbGeo g = geo_of(*d);
+  if (work_doubles(g) > b->work_cap) return bfail(b, WB_ERR_NOMEM, "box workspace exceeds the pool workspace");
+  int slot = -1;
+  for (int i = 0; i < b->cap; ++i)
+    if (!b->alive[i]) { slot = i; break; }
+  if (slot < 0) return bfail(b, WB_ERR_NOMEM, "no free box slot");
+  const size_t need = state_doubles(g);
+  auto it = b->free_.begin();
+  for (; it != b->free_.end(); ++it)
+    if (it->second >= need) break;
+  if (it == b->free_.end()) return bfail(b, WB_ERR_NOMEM, "state region full");
+  const size_t off = it->first, len = it->second;
+  b->free_.erase(it);
+  if (len > need) b->free_[off + need] = len - need;
+  b->alive[slot] = 1;
+  b->d[slot] = *d;
+  b->geo[slot] = g;
+  b->state_off[slot] = off;
+  BoxInfo& bi = b->info[slot];
+  std::memset(&bi, 0, sizeof(bi));
+  bi.v.geo = g;
+  for (int a = 0; a < 3; ++a) bi.bc[a] = d->bc[a];
+  double* st = b->state_base + off;
+  for (int c = 0; c < 8; ++c) bi.v.q[c] = st + (size_t)c * g.V;
+  for (int c = 0; c < 3; ++c) bi.v.b[c] = st + (size_t)(8 + c) * g.V;
+  bi.v.scal = b->d_scal + slot;
+  b->dirty = true;
+  cudaError_t e = cudaMemsetAsync(b->d_scal + slot, 0, sizeof(WbScalars), b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_steps + slot, 0, sizeof(int), b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "admit");
+  *box = slot;
+  return WB_OK;
+}
+
+int wb_pool_release(wb_batch* b, int box) {
+  if (!b || box < 0 || box >= b->cap || !b->alive[box]) return bfail(b, WB_ERR_INVALID, "bad box");
+  size_t off = b->state_off[box], len = state_doubles(b->geo[box]);
+  // coalesce with neighbours
+  auto next = b->free_.lower_bound(off);
+  if (next != b->free_.end() && off + len == next->first) {
+    len += next->second;
+    next = b->free_.erase(next);
+  }
+  if (next != b->free_.begin()) {
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == off) {
+      off = prev->first;
+      len += prev->second;
+      b->free_.erase(prev);
+    }
+  }
+  b->free_[off] = len;
+  b->alive[box] = 0;
+  b->dirty = true;
+  cudaError_t e = cudaMemsetAsync(b->d_steps + box, 0, sizeof(int), b->stream);
+  return bcuda(b, e, "release");
+}
+
+int wb_pool_free_bytes(wb_batch* b, size_t* largest, size_t* total) {
+  if (!b) return WB_ERR_INVALID;
+  size_t lg = 0, tot = 0;
+  for (auto& kv : b->free_) {
+    lg = std::max(lg, kv.second);
+    tot += kv.second;
+  }
+  if (largest) *largest = lg * sizeof(double);
+  if (total) *total = tot * sizeof(double);
+  return WB_OK;
+}
+
+int wb_batch_steps_left(wb_batch* b, int* out) {
+  if (!b || !out) return bfail(b, WB_ERR_INVALID, "null argument");
+  cudaError_t e = cudaMemcpyAsync(out, b->d_steps, sizeof(int) * b->cap, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return bcuda(b, e, "steps left");
+}
+
+int wb_batch_bytes(int nbox, const wb_desc* descs, size_t work_budget, size_t* bytes) {
+  if (nbox < 1 || !descs || !bytes) return WB_ERR_INVALID;
+  size_t st = 0, wmax = 0, wsum = 0;
+  int maxn = 1;
+  for (int i = 0; i < nbox; ++i) {
+    if (!box_ok(descs[i]) || !same_physics(descs[i], descs[0])) return WB_ERR_INVALID;
+    WbGeo g = geo_of(descs[i]);
+    st += state_doubles(g);
+    wmax = std::max(wmax, work_doubles(g));
+    wsum += work_doubles(g);
+    for (int a = 0; a < 3; ++a) maxn = std::max(maxn, descs[i].n[a]);
+  }
+  size_t budget = work_budget > 0 ? work_budget : ((size_t)64 << 30);
+  size_t work = std::max(wmax * sizeof(double), std::min(budget, wsum * sizeof(double)));
+  *bytes = pool_sizes(st * sizeof(double), work, nbox, maxn).total;
+  return WB_OK;
+}
+
+int wb_batch_create(int nbox, const wb_desc* descs, size_t work_budget, void* dev_mem, size_t bytes,
+                    void* stream, wb_batch** out) {
+  if (!out) return WB_ERR_INVALID;
+  *out = nullptr;
+  size_t need = 0;
+  int rc = wb_batch_bytes(nbox, descs, work_budget, &need);
+  if (rc) return rc;
+  if (bytes < need) return WB_ERR_NOMEM;
+  size_t st = 0, wmax = 0, wsum = 0;
+  int maxn = 1;
+  for (int i = 0; i < nbox; ++i) {
+    WbGeo g = geo_of(descs[i]);
+    st += state_doubles(g);
+    wmax = std::max(wmax, work_doubles(g));
+    wsum += work_doubles(g);
+    for (int a = 0; a < 3; ++a) maxn = std::max(maxn, descs[i].n[a]);
+  }
+  size_t budget = work_budget > 0 ? work_budget : ((size_t)64 << 30);
+  size_t work = std::max(wmax * sizeof(double), std::min(budget, wsum * sizeof(double)));
+  wb_batch* b = nullptr;
+  rc = wb_pool_create(&descs[0], st * sizeof(double), work, nbox, maxn, dev_mem, bytes, stream, &b);
+  if (rc) return rc;
+  for (int i = 0; i < nbox; ++i) {
+    int slot = -1;
+    rc = wb_pool_admit(b, &descs[i], &slot);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+  }
+  apply_tune_cache(b);
+  rc = rebuild(b);
+  if (rc) {
     delete b;
-    return WB_ERR_CUDA;
+    return rc;
   }
   *out = b;
   return WB_OK;
@@ -731,7 +901,8 @@ int wb_batch_destroy(wb_batch* b) {
 
 int wb_batch_load(wb_batch* b, int box, const double* U, const double* bx, const double* by,
                   const double* bz, int on_device, int primitive) {
-  if (!b || box < 0 || box >= b->nbox || !U || !bx || !by || !bz) return bfail(b, WB_ERR_INVALID, "bad argument");
+  if (!b || box < 0 || box >= b->cap || !b->alive[box] || !U || !bx || !by || !bz)
+    return bfail(b, WB_ERR_INVALID, "bad argument");
   const wb_desc& d = b->d[box];
   const WbGeo& g = b->geo[box];
   GridMap m;
@@ -771,17 +942,21 @@ int wb_batch_load(wb_batch* b, int box, const double* U, const double* bx, const
   cudaError_t e = cudaMemsetAsync(b->d_scal + box, 0, sizeof(WbScalars), s);
   if (e != cudaSuccess) return bcuda(b, e, "batch load");
   const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_box_rate<<<(unsigned)((nint + 255) / 256), 256, 0, s>>>(b->d_info, b->d_scal, box, b->phys);
+  k_box_rate<<<(unsigned)((nint + 255) / 256), 256, 0, s>>>(bi.v, b->d_scal + box, b->phys);
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
   return bcuda(b, e, "batch load");
 }
 
 int wb_batch_set_steps(wb_batch* b, int box, int nsteps) {
-  if (!b || box < -1 || box >= b->nbox || nsteps < 0) return bfail(b, WB_ERR_INVALID, "bad argument");
+  if (!b || box < -1 || box >= b->cap || nsteps < 0) return bfail(b, WB_ERR_INVALID, "bad argument");
+  if (box >= 0 && !b->alive[box]) return bfail(b, WB_ERR_INVALID, "box not resident");
   std::vector<int> v;
-  int first = box < 0 ? 0 : box, count = box < 0 ? b->nbox : 1;
+  int first = box < 0 ? 0 : box, count = box < 0 ? b->cap : 1;
   v.assign(count, nsteps);
+  if (box < 0)
+    for (int i = 0; i < b->cap; ++i)
+      if (!b->alive[i]) v[i] = 0;
   cudaError_t e = cudaMemcpyAsync(b->d_steps + first, v.data(), sizeof(int) * count, cudaMemcpyHostToDevice,
                                   b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -791,6 +966,8 @@ int wb_batch_set_steps(wb_batch* b, int box, int nsteps) {
 int wb_batch_advance(wb_batch* b, int nsteps, int use_graph) {
   if (!b || nsteps < 0) return bfail(b, WB_ERR_INVALID, "bad argument");
   if (nsteps == 0) return WB_OK;
+  int brc = ensure_built(b);
+  if (brc) return brc;
   cudaError_t e;
   if (use_graph && b->graph_ok) {
     if (!b->graph || b->graph_steps != nsteps) {
@@ -825,7 +1002,7 @@ int wb_batch_advance(wb_batch* b, int nsteps, int use_graph) {
 
 int wb_batch_read(wb_batch* b, int box, double* U, double* bx, double* by, double* bz, double* B,
                   int on_device) {
-  if (!b || box < 0 || box >= b->nbox) return bfail(b, WB_ERR_INVALID, "bad argument");
+  if (!b || box < 0 || box >= b->cap || !b->alive[box]) return bfail(b, WB_ERR_INVALID, "bad argument");
   const wb_desc& d = b->d[box];
   const WbGeo& g = b->geo[box];
   GridMap m;
@@ -861,7 +1038,7 @@ int wb_batch_read(wb_batch* b, int box, double* U, double* bx, double* by, doubl
 }
 
 int wb_batch_counters(wb_batch* b, int box, wb_counters_t* c) {
-  if (!b || !c || box < 0 || box >= b->nbox) return bfail(b, WB_ERR_INVALID, "bad argument");
+  if (!b || !c || box < 0 || box >= b->cap) return bfail(b, WB_ERR_INVALID, "bad argument");
   WbScalars sc;
   cudaError_t e = cudaMemcpyAsync(&sc, b->d_scal + box, sizeof(sc), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -880,7 +1057,8 @@ int wb_batch_config(wb_batch* b, int seg_len, int blocks_per_sm, long long barri
   if (blocks_per_sm > 0) b->blocks_per_sm = std::min(blocks_per_sm, b->max_blocks_per_sm);
   if (barrier_budget_cycles > 0) b->budget = barrier_budget_cycles;
   drop_graph(b);
-  return upload_tables(b);
+  b->dirty = true;
+  return ensure_built(b);
 }
 
 int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* groups) {
@@ -888,6 +1066,11 @@ int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* grou
   if (seg_len) *seg_len = b->seg_len;
   if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
   if (groups) *groups = (int)b->gfirst.size() - 1;
+  if (b->dirty) {
+    int rc = ensure_built(b);
+    if (rc) return rc;
+    if (groups) *groups = (int)b->gfirst.size() - 1;
+  }
   return WB_OK;
 }
 
@@ -897,6 +1080,8 @@ int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* grou
 // simulation (results do not depend on the configuration).
 int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms) {
   if (!b || trial_steps < 1) return bfail(b, WB_ERR_INVALID, "bad argument");
+  int brc = ensure_built(b);
+  if (brc) return brc;
   const int segs[] = {16, 24, 32, 48, 64, 96};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -934,7 +1119,8 @@ int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneKey key;
-    for (int i = 0; i < b->nbox; ++i) key.sizes.push_back(b->d[i].n[0] * 1000000 + b->d[i].n[1] * 1000 + b->d[i].n[2]);
+    for (int i = 0; i < b->cap; ++i)
+      if (b->alive[i]) key.sizes.push_back(b->d[i].n[0] * 1000000 + b->d[i].n[1] * 1000 + b->d[i].n[2]);
     std::sort(key.sizes.begin(), key.sizes.end());
     g_tune_cache[key] = {best_seg, best_b};
   }

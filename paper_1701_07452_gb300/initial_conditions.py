@@ -21,7 +21,7 @@ import math
 
 import numpy as np
 
-__all__ = ["random_box", "turbulence_box", "mode_table", "curl_faces", "State"]
+__all__ = ["random_box", "turbulence_box", "turbulence_box_device", "mode_table", "curl_faces", "State"]
 
 
 class State(dict):
@@ -137,6 +137,72 @@ def turbulence_box(n, seed, gamma=5.0 / 3.0, beta=100.0, mach=1.0, db_frac=0.1):
     bx, by, bz = curl_faces(Ax, Ay, Az, 1.0 / nx, 1.0 / ny, 1.0 / nz)
     bx = bx + B0
     W = np.empty((5, nz, ny, nx))
+    W[0] = rho0
+    W[1], W[2], W[3] = vx, vy, vz
+    W[4] = p0
+    return State(W=W, bx=bx, by=by, bz=bz, length=(1.0, 1.0, 1.0))
+
+
+def _eval_modes_torch(k, a, ph, n, offsets, device):
+    """_eval_modes with torch on a device (large grids); returns tensors."""
+    import torch
+    nx, ny, nz = n
+    kmax = int(np.abs(k).max())
+    nk = 2 * kmax + 1
+    kr = torch.arange(-kmax, kmax + 1, dtype=torch.float64, device=device)
+    def basis(m, off):
+        x = (torch.arange(m, dtype=torch.float64, device=device) + off) / m
+        return torch.exp(2j * math.pi * torch.outer(x, kr).to(torch.complex128))
+    ex, ey, ez = basis(nx, offsets[0]), basis(ny, offsets[1]), basis(nz, offsets[2])
+    idx = k.astype(int) + kmax
+    out = []
+    for c in range(a.shape[1]):
+        C = np.zeros((nk, nk, nk), dtype=np.complex128)
+        np.add.at(C, (idx[:, 2], idx[:, 1], idx[:, 0]), a[:, c] * np.exp(1j * ph))
+        Ct = torch.from_numpy(C).to(device)
+        T1 = Ct @ ex.T                                  # [kz, ky, x]
+        T2 = torch.einsum("yb,zbx->zyx", ey, T1)         # [kz, y, x]
+        f = (ez @ T2.reshape(nk, ny * nx)).real.reshape(nz, ny, nx).contiguous()
+        out.append(f)
+    return out
+
+
+def _curl_faces_torch(Ax, Ay, Az, dx, dy, dz):
+    import torch
+    bx = (torch.roll(Az, -1, 1) - Az) / dy - (torch.roll(Ay, -1, 0) - Ay) / dz
+    by = (torch.roll(Ax, -1, 0) - Ax) / dz - (torch.roll(Az, -1, 2) - Az) / dx
+    bz = (torch.roll(Ay, -1, 2) - Ay) / dx - (torch.roll(Ax, -1, 1) - Ax) / dy
+    bx = torch.cat([bx, bx[:, :, :1]], dim=2).contiguous()
+    by = torch.cat([by, by[:, :1, :]], dim=1).contiguous()
+    bz = torch.cat([bz, bz[:1, :, :]], dim=0).contiguous()
+    return bx, by, bz
+
+
+def turbulence_box_device(n, seed, device, gamma=5.0 / 3.0, beta=100.0, mach=1.0, db_frac=0.1):
+    """turbulence_box evaluated with torch on ``device`` (same mode table and
+    scaling; values agree with the NumPy version to rounding).  Returns a
+    State whose arrays are device tensors."""
+    import torch
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    nx, ny, nz = n
+    rho0, p0 = 1.0, 1.0
+    cs = math.sqrt(gamma * p0 / rho0)
+    kv, av, pv = mode_table(seed, 1, 8, slope=-2.0)
+    vscale = mach * cs / math.sqrt(0.5 * float(np.sum(av * av)))
+    vx, vy, vz = _eval_modes_torch(kv, av * vscale, pv, n, (0.5, 0.5, 0.5), device)
+    B0 = math.sqrt(2.0 * p0 / beta)
+    kb, ab, pb = mode_table(seed + 7919, 1, 4, slope=-2.0)
+    kn = np.linalg.norm(kb, axis=1)
+    brms = math.sqrt(0.5 * float(np.sum((2.0 * math.pi * kn[:, None] * ab) ** 2)))
+    ab = ab * (db_frac * B0 / brms)
+    Ax = _eval_modes_torch(kb, ab[:, 0:1], pb, n, (0.5, 0.0, 0.0), device)[0]
+    Ay = _eval_modes_torch(kb, ab[:, 1:2], pb, n, (0.0, 0.5, 0.0), device)[0]
+    Az = _eval_modes_torch(kb, ab[:, 2:3], pb, n, (0.0, 0.0, 0.5), device)[0]
+    bx, by, bz = _curl_faces_torch(Ax, Ay, Az, 1.0 / nx, 1.0 / ny, 1.0 / nz)
+    del Ax, Ay, Az
+    bx = bx + B0
+    W = torch.empty((5, nz, ny, nx), dtype=torch.float64, device=device)
     W[0] = rho0
     W[1], W[2], W[3] = vx, vy, vz
     W[4] = p0

@@ -1,0 +1,111 @@
+"""Continuous-batching request loop over the GPU pool (wb_pool_* C ABI).
+
+Independent MHD runs (grid size, step count, initial data) arrive over time.
+Each loop iteration admits the queued runs whose state fits the HBM budget of
+the pool (first come first served, later runs may backfill when an earlier
+one does not fit), loads their initial data, advances every resident run by
+up to ``tick_steps`` steps in one shared persistent launch, and reads back and
+releases the runs that finished.  Completion latency is measured from a run's
+arrival to the end of the tick in which its last step ran.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import binding
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the stream
+    n: tuple                # zones per axis
+    steps: int
+    state: dict             # primitive W and faces (initial_conditions format)
+    length: tuple = (1.0, 1.0, 1.0)
+
+
+@dataclasses.dataclass
+class Record:
+    rid: int
+    n: tuple
+    steps: int
+    arrival: float
+    admitted: float = float("nan")
+    finished: float = float("nan")
+    result: tuple = None
+
+
+class Server:
+    def __init__(self, state_bytes, work_bytes, max_boxes=512, max_n=256, tick_steps=4,
+                 use_graph=True, keep_results=False, **physics):
+        self.pool = binding.Pool(state_bytes, work_bytes, max_boxes=max_boxes, max_n=max_n, **physics)
+        self.tick_steps = int(tick_steps)
+        self.use_graph = use_graph
+        self.keep_results = keep_results
+        self.ticks = 0
+
+    def run(self, requests, clock=time.perf_counter, sleep=time.sleep):
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        queue = []
+        resident = {}   # slot -> (request, record)
+        records = {}
+        t0 = clock()
+        while pending or queue or resident:
+            now = clock() - t0
+            while pending and pending[0].arrival <= now:
+                r = pending.popleft()
+                queue.append(r)
+                records[r.rid] = Record(r.rid, tuple(r.n), r.steps, r.arrival)
+            # admission by HBM budget, FIFO with backfill
+            still = []
+            for r in queue:
+                slot = self.pool.admit(r.n, r.length)
+                if slot is None:
+                    still.append(r)
+                    continue
+                st = r.state
+                self.pool.load(slot, st["W"], st["bx"], st["by"], st["bz"], primitive=True)
+                self.pool.set_steps(slot, r.steps)
+                records[r.rid].admitted = clock() - t0
+                resident[slot] = r
+            queue = still
+            if not resident:
+                if pending:
+                    sleep(max(0.0, min(0.05, pending[0].arrival - (clock() - t0))))
+                continue
+            self.pool.advance(self.tick_steps, use_graph=self.use_graph)
+            self.ticks += 1
+            left = self.pool.steps_left()
+            done_at = clock() - t0
+            for slot in [s for s in resident if left[s] == 0]:
+                r = resident.pop(slot)
+                rec = records[r.rid]
+                rec.finished = done_at
+                if self.keep_results:
+                    rec.result = self.pool.read(slot)
+                c = self.pool.counters(slot)
+                if c["unphysical"]:
+                    raise binding.WombatError(binding.WB_ERR_UNPHYSICAL, f"run {r.rid} became unphysical")
+                self.pool.release(slot)
+        return [records[k] for k in sorted(records)]
+
+
+def summarize(records):
+    lat = np.array([r.finished - r.arrival for r in records])
+    wall = max(r.finished for r in records) - min(r.arrival for r in records)
+    cells = float(sum(np.prod(r.n) * r.steps for r in records))
+    return {
+        "requests": len(records),
+        "p50_s": float(np.percentile(lat, 50)),
+        "p99_s": float(np.percentile(lat, 99)),
+        "mean_s": float(lat.mean()),
+        "wall_s": float(wall),
+        "cell_updates": cells,
+        "cell_updates_per_s": cells / wall,
+        "solves_per_s": len(records) / wall,
+    }

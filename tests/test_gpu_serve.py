@@ -1,0 +1,64 @@
+"""Serving pattern on the GPU: runs that arrive while others are resident are
+admitted as memory frees up, share launches, and each result is bit-identical
+to the same run served alone."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_07452_gb300 import binding, serve
+    binding.lib()
+    return binding, serve
+
+
+def requests():
+    from paper_1701_07452_gb300 import serve
+    from paper_1701_07452_gb300.initial_conditions import random_box, turbulence_box
+    spec = [((12, 12, 12), 7, 0.00), ((16, 12, 10), 5, 0.00), ((10, 10, 10), 9, 0.02),
+            ((14, 14, 14), 4, 0.04), ((8, 16, 12), 6, 0.05)]
+    out = []
+    for i, (n, steps, t) in enumerate(spec):
+        st = turbulence_box(n, seed=50 + i) if i % 2 else random_box(n, seed=60 + i)
+        out.append(serve.Request(i, t, n, steps, st, st["length"]))
+    return out
+
+
+def test_served_results_equal_alone_results(mods):
+    binding, serve = mods
+    reqs = requests()
+    # the state budget holds about two of these boxes at a time
+    per = max(11 * 8 * (n[0] + 10) * (n[1] + 10) * (n[2] + 10) for n in [r.n for r in reqs])
+    srv = serve.Server(state_bytes=2 * per + 4096, work_bytes=64 << 20, max_boxes=8, max_n=32,
+                       tick_steps=2, keep_results=True)
+    recs = srv.run(reqs)
+    assert len(recs) == len(reqs)
+    assert any(r.admitted > r.arrival + 1e-6 for r in recs), "budget never delayed an admission"
+    for r, rec in zip(reqs, recs):
+        alone = serve.Server(state_bytes=per + 4096, work_bytes=64 << 20, max_boxes=2, max_n=32,
+                             tick_steps=3, keep_results=True)
+        (arec,) = alone.run([serve.Request(r.rid, 0.0, r.n, r.steps, r.state, r.length)])
+        for a, b in zip(arec.result, rec.result):
+            assert np.array_equal(a, b), r.rid
+
+
+def test_pool_admission_accounting(mods):
+    binding, _ = mods
+    per = 11 * 8 * 20 ** 3
+    pool = binding.Pool(state_bytes=3 * per, work_bytes=32 << 20, max_boxes=4, max_n=16)
+    a = pool.admit((10, 10, 10))
+    b = pool.admit((10, 10, 10))
+    c = pool.admit((10, 10, 10))
+    assert None not in (a, b, c)
+    assert pool.admit((10, 10, 10)) is None          # state region full
+    pool.release(b)
+    assert pool.free_bytes()[0] >= per
+    d = pool.admit((10, 10, 10))
+    assert d is not None
+    with pytest.raises(binding.WombatError):
+        pool.admit((40, 40, 40))                      # beyond max_n

@@ -1,0 +1,120 @@
+"""Host-side logic of the serving loop (admission by HBM budget with backfill,
+completion detection, latency bookkeeping) against a fake pool on the CPU."""
+import numpy as np
+
+from paper_1701_07452_gb300 import serve
+
+
+class FakePool:
+    """Stands in for binding.Pool: a byte budget, slots and step counters."""
+
+    def __init__(self, budget):
+        self.budget = budget
+        self.used = {}
+        self.left = {}
+        self.loaded = set()
+        self.max_resident = 0
+        self.advances = 0
+
+    @staticmethod
+    def size(n):
+        return int(np.prod(n))
+
+    def admit(self, n, length=None):
+        need = self.size(n)
+        if sum(self.used.values()) + need > self.budget:
+            return None
+        slot = 0
+        while slot in self.used:
+            slot += 1
+        self.used[slot] = need
+        self.left[slot] = 0
+        self.max_resident = max(self.max_resident, len(self.used))
+        return slot
+
+    def load(self, slot, *a, **k):
+        self.loaded.add(slot)
+
+    def set_steps(self, slot, n):
+        self.left[slot] = n
+
+    def advance(self, k, use_graph=True):
+        self.advances += 1
+        for s in self.left:
+            self.left[s] = max(0, self.left[s] - k)
+
+    def steps_left(self):
+        out = [0] * 64
+        for s, v in self.left.items():
+            out[s] = v
+        return out
+
+    def read(self, slot):
+        return ("result", slot)
+
+    def counters(self, slot):
+        return {"unphysical": 0}
+
+    def release(self, slot):
+        del self.used[slot]
+        del self.left[slot]
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 0.001
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 0.0)
+
+
+def make_server(budget, tick):
+    srv = serve.Server.__new__(serve.Server)
+    srv.pool = FakePool(budget)
+    srv.tick_steps = tick
+    srv.use_graph = True
+    srv.keep_results = True
+    srv.ticks = 0
+    return srv
+
+
+def test_every_request_completes_within_budget_with_backfill():
+    empty = {"W": None, "bx": None, "by": None, "bz": None}
+    reqs = [serve.Request(i, 0.01 * i, (8, 8, 8) if i % 3 else (16, 16, 16), 5 + i, empty) for i in range(12)]
+    srv = make_server(budget=16 ** 3 + 8 ** 3, tick=2)
+    clk = FakeClock()
+    recs = srv.run(reqs, clock=clk, sleep=clk.sleep)
+    assert len(recs) == 12
+    for r in recs:
+        assert r.arrival <= r.admitted <= r.finished
+        assert r.result is not None
+    # never more state resident than the budget allows
+    assert srv.pool.max_resident <= 2
+    summ = serve.summarize(recs)
+    assert summ["requests"] == 12 and summ["p99_s"] >= summ["p50_s"] > 0
+
+
+def test_small_run_backfills_behind_a_big_one():
+    empty = {"W": None, "bx": None, "by": None, "bz": None}
+    reqs = [serve.Request(0, 0.0, (16, 16, 16), 10, empty),
+            serve.Request(1, 0.0001, (16, 16, 16), 2, empty),
+            serve.Request(2, 0.0002, (8, 8, 8), 2, empty)]
+    srv = make_server(budget=16 ** 3 + 8 ** 3, tick=2)
+    clk = FakeClock()
+    recs = srv.run(reqs, clock=clk, sleep=clk.sleep)
+    assert recs[2].admitted < recs[1].admitted      # later, smaller run admitted first
+    assert recs[1].admitted >= recs[0].finished     # the big one waited for memory
+
+
+def test_ticks_cover_the_longest_run():
+    empty = {"W": None, "bx": None, "by": None, "bz": None}
+    reqs = [serve.Request(0, 0.0, (8, 8, 8), 7, empty), serve.Request(1, 0.0, (8, 8, 8), 3, empty)]
+    srv = make_server(budget=10 ** 6, tick=2)
+    clk = FakeClock()
+    recs = srv.run(reqs, clock=clk, sleep=clk.sleep)
+    assert srv.ticks == 4            # ceil(7 / 2)
+    assert recs[1].finished < recs[0].finished
