@@ -42,10 +42,14 @@ METRIC = "FP64 cell-updates/s"
 UNIT = "cell-updates/s"
 N_BOX = 256
 SEED = 2
-# FP64 flops the MHDTVD sweep performs per interface (add/sub/mul = 1, fma = 2,
-# div/sqrt/rsqrt = 1), counted from the face formulation of the sweep kernel
-# (see the kernel-level summary under profiles/).
-FLOPS_PER_FACE = 560.0
+# FP64 flops (DFMA = 2, DMUL = DADD = 1) the MHDTVD sweep executes per interface
+# system it computes, from the ncu FP64 instruction counters of k_sweep on the
+# 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full_v3.md): 594 M flops
+# over 9604 pencils x 107 interface systems.
+FLOPS_PER_FACE = 578.0
+# FP64 issue rate of one GB300 SM: 2 DFMA per clock (measured with the DFMA
+# probe: 1196 GFLOP/s at 1995 MHz on 152 SMs), i.e. 4 flops per clock per SM.
+FP64_FLOPS_PER_CLK_PER_SM = 4.0
 
 
 def sweep_faces_per_step(n):
@@ -402,7 +406,10 @@ def main():
         per_launch_ms = sweep_ms / max(sweep_launches, 1)
         faces_per_launch = sweep_faces_per_step(n) / 6.0
         achieved = FLOPS_PER_FACE * faces_per_launch / (per_launch_ms * 1e-3) / 1e12
-        peak = fp64_peak / 1e12
+        clk_summary = clk.summary()
+        sm_mhz = clk_summary["sm_mhz"] or 2070.0
+        props = torch.cuda.get_device_properties(dev)
+        peak = props.multi_processor_count * FP64_FLOPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
         launches_per_step = 26
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -416,11 +423,12 @@ def main():
                     "steps": args.e2e_steps},
             "roofline": {"bound": "alu", "kernel": "k_sweep (MHDTVD flux)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": "FP64 DFMA probe run in this process",
+                         "peak_source": "SMs x 2 DFMA/clk x 2 flops x median SM clock under load; "
+                                        "DFMA probe in this process: %.3f TFLOP/s" % (fp64_peak / 1e12),
                          "sweep_ms_per_launch": per_launch_ms,
                          "sweep_share_of_step": sweep_ms / ms},
             "cpu_baseline": cpu,
-            "clocks": clk.summary(),
+            "clocks": clk_summary,
             "gpu_launches": launches_per_step * args.steps,
         }
         print(json.dumps(line), flush=True)

@@ -52,7 +52,6 @@ struct WbScalars {
   long long timeouts;
 };
 
-__device__ __forceinline__ double wb_sgn(double x) { return x >= 0.0 ? 1.0 : -1.0; }
 
 // magnitude comparison on the IEEE bit pattern (integer pipe): |a| < |b|
 __device__ __forceinline__ bool wb_abs_less(double a, double b) {
@@ -67,16 +66,6 @@ __device__ __forceinline__ double wb_minmod(double a, double b) {
   long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
   double r = wb_abs_less(a, b) ? a : b;
   return ((ia ^ ib) >= 0) ? r : 0.0;
-}
-
-// SWEBY limiter g = SIGN(a) max(0, min(beta|a|, s b), min(|a|, beta s b)), s = SIGN(a)
-__device__ __forceinline__ double wb_sweby(double a, double b, double beta, int minmod) {
-  if (minmod) return wb_minmod(a, b);
-  double s = wb_sgn(a);
-  double aa = fabs(a);
-  double m1 = fmin(beta * aa, s * b);
-  double m2 = fmin(aa, beta * s * b);
-  return s * fmax(0.0, fmax(m1, m2));
 }
 
 // Reciprocal and reciprocal square root for FP64 without the library
@@ -102,6 +91,46 @@ __device__ __forceinline__ double wb_rsqrt(double x) {
   double e = fma(-h, y, 1.0);
   double p = fma(0.375, e, 0.5);
   return fma(y * e, p, y);
+}
+
+// Comparisons on the IEEE bit patterns (integer pipe; the FP64 pipe is the
+// scarce unit on this GPU).
+// x > 0, finite (false for +inf and NaN)
+__device__ __forceinline__ bool wb_pos(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7ff0000000000000LL;
+}
+// x < 0 (false for -0.0 and NaN)
+__device__ __forceinline__ bool wb_neg(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 && (b & 0x7fffffffffffffffLL) != 0 && (b & 0x7fffffffffffffffLL) <= 0x7ff0000000000000LL;
+}
+// x == 0 (either sign)
+__device__ __forceinline__ bool wb_zero(double x) {
+  return (__double_as_longlong(x) << 1) == 0;
+}
+// a <= b for a, b >= 0 (non-negative, non-NaN operands)
+__device__ __forceinline__ bool wb_le_nonneg(double a, double b) {
+  return __double_as_longlong(a) <= __double_as_longlong(b);
+}
+// min(max(x, 0), 1)
+__device__ __forceinline__ double wb_clamp01(double x) {
+  const long long b = __double_as_longlong(x);
+  if (b <= 0) return 0.0;                                 // negative or zero
+  return b > 0x3ff0000000000000LL ? 1.0 : x;              // above 1 (or NaN -> 1)
+}
+
+// +1 for x >= 0 (including -0.0), -1 for x < 0
+__device__ __forceinline__ double wb_sgn(double x) { return wb_neg(x) ? -1.0 : 1.0; }
+
+// SWEBY limiter g = SIGN(a) max(0, min(beta|a|, s b), min(|a|, beta s b)), s = SIGN(a)
+__device__ __forceinline__ double wb_sweby(double a, double b, double beta, int minmod) {
+  if (minmod) return wb_minmod(a, b);
+  double s = wb_sgn(a);
+  double aa = fabs(a);
+  double m1 = fmin(beta * aa, s * b);
+  double m2 = fmin(aa, beta * s * b);
+  return s * fmax(0.0, fmax(m1, m2));
 }
 
 // |x| with the sign of s (integer pipe)

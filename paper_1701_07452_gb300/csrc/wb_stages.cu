@@ -73,16 +73,16 @@ __global__ void k_ct(StageArgs A, bool fin, Boxes3 B) {
   if (wbu::in_box(B.b[2], i, j, k)) wbu::ct<2>(A.v, qo, wo, fin, dt, i, j, k);
 }
 
-// Steps 5 and 7: the three transverse-flux preconditioned states.
+// Steps 5 and 7: the three transverse-flux preconditioned states, all
+// directions of a zone in one thread.
 __global__ void k_transverse(StageArgs A, Boxes3 B) {
   const double dt = A.v.scal->dt;
   if (!(dt > 0.0)) return;
   int i, j, k;
   if (!box_index(B.u, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
-  const long long qo = blockIdx.y * A.slot_q, wo = blockIdx.y * A.slot_w;
-  if (wbu::in_box(B.b[0], i, j, k)) wbu::transverse<0>(A.v, qo, wo, dt, i, j, k);
-  if (wbu::in_box(B.b[1], i, j, k)) wbu::transverse<1>(A.v, qo, wo, dt, i, j, k);
-  if (wbu::in_box(B.b[2], i, j, k)) wbu::transverse<2>(A.v, qo, wo, dt, i, j, k);
+  const int mask = (wbu::in_box(B.b[0], i, j, k) ? 1 : 0) | (wbu::in_box(B.b[1], i, j, k) ? 2 : 0) |
+                   (wbu::in_box(B.b[2], i, j, k) ? 4 : 0);
+  if (mask) wbu::transverse_set(A.v, blockIdx.y * A.slot_q, blockIdx.y * A.slot_w, dt, mask, i, j, k);
 }
 
 // Step 8: half-step reference EMF.

@@ -32,8 +32,14 @@ namespace {
 
 using wbu::kBlock;
 
+// resident blocks per SM the sweep is compiled for (registers per thread
+// follow from it)
+#ifndef WB_SWEEP_MIN_BLOCKS
+#define WB_SWEEP_MIN_BLOCKS 4
+#endif
+
 template <int D>
-__global__ void __launch_bounds__(wbu::kBlock, 4) k_sweep(SweepArgs A) {
+__global__ void __launch_bounds__(wbu::kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs A) {
   constexpr int U = (D == 0) ? 1 : 0;  // fastest transverse axis of the thread map
   constexpr int W = (D == 2) ? 1 : 2;
   __shared__ double srec[2][wbu::R_WORDS][wbu::kBlock];

@@ -116,7 +116,7 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
   const double v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
   const double bt2s = bt1 * bt1 + bt2 * bt2;
   const double a2 = P.gm1 * (H - 0.5 * v2 - (b2 + bt2s) * irho) - P.gm2 * X;
-  if (!(a2 > 0.0)) return false;
+  if (!wb_pos(a2)) return false;
   const double isrho = wb_rsqrt(rho);
   const double srho = rho * isrho;
   const double ca2 = b2 * irho, ct2 = bt2s * irho;
@@ -124,7 +124,7 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
   const double disc = dac * dac + ct2 * (ct2 + 2.0 * (a2 + ca2));
   const double sum = a2 + ca2 + ct2;
   double rsd = 0.0, sd = 0.0;
-  if (disc > 0.0) {
+  if (wb_pos(disc)) {
     rsd = wb_rsqrt(disc);
     sd = disc * rsd;
   }
@@ -136,8 +136,8 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
   const double cf = cf2 * icf;
   const double cs = a * ca * icf;  // c_f c_s = a c_a
   double af, as;
-  if (sd <= 1e-12 * sum) {
-    const bool fast = a2 >= ca2;
+  if (wb_le_nonneg(sd, 1e-12 * sum)) {
+    const bool fast = wb_le_nonneg(ca2, a2);
     af = fast ? 1.0 : 0.0;
     as = fast ? 0.0 : 1.0;
   } else {
@@ -145,7 +145,7 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
     // two needs a quotient
     const double t1 = ca2 + ct2 - a2;
     const double t2 = a2 - ca2 + ct2;
-    const bool n1 = t1 < 0.0, n2 = t2 < 0.0;
+    const bool n1 = wb_neg(t1), n2 = wb_neg(t2);
     double qd = 0.0;
     if (n1 || n2) {
       const double num = n1 ? 2.0 * a2 * ct2 : 2.0 * ca2 * ct2;
@@ -154,13 +154,13 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
     }
     const double cf2_a2 = n1 ? qd : 0.5 * (t1 + sd);
     const double cf2_ca2 = n2 ? qd : 0.5 * (t2 + sd);
-    const double af2 = fmin(fmax(a2 * cf2_ca2 * (icf * icf) * rsd, 0.0), 1.0);
-    const double as2 = fmin(fmax(cf2_a2 * rsd, 0.0), 1.0);
-    af = (af2 > 0.0) ? af2 * wb_rsqrt(af2) : 0.0;
-    as = (as2 > 0.0) ? as2 * wb_rsqrt(as2) : 0.0;
+    const double af2 = wb_clamp01(a2 * cf2_ca2 * (icf * icf) * rsd);
+    const double as2 = wb_clamp01(cf2_a2 * rsd);
+    af = wb_zero(af2) ? 0.0 : af2 * wb_rsqrt(af2);
+    as = wb_zero(as2) ? 0.0 : as2 * wb_rsqrt(as2);
   }
   double b1n, b2n;
-  if (bt2s <= 1e-24 * (rho * a2 + b2 + bt2s)) {
+  if (wb_le_nonneg(bt2s, 1e-24 * (rho * a2 + b2 + bt2s))) {
     b1n = b2n = 0.70710678118654752440;
   } else {
     const double ib = wb_rsqrt(bt2s);
@@ -197,11 +197,12 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
   al[1] = 0.5 * (dvp + Aa);
   al[5] = 0.5 * (dvp - Aa);
   al[3] = drho - dp * (2.0 * i2a2);
-  // eigenvalues a_1..a_7 (Sec. 3)
-  const double lam[7] = {vn - cf, vn - ca, vn - cs, vn, vn + cs, vn + ca, vn + cf};
+  // nu_k = (dt/dx) a_k for the eigenvalues a_1..a_7 (Sec. 3)
+  const double tvn = dtdx * vn, tcf = dtdx * cf, tca = dtdx * ca, tcs = dtdx * cs;
+  const double nuk[7] = {tvn - tcf, tvn - tca, tvn - tcs, tvn, tvn + tcs, tvn + tca, tvn + tcf};
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    const double nu = dtdx * lam[k];
+    const double nu = nuk[k];
     f[R_AL + k] = al[k];
     f[R_NU + k] = nu;
     gt[k] = (Qk(nu, k, P) - nu * nu) * (0.5 * al[k]);
@@ -221,7 +222,7 @@ __device__ __forceinline__ double beta_k(double al, double nu, double gi, double
                                          const WbPhys& P) {
   const double w = fma(nu, al, gi1 - gi);             // (nu + gamma) alpha
   double qa;
-  if (al == 0.0) {
+  if (wb_zero(al)) {
     qa = 0.0;                                           // gamma = 0, Q(nu) 0
   } else if (!wb_abs_less(w, P.two_eps[k] * al)) {
     qa = wb_copysign_abs(w, al);                        // |nu + gamma| >= 2 eps
@@ -365,6 +366,14 @@ __device__ __forceinline__ void eref(const WbView& v, long long qo, long long wo
   v.Eref[2][w] = vy * bx - vx * by;
 }
 
+// value upwind of the mass flux m: from the minus-side zone if m > 0, the
+// plus-side zone if m < 0, their mean if m = 0 (rare: a branch, not a select)
+__device__ __forceinline__ double upwind(double m, double xm, double x0) {
+  double d = wb_neg(m) ? x0 : xm;
+  if (wb_zero(m)) d = 0.5 * (xm + x0);
+  return d;
+}
+
 // Steps 3 and 9: upwinded corner EMF (GS05 "CT-contact" form).  Edge along
 // axis C at the low faces of axes a = C+1 and b = C+2 (cyclic).  Face EMFs
 // E^a = -F_a[B_b], E^b = +F_b[B_a]; the corner value is their average plus
@@ -388,16 +397,12 @@ __device__ __forceinline__ void edge(const WbView& v, long long wo, bool corr, i
   const double ma_0 = Fa[F_RHO][o], ma_m = Fa[F_RHO][o - sb];
   const double mb_0 = Fb[F_RHO][o], mb_m = Fb[F_RHO][o - sa];
   const double R00 = Er[o], Rm0 = Er[o - sa], R0m = Er[o - sb], Rmm = Er[o - sa - sb];
-  const double db_hi_m = Rm0 - Eb_m, db_hi_0 = R00 - Eb_0;
-  const double db_hi = ma_0 > 0.0 ? db_hi_m : (ma_0 < 0.0 ? db_hi_0 : 0.5 * (db_hi_m + db_hi_0));
-  const double db_lo_m = Eb_m - Rmm, db_lo_0 = Eb_0 - R0m;
-  const double db_lo = ma_m > 0.0 ? db_lo_m : (ma_m < 0.0 ? db_lo_0 : 0.5 * (db_lo_m + db_lo_0));
-  const double da_hi_m = R0m - Ea_m, da_hi_0 = R00 - Ea_0;
-  const double da_hi = mb_0 > 0.0 ? da_hi_m : (mb_0 < 0.0 ? da_hi_0 : 0.5 * (da_hi_m + da_hi_0));
-  const double da_lo_m = Ea_m - Rmm, da_lo_0 = Ea_0 - Rm0;
-  const double da_lo = mb_m > 0.0 ? da_lo_m : (mb_m < 0.0 ? da_lo_0 : 0.5 * (da_lo_m + da_lo_0));
+  const double db_hi = upwind(ma_0, Rm0 - Eb_m, R00 - Eb_0);
+  const double db_lo = upwind(ma_m, Eb_m - Rmm, Eb_0 - R0m);
+  const double da_hi = upwind(mb_0, R0m - Ea_m, R00 - Ea_0);
+  const double da_lo = upwind(mb_m, Ea_m - Rmm, Ea_0 - Rm0);
   double* out = corr ? v.Eedgeh[C] : v.Eedge[C];
-  out[o] = 0.25 * (Ea_0 + Ea_m + Eb_0 + Eb_m) + 0.25 * (db_lo - db_hi) + 0.25 * (da_lo - da_hi);
+  out[o] = 0.25 * ((Ea_0 + Ea_m) + (Eb_0 + Eb_m) + (db_lo - db_hi) + (da_lo - da_hi));
 }
 
 // Steps 4 and 11: b_out = b_in - tau curl E on the faces normal to D.
@@ -420,12 +425,6 @@ __device__ __forceinline__ void ct(const WbView& v, long long qo, long long wo, 
   else v.bh[D][w] = bn;
 }
 
-__device__ __forceinline__ double minmod_src(double x, double y) {
-  if (x > 0.0 && y > 0.0) return fmin(x, y);
-  if (x < 0.0 && y < 0.0) return fmax(x, y);
-  return 0.0;
-}
-
 // Steps 5 and 7: q^{n+1/2}_D = q^n - dt/2 (transverse flux divergence)
 // + dt/2 S_D, zone B_D := mean of b_D^{n+1/2}, with the GS08-type div B
 // source S_D built from face differences of b^n and minmod pairings.
@@ -446,8 +445,8 @@ __device__ __forceinline__ void transverse(const WbView& v, long long qo, long l
     B[e] = v.q[F_BX + e][q];
     db[e] = (v.b[e][q + s[e]] - v.b[e][q]) * g.idx[e];
   }
-  const double m2 = minmod_src(db[D], -db[t1]);  // for the t2 field component
-  const double m1 = minmod_src(db[D], -db[t2]);  // for the t1 field component
+  const double m2 = wb_minmod(db[D], -db[t1]);  // for the t2 field component
+  const double m1 = wb_minmod(db[D], -db[t2]);  // for the t1 field component
   double S[8];
   S[F_RHO] = 0.0;
 #pragma unroll
@@ -457,15 +456,78 @@ __device__ __forceinline__ void transverse(const WbView& v, long long qo, long l
   S[F_BX + t1] = vv[t1] * m1;
   S[F_BX + t2] = vv[t2] * m2;
   const double c1 = hdt * g.idx[t1], c2 = hdt * g.idx[t2];
+  // rho: no source; momentum and energy: both transverse fluxes and the
+  // source; B_t1 (B_t2): only the t2 (t1) sweep carries it
+  v.qh[D][F_RHO][w] = v.q[F_RHO][q] - ((v.Fp[t1][F_RHO][w + s[t1]] - v.Fp[t1][F_RHO][w]) * c1 +
+                                       (v.Fp[t2][F_RHO][w + s[t2]] - v.Fp[t2][F_RHO][w]) * c2);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    if (c == F_BX + D) continue;
-    // normal-field fluxes of a sweep vanish (F_d[B_d] = 0)
-    const double d1 = (c == F_BX + t1) ? 0.0 : (v.Fp[t1][c][w + s[t1]] - v.Fp[t1][c][w]) * c1;
-    const double d2 = (c == F_BX + t2) ? 0.0 : (v.Fp[t2][c][w + s[t2]] - v.Fp[t2][c][w]) * c2;
+  for (int c = F_MX; c <= F_EN; ++c) {
+    const double d1 = (v.Fp[t1][c][w + s[t1]] - v.Fp[t1][c][w]) * c1;
+    const double d2 = (v.Fp[t2][c][w + s[t2]] - v.Fp[t2][c][w]) * c2;
     v.qh[D][c][w] = v.q[c][q] - (d1 + d2) + hdt * S[c];
   }
+  v.qh[D][F_BX + t1][w] = v.q[F_BX + t1][q] - (v.Fp[t2][F_BX + t1][w + s[t2]] - v.Fp[t2][F_BX + t1][w]) * c2 +
+                          hdt * S[F_BX + t1];
+  v.qh[D][F_BX + t2][w] = v.q[F_BX + t2][q] - (v.Fp[t1][F_BX + t2][w + s[t1]] - v.Fp[t1][F_BX + t2][w]) * c1 +
+                          hdt * S[F_BX + t2];
   v.qh[D][F_BX + D][w] = 0.5 * (v.bh[D][w] + v.bh[D][w + s[D]]);
+}
+
+// Steps 5 and 7 for the directions in mask (bit d) at one zone, sharing the
+// zone's velocity, field, face differences and each transverse flux
+// difference between the two states that use it.  Same arithmetic as
+// transverse<D> for every direction.
+__device__ __forceinline__ void transverse_set(const WbView& v, long long qo, long long wo, double dt,
+                                               int mask, int i, int j, int k) {
+  const WbGeo& g = v.geo;
+  const long long q = qo + wb_at(g, i, j, k);
+  const long long w = wo + wb_at(g, i, j, k);
+  const long long s[3] = {1, g.sy, g.sz};
+  const double hdt = 0.5 * dt;
+  const double ir = wb_rcp(v.q[F_RHO][q]);
+  double vv[3], B[3], db[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    vv[e] = v.q[F_MX + e][q] * ir;
+    B[e] = v.q[F_BX + e][q];
+    db[e] = (v.b[e][q + s[e]] - v.b[e][q]) * g.idx[e];
+  }
+  // flux differences (times dt/2 / dx_e) of every direction some state needs
+  double dF[3][8];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const bool need = (mask & ~(1 << e)) != 0;
+    const double c = hdt * g.idx[e];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      if (cc == F_BX + e || !need) { dF[e][cc] = 0.0; continue; }
+      dF[e][cc] = (v.Fp[e][cc][w + s[e]] - v.Fp[e][cc][w]) * c;
+    }
+  }
+  double qn[8];
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) qn[cc] = v.q[cc][q];
+#pragma unroll
+  for (int D = 0; D < 3; ++D) {
+    if (!(mask & (1 << D))) continue;
+    const int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+    const double m2 = wb_minmod(db[D], -db[t1]);
+    const double m1 = wb_minmod(db[D], -db[t2]);
+    double S[8];
+    S[F_RHO] = 0.0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) S[F_MX + e] = B[e] * db[D];
+    S[F_EN] = B[D] * vv[D] * db[D] + B[t1] * vv[t1] * m1 + B[t2] * vv[t2] * m2;
+    S[F_BX + D] = 0.0;
+    S[F_BX + t1] = vv[t1] * m1;
+    S[F_BX + t2] = vv[t2] * m2;
+    v.qh[D][F_RHO][w] = qn[F_RHO] - (dF[t1][F_RHO] + dF[t2][F_RHO]);
+#pragma unroll
+    for (int cc = F_MX; cc <= F_EN; ++cc) v.qh[D][cc][w] = qn[cc] - (dF[t1][cc] + dF[t2][cc]) + hdt * S[cc];
+    v.qh[D][F_BX + t1][w] = qn[F_BX + t1] - dF[t2][F_BX + t1] + hdt * S[F_BX + t1];
+    v.qh[D][F_BX + t2][w] = qn[F_BX + t2] - dF[t1][F_BX + t2] + hdt * S[F_BX + t2];
+    v.qh[D][F_BX + D][w] = 0.5 * (v.bh[D][w] + v.bh[D][w + s[D]]);
+  }
 }
 
 // Step 8: reference EMF at n+1/2 from v of q^n - dt/2 div F* and B = mean of
