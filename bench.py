@@ -44,12 +44,22 @@ N_BOX = 256
 SEED = 2
 # FP64 flops (DFMA = 2, DMUL = DADD = 1) the MHDTVD sweep executes per interface
 # system it computes, from the ncu FP64 instruction counters of k_sweep on the
-# 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full_v3.md): 594 M flops
+# 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full_v4.md): 552 M flops
 # over 9604 pencils x 107 interface systems.
-FLOPS_PER_FACE = 578.0
+FLOPS_PER_FACE = 537.0
 # FP64 issue rate of one GB300 SM: 2 DFMA per clock (measured with the DFMA
 # probe: 1196 GFLOP/s at 1995 MHz on 152 SMs), i.e. 4 flops per clock per SM.
 FP64_FLOPS_PER_CLK_PER_SM = 4.0
+
+
+def step_launches(desc):
+    """Kernels one wb_advance step launches: the dt kernel, 14 per pass over a
+    batch of patches (6 sweeps, reference EMF, corner EMFs, half CT,
+    transverse states, half-step reference EMF, corner EMFs, final CT, update)
+    and the ghost fill."""
+    npatch = desc.patches[0] * desc.patches[1] * desc.patches[2]
+    per_pass = desc.batch_patches if desc.batch_patches > 0 else npatch
+    return 2 + 14 * (-(-npatch // per_pass))
 
 
 def sweep_faces_per_step(n):
@@ -410,7 +420,7 @@ def main():
         sm_mhz = clk_summary["sm_mhz"] or 2070.0
         props = torch.cuda.get_device_properties(dev)
         peak = props.multi_processor_count * FP64_FLOPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
-        launches_per_step = 26
+        launches_per_step = step_launches(g.desc)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

@@ -626,26 +626,6 @@ void drop_graph(wb_batch* b) {
   b->graph_steps = 0;
 }
 
-WbPhys phys_of(const wb_desc& d0) {
-  WbPhys p;
-  p.gamma = d0.gamma;
-  p.gm1 = d0.gamma - 1.0;
-  p.gm2 = d0.gamma - 2.0;
-  p.g_over_gm1 = d0.gamma / (d0.gamma - 1.0);
-  p.inv_gm1 = 1.0 / (d0.gamma - 1.0);
-  p.gm2_over_gm1 = (d0.gamma - 2.0) / (d0.gamma - 1.0);
-  p.cfl = d0.cfl;
-  for (int k = 0; k < 7; ++k) {
-    p.eps[k] = d0.eps[k];
-    p.two_eps[k] = 2.0 * d0.eps[k];
-    p.inv4eps[k] = d0.eps[k] > 0.0 ? 1.0 / (4.0 * d0.eps[k]) : 0.0;
-  }
-  p.sweby = d0.sweby_beta;
-  p.minmod = d0.sweby_beta == 1.0 ? 1 : 0;
-  p.rho_floor = d0.rho_floor;
-  p.p_floor = d0.p_floor;
-  return p;
-}
 
 bool phys_ok(const wb_desc& d) {
   if (!(d.gamma > 1.0) || d.gamma > 2.0 || !(d.cfl > 0.0)) return false;
@@ -702,7 +682,7 @@ int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes
   b->free_[0] = b->state_cap;
   b->max_n = max_n;
   b->phys_desc = *physics;
-  b->phys = phys_of(*physics);
+  b->phys = wb_phys_of(physics);
   b->cfl = physics->cfl;
   b->stream = reinterpret_cast<cudaStream_t>(stream);
   b->mem = reinterpret_cast<char*>(dev_mem);

@@ -112,19 +112,24 @@ Layout layout(const wb_desc* d) {
   return L;
 }
 
-WbPhys make_phys(const wb_desc* d) {
+}  // namespace
+
+WbPhys wb_phys_of(const wb_desc* d) {
   WbPhys p;
   p.gamma = d->gamma;
   p.gm1 = d->gamma - 1.0;
   p.gm2 = d->gamma - 2.0;
+  p.hgm2 = 0.5 * (d->gamma - 2.0);
   p.g_over_gm1 = d->gamma / (d->gamma - 1.0);
   p.inv_gm1 = 1.0 / (d->gamma - 1.0);
   p.gm2_over_gm1 = (d->gamma - 2.0) / (d->gamma - 1.0);
   p.cfl = d->cfl;
+  p.eps_zero = 0;
   for (int k = 0; k < 7; ++k) {
     p.eps[k] = d->eps[k];
     p.two_eps[k] = 2.0 * d->eps[k];
     p.inv4eps[k] = d->eps[k] > 0.0 ? 1.0 / (4.0 * d->eps[k]) : 0.0;
+    if (d->eps[k] == 0.0) p.eps_zero |= 1 << k;
   }
   p.sweby = d->sweby_beta;
   p.minmod = d->sweby_beta == 1.0 ? 1 : 0;
@@ -132,6 +137,8 @@ WbPhys make_phys(const wb_desc* d) {
   p.p_floor = d->p_floor;
   return p;
 }
+
+namespace {
 
 int fail(wb_grid* g, int code, const std::string& msg) {
   if (g) g->err = msg;
@@ -344,7 +351,7 @@ int wb_grid_create(const wb_desc* d, void* dev_mem, size_t bytes, void* stream, 
   g->map.npatch = L.npatch;
   g->npatch = L.npatch;
   g->S = L.S;
-  g->phys = make_phys(d);
+  g->phys = wb_phys_of(d);
   g->stream = reinterpret_cast<cudaStream_t>(stream);
   g->mem = reinterpret_cast<char*>(dev_mem);
   g->bytes = bytes;
@@ -749,7 +756,7 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
   g.map.npatch = 1;
   g.npatch = 1;
   g.S = 1;
-  g.phys = make_phys(&one);
+  g.phys = wb_phys_of(&one);
   g.stream = reinterpret_cast<cudaStream_t>(stream);
   g.mem = reinterpret_cast<char*>(base);
   g.bytes = kNoallocBytes;

@@ -11,7 +11,9 @@ enum { F_RHO = 0, F_MX = 1, F_MY = 2, F_MZ = 3, F_EN = 4, F_BX = 5, F_BY = 6, F_
 
 struct WbPhys {
   double gamma, gm1, gm2, g_over_gm1, inv_gm1, gm2_over_gm1, cfl;
+  double hgm2;  // (gamma - 2) / 2
   double eps[7], two_eps[7], inv4eps[7];
+  int eps_zero;  // bit k set when eps_k == 0
   double sweby;
   int minmod;  // sweby == 1
   double rho_floor, p_floor;
@@ -131,6 +133,12 @@ __device__ __forceinline__ double wb_sweby(double a, double b, double beta, int 
   double m1 = fmin(beta * aa, s * b);
   double m2 = fmin(aa, beta * s * b);
   return s * fmax(0.0, fmax(m1, m2));
+}
+
+// x * s for s = +1 or -1: the sign bit of s flips x (integer pipe)
+__device__ __forceinline__ double wb_xsgn(double x, double s) {
+  const long long sg = __double_as_longlong(s) & (long long)0x8000000000000000ULL;
+  return __longlong_as_double(__double_as_longlong(x) ^ sg);
 }
 
 // |x| with the sign of s (integer pipe)

@@ -5,6 +5,10 @@
 #include "wb_device.cuh"
 #include "wb_units.cuh"
 
+struct wb_desc;
+// Physics constants of a descriptor (gamma, CFL, eps_k, limiter, floors).
+WbPhys wb_phys_of(const struct wb_desc* d);
+
 struct SweepArgs {
   const double* q[8];      // input zone fields (slot 0)
   const double* bn;        // normal face field (slot 0)

@@ -19,6 +19,10 @@
 // variables w = (rho, vn, vt, Bt, p) and sum_k beta_k R_k is accumulated in w
 // and mapped to conserved variables once (the map is linear).
 //
+// The default entropy-fix widths vanish on the linearly degenerate waves
+// (Alfven and entropy); a specialisation with those eps_k = 0 known at compile
+// time drops their Q-branch arithmetic.
+//
 // FP64 is the scarce unit on this GPU, so the arithmetic avoids the library
 // divide and square-root sequences (wb_rcp / wb_rsqrt), and gamma_k = dg/alpha
 // is never formed: Q(nu + gamma) alpha = |nu alpha + dg| sign(alpha) when
@@ -38,7 +42,10 @@ using wbu::kBlock;
 #define WB_SWEEP_MIN_BLOCKS 4
 #endif
 
-template <int D>
+// waves 2, 4, 6 (Alfven, entropy, Alfven) have eps = 0
+constexpr int kEpsZeroLD = (1 << 1) | (1 << 3) | (1 << 5);
+
+template <int D, int EZ>
 __global__ void __launch_bounds__(wbu::kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs A) {
   constexpr int U = (D == 0) ? 1 : 0;  // fastest transverse axis of the thread map
   constexpr int W = (D == 2) ? 1 : 2;
@@ -59,18 +66,18 @@ __global__ void __launch_bounds__(wbu::kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(Swee
   if (fb > A.box.hi[D]) fb = A.box.hi[D];
   if (fa > fb) return;
   const wbu::Rec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
-  const int bad = wbu::sweep_segment<D, true>(A.geo, A.q, A.bn, A.F, slot * A.slot_in, slot * A.slot_out,
+  const int bad = wbu::sweep_segment<D, true, EZ>(A.geo, A.q, A.bn, A.F, slot * A.slot_in, slot * A.slot_out,
                                         A.box.lo[U] + (int)(pen % nu_), A.box.lo[W] + (int)(pen / nu_),
                                         fa, fb, dt, A.phys, rec);
   if (bad) atomicAdd((unsigned long long*)&A.scal->unphysical, (unsigned long long)bad);
 }
 
-template <int D>
+template <int D, int EZ>
 int blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<D>, kBlock, 0) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<D, EZ>, kBlock, 0) != cudaSuccess || nb < 1)
       nb = 1;
     cached = nb;
   }
@@ -106,24 +113,30 @@ int choose_segments(long long pencils, int len, int resident) {
 
 }  // namespace
 
-template <int D>
+template <int D, int EZ>
 static void launch_sweep(SweepArgs a, int nslots, cudaStream_t s) {
   constexpr int U = (D == 0) ? 1 : 0;
   constexpr int W = (D == 2) ? 1 : 2;
   long long npen = (long long)(a.box.hi[U] - a.box.lo[U] + 1) * (a.box.hi[W] - a.box.lo[W] + 1);
   int len = a.box.hi[D] - a.box.lo[D] + 1;
-  int resident = blocks_per_sm<D>() * sm_count() * kBlock;
+  int resident = blocks_per_sm<D, EZ>() * sm_count() * kBlock;
   int nseg = a.nseg > 0 ? a.nseg : choose_segments(npen * nslots, len, resident);
   a.nseg = nseg;
   a.seg_len = (len + nseg - 1) / nseg;
   dim3 grid((unsigned)((npen * nseg + kBlock - 1) / kBlock), (unsigned)nslots);
-  k_sweep<D><<<grid, kBlock, 0, s>>>(a);
+  k_sweep<D, EZ><<<grid, kBlock, 0, s>>>(a);
+}
+
+template <int EZ>
+static void launch_sweep_dir(int dir, const SweepArgs& a, int nslots, cudaStream_t s) {
+  if (dir == 0) launch_sweep<0, EZ>(a, nslots, s);
+  else if (dir == 1) launch_sweep<1, EZ>(a, nslots, s);
+  else launch_sweep<2, EZ>(a, nslots, s);
 }
 
 void wb_launch_sweep(int dir, const SweepArgs& a, int nslots, cudaStream_t s) {
-  if (dir == 0) launch_sweep<0>(a, nslots, s);
-  else if (dir == 1) launch_sweep<1>(a, nslots, s);
-  else launch_sweep<2>(a, nslots, s);
+  if ((a.phys.eps_zero & kEpsZeroLD) == kEpsZeroLD) launch_sweep_dir<kEpsZeroLD>(dir, a, nslots, s);
+  else launch_sweep_dir<0>(dir, a, nslots, s);
 }
 
 // Self-test of the FP64 reciprocal helpers against the library division and

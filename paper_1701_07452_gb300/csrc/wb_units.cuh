@@ -32,8 +32,8 @@ struct Cell {
   double vn, vt1, vt2;
   double bt1, bt2;
   double eref;                    // E - bn^2/2 (energy referred to the face field)
-  double h;                       // gamma/(gamma-1) P + rho v^2/2 + |Bt|^2
-  double F[7];                    // Sec. 3 flux (rho, Mn, Mt1, Mt2, Bt1, Bt2, E)
+  double hr;                      // (gamma/(gamma-1) P + rho v^2/2 + |Bt|^2) / rho
+  double F[7];                    // half the Sec. 3 flux (rho, Mn, Mt1, Mt2, Bt1, Bt2, E)
   double mn, mt1, mt2;
 };
 
@@ -71,20 +71,23 @@ __device__ __forceinline__ void load_cell(const double* const* q, long long off,
   const double p = P.gm1 * (e - ke - me);
   const double pstar = p + me;
   c.eref = e - 0.5 * bn2;
-  c.h = P.g_over_gm1 * p + ke + bt2;
-  c.F[0] = c.mn;
-  c.F[1] = c.mn * c.vn + pstar - bn2;
-  c.F[2] = c.mn * c.vt1 - bn * c.bt1;
-  c.F[3] = c.mn * c.vt2 - bn * c.bt2;
-  c.F[4] = c.bt1 * c.vn - bn * c.vt1;
-  c.F[5] = c.bt2 * c.vn - bn * c.vt2;
-  c.F[6] = (e + pstar) * c.vn - bn * (bn * c.vn + c.bt1 * c.vt1 + c.bt2 * c.vt2);
+  c.hr = (P.g_over_gm1 * p + ke + bt2) * c.ir;
+  // half fluxes: the face needs (F_L + F_R) / 2
+  const double hmn = 0.5 * c.mn, hvn = 0.5 * c.vn, hbn = 0.5 * bn;
+  c.F[0] = hmn;
+  c.F[1] = fma(hmn, c.vn, 0.5 * (pstar - bn2));
+  c.F[2] = hmn * c.vt1 - hbn * c.bt1;
+  c.F[3] = hmn * c.vt2 - hbn * c.bt2;
+  c.F[4] = c.bt1 * hvn - hbn * c.vt1;
+  c.F[5] = c.bt2 * hvn - hbn * c.vt2;
+  c.F[6] = (e + pstar) * hvn - hbn * (bn * c.vn + c.bt1 * c.vt1 + c.bt2 * c.vt2);
 }
 
-// Per-face record (shared memory, structure of arrays over the block)
+// Per-face record (shared memory, structure of arrays over the block).
+// R_PG = rho a^2 / (gamma-1); R_KX = v^2/2 + (gamma-2)/(gamma-1) X.
 enum {
-  R_AL = 0, R_NU = 7, R_RHO = 14, R_SRHO, R_A, R_A2, R_CF, R_CS, R_AF, R_AS, R_B1, R_B2, R_S,
-  R_VN, R_VT1, R_VT2, R_BT1, R_BT2, R_X, R_FAVG, R_WORDS = R_FAVG + 7
+  R_AL = 0, R_NU = 7, R_RHO = 14, R_SRHO, R_A, R_PG, R_CF, R_CS, R_AF, R_AS, R_B1, R_B2, R_S,
+  R_VN, R_VT1, R_VT2, R_BT1, R_BT2, R_KX, R_FAVG, R_WORDS = R_FAVG + 7
 };
 
 struct Rec {
@@ -92,12 +95,17 @@ struct Rec {
   __device__ __forceinline__ double& operator[](int w) const { return p[w * kBlock]; }
 };
 
-// Q_k(chi) of App. A; the branch test runs on the integer pipe
-__device__ __forceinline__ double Qk(double chi, int k, const WbPhys& P) {
-  return wb_abs_less(chi, P.two_eps[k]) ? fma(chi * chi, P.inv4eps[k], P.eps[k]) : fabs(chi);
+// Q_k(nu) - nu^2 for the g-tilde of App. A.  Waves in the compile-time mask
+// EZ have eps_k = 0, where Q is |nu|; the branch test runs on the integer pipe.
+template <int EZ>
+__device__ __forceinline__ double Qk_m_nu2(double nu, int k, const WbPhys& P) {
+  const double n2 = nu * nu;
+  if (EZ & (1 << k)) return fabs(nu) - n2;
+  return (wb_abs_less(nu, P.two_eps[k]) ? fma(n2, P.inv4eps[k], P.eps[k]) : fabs(nu)) - n2;
 }
 
 // Roe state, eigen-system, alpha_k, nu_k and g-tilde_k of one interface
+template <int EZ>
 __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double b, double dtdx,
                                             const WbPhys& P, const Rec& f, double gt[7]) {
   const double iD = wb_rcp(L.sr + R.sr);
@@ -110,12 +118,13 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
   const double bt1 = wR * L.bt1 + wL * R.bt1;
   const double bt2 = wR * L.bt2 + wL * R.bt2;
   const double b2 = b * b;
-  const double H = wL * ((L.h + b2) * L.ir) + wR * ((R.h + b2) * R.ir);
+  // H = wL (h_L + b^2)/rho_L + wR (h_R + b^2)/rho_R, with wL/rho_L + wR/rho_R = 1/rho_
+  const double H = fma(b2, irho, wL * L.hr + wR * R.hr);
   const double dbt1 = R.bt1 - L.bt1, dbt2 = R.bt2 - L.bt2;
-  const double X = 0.5 * (dbt1 * dbt1 + dbt2 * dbt2) * (iD * iD);
-  const double v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+  const double gX = P.hgm2 * ((dbt1 * dbt1 + dbt2 * dbt2) * (iD * iD));  // (gamma-2) X
+  const double hv2 = 0.5 * (vn * vn + vt1 * vt1 + vt2 * vt2);
   const double bt2s = bt1 * bt1 + bt2 * bt2;
-  const double a2 = P.gm1 * (H - 0.5 * v2 - (b2 + bt2s) * irho) - P.gm2 * X;
+  const double a2 = P.gm1 * (H - hv2 - (b2 + bt2s) * irho) - gX;
   if (!wb_pos(a2)) return false;
   const double isrho = wb_rsqrt(rho);
   const double srho = rho * isrho;
@@ -159,8 +168,9 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
     af = wb_zero(af2) ? 0.0 : af2 * wb_rsqrt(af2);
     as = wb_zero(as2) ? 0.0 : as2 * wb_rsqrt(as2);
   }
+  const double ra2 = rho * a2;
   double b1n, b2n;
-  if (wb_le_nonneg(bt2s, 1e-24 * (rho * a2 + b2 + bt2s))) {
+  if (wb_le_nonneg(bt2s, 1e-24 * (ra2 + b2 + bt2s))) {
     b1n = b2n = 0.70710678118654752440;
   } else {
     const double ib = wb_rsqrt(bt2s);
@@ -168,35 +178,38 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
     b2n = bt2 * ib;
   }
   const double S = wb_sgn(b);
-  // primitive differences of the 7-variable system
+  // primitive differences of the 7-variable system; the velocity differences
+  // are kept times rho_ (dv' = rho_ dv), the 1/rho_ goes into the coefficients
   const double drho = R.rho - L.rho;
   const double dmn = R.mn - L.mn, dmt1 = R.mt1 - L.mt1, dmt2 = R.mt2 - L.mt2;
   const double de = R.eref - L.eref;
-  const double dvn = (dmn - vn * drho) * irho;
-  const double dvt1 = (dmt1 - vt1 * drho) * irho;
-  const double dvt2 = (dmt2 - vt2 * drho) * irho;
-  const double dp = P.gm1 * (de - (vn * dmn + vt1 * dmt1 + vt2 * dmt2) + 0.5 * v2 * drho -
-                             (bt1 * dbt1 + bt2 * dbt2)) - P.gm2 * X * drho;
-  // projections on the transverse field direction beta and its normal
-  const double dvb = b1n * dvt1 + b2n * dvt2, dvp = -b2n * dvt1 + b1n * dvt2;
-  const double dbb = b1n * dbt1 + b2n * dbt2, dbp = -b2n * dbt1 + b1n * dbt2;
-  const double i2a2 = 0.5 * ia * ia;
-  const double i2ra = 0.5 * isrho * ia;
-  const double dpr = dp * irho * i2a2;  // dp / (2 rho a^2)
+  const double dvn = dmn - vn * drho;
+  const double dvt1 = dmt1 - vt1 * drho;
+  const double dvt2 = dmt2 - vt2 * drho;
+  const double dp = P.gm1 * (de - (vn * dmn + vt1 * dmt1 + vt2 * dmt2) + hv2 * drho -
+                             (bt1 * dbt1 + bt2 * dbt2)) - gX * drho;
+  // projections on the transverse field direction beta and its normal; S = sign(b)
+  const double dvbS = wb_xsgn(b1n * dvt1 + b2n * dvt2, S), dvp = -b2n * dvt1 + b1n * dvt2;
+  const double dbb = b1n * dbt1 + b2n * dbt2, dbpS = wb_xsgn(-b2n * dbt1 + b1n * dbt2, S);
+  const double ia2 = ia * ia;
+  const double hir = 0.5 * irho, hisr = 0.5 * isrho;
+  const double i2ra = hisr * ia;         // 1 / (2 sqrt(rho) a)
+  const double ri2a2 = hir * ia2;        // 1 / (2 rho a^2)
+  const double dpr = dp * ri2a2;
   const double afcf = af * cf, ascs = as * cs;
-  const double Af = (afcf * dvn - ascs * S * dvb) * i2a2;
+  const double Af = (afcf * dvn - ascs * dvbS) * ri2a2;
   const double Cf = as * dbb * i2ra + af * dpr;
-  const double As = (ascs * dvn + afcf * S * dvb) * i2a2;
+  const double As = (ascs * dvn + afcf * dvbS) * ri2a2;
   const double Cs = -af * dbb * i2ra + as * dpr;
-  const double Aa = S * dbp * isrho;
+  const double hAa = hisr * dbpS;
   double al[7];
   al[0] = Cf - Af;
   al[6] = Cf + Af;
   al[2] = Cs - As;
   al[4] = Cs + As;
-  al[1] = 0.5 * (dvp + Aa);
-  al[5] = 0.5 * (dvp - Aa);
-  al[3] = drho - dp * (2.0 * i2a2);
+  al[1] = fma(hir, dvp, hAa);
+  al[5] = fma(hir, dvp, -hAa);
+  al[3] = fma(-dp, ia2, drho);
   // nu_k = (dt/dx) a_k for the eigenvalues a_1..a_7 (Sec. 3)
   const double tvn = dtdx * vn, tcf = dtdx * cf, tca = dtdx * ca, tcs = dtdx * cs;
   const double nuk[7] = {tvn - tcf, tvn - tca, tvn - tcs, tvn, tvn + tcs, tvn + tca, tvn + tcf};
@@ -205,26 +218,28 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
     const double nu = nuk[k];
     f[R_AL + k] = al[k];
     f[R_NU + k] = nu;
-    gt[k] = (Qk(nu, k, P) - nu * nu) * (0.5 * al[k]);
+    gt[k] = Qk_m_nu2<EZ>(nu, k, P) * (0.5 * al[k]);
   }
-  f[R_RHO] = rho; f[R_SRHO] = srho; f[R_A] = a; f[R_A2] = a2; f[R_CF] = cf; f[R_CS] = cs;
-  f[R_AF] = af; f[R_AS] = as; f[R_B1] = b1n; f[R_B2] = b2n; f[R_S] = S;
-  f[R_VN] = vn; f[R_VT1] = vt1; f[R_VT2] = vt2; f[R_BT1] = bt1; f[R_BT2] = bt2; f[R_X] = X;
+  f[R_RHO] = rho; f[R_SRHO] = srho; f[R_A] = a; f[R_PG] = ra2 * P.inv_gm1; f[R_CF] = cf;
+  f[R_CS] = cs; f[R_AF] = af; f[R_AS] = as; f[R_B1] = b1n; f[R_B2] = b2n; f[R_S] = S;
+  f[R_VN] = vn; f[R_VT1] = vt1; f[R_VT2] = vt2; f[R_BT1] = bt1; f[R_BT2] = bt2;
+  f[R_KX] = fma(gX, P.inv_gm1, hv2);
 #pragma unroll
-  for (int m = 0; m < 7; ++m) f[R_FAVG + m] = 0.5 * (L.F[m] + R.F[m]);
+  for (int m = 0; m < 7; ++m) f[R_FAVG + m] = L.F[m] + R.F[m];
   return true;
 }
 
 // beta_k of App. A without forming gamma_k: Q(nu + gamma) alpha equals
 // |nu alpha + dg| sign(alpha) when |nu alpha + dg| >= 2 eps |alpha|, else
 // (nu alpha + dg)^2 / (4 eps alpha) + eps alpha
+template <int EZ>
 __device__ __forceinline__ double beta_k(double al, double nu, double gi, double gi1, int k,
                                          const WbPhys& P) {
   const double w = fma(nu, al, gi1 - gi);             // (nu + gamma) alpha
   double qa;
   if (wb_zero(al)) {
     qa = 0.0;                                           // gamma = 0, Q(nu) 0
-  } else if (!wb_abs_less(w, P.two_eps[k] * al)) {
+  } else if ((EZ & (1 << k)) || !wb_abs_less(w, P.two_eps[k] * al)) {
     qa = wb_copysign_abs(w, al);                        // |nu + gamma| >= 2 eps
   } else if (wb_abs_less(al, 1e-290)) {
     qa = P.eps[k] * al;                                 // w^2/(4 eps alpha) < eps |alpha|
@@ -235,11 +250,12 @@ __device__ __forceinline__ double beta_k(double al, double nu, double gi, double
 }
 
 // u-bar = (F_L + F_R)/2 - (dx/(2 dt)) sum_k beta_k R_k  (App. A)
+template <int EZ>
 __device__ __forceinline__ void face_flux(const Rec& f, const double gi[7], const double gi1[7],
                                           double dx_2dt, const WbPhys& P, double out[7]) {
   double be[7];
 #pragma unroll
-  for (int k = 0; k < 7; ++k) be[k] = beta_k(f[R_AL + k], f[R_NU + k], gi[k], gi1[k], k, P);
+  for (int k = 0; k < 7; ++k) be[k] = beta_k<EZ>(f[R_AL + k], f[R_NU + k], gi[k], gi1[k], k, P);
   const double rho = f[R_RHO], af = f[R_AF], as = f[R_AS], cf = f[R_CF], cs = f[R_CS];
   const double S = f[R_S], b1 = f[R_B1], b2 = f[R_B2];
   // sum_k beta_k r_k in w = (rho, vn, vt, Bt, p)
@@ -249,22 +265,20 @@ __device__ __forceinline__ void face_flux(const Rec& f, const double gi[7], cons
   const double wr = rho * tfs + be[3];
   const double afcf = af * cf, ascs = as * cs;
   const double wvn = afcf * df + ascs * ds;
-  const double vb = S * (afcf * ds - ascs * df);   // along beta
-  const double vp = be[1] + be[5];                 // along beta-perp
+  const double vb = wb_xsgn(afcf * ds - ascs * df, S);   // along beta
+  const double vp = be[1] + be[5];                       // along beta-perp
   const double ra = f[R_SRHO] * f[R_A];
   const double bb = ra * (as * sf - af * ss);
-  const double bp = S * f[R_SRHO] * (be[1] - be[5]);
-  const double wp = rho * f[R_A2] * tfs;
+  const double bp = wb_xsgn(f[R_SRHO] * (be[1] - be[5]), S);
   const double wvt1 = b1 * vb - b2 * vp, wvt2 = b2 * vb + b1 * vp;
   const double wbt1 = b1 * bb - b2 * bp, wbt2 = b2 * bb + b1 * bp;
-  // to conserved variables
+  // to conserved variables (the pressure row enters the energy as p/(gamma-1))
   const double vn = f[R_VN], vt1 = f[R_VT1], vt2 = f[R_VT2];
-  const double v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
   const double u1 = vn * wr + rho * wvn;
   const double u2 = vt1 * wr + rho * wvt1;
   const double u3 = vt2 * wr + rho * wvt2;
-  const double u6 = wp * P.inv_gm1 + (0.5 * v2 + P.gm2_over_gm1 * f[R_X]) * wr +
-                    rho * (vn * wvn + vt1 * wvt1 + vt2 * wvt2) + f[R_BT1] * wbt1 + f[R_BT2] * wbt2;
+  const double u6 = f[R_PG] * tfs + f[R_KX] * wr + rho * (vn * wvn + vt1 * wvt1 + vt2 * wvt2) +
+                    f[R_BT1] * wbt1 + f[R_BT2] * wbt2;
   out[0] = f[R_FAVG + 0] - dx_2dt * wr;
   out[1] = f[R_FAVG + 1] - dx_2dt * u1;
   out[2] = f[R_FAVG + 2] - dx_2dt * u2;
@@ -286,7 +300,7 @@ __device__ __forceinline__ void poison(const Rec& f, double gt[7]) {
 // normal face field bn; outputs F.  qo / wo: slot offsets of the input and
 // output arrays.  rec: two shared-memory face records of this thread.
 // Returns the number of unphysical interfaces met.
-template <int D, bool NC>
+template <int D, bool NC, int EZ = 0>
 __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const* q,
                                              const double* bn, double* const* F, long long qo,
                                              long long wo, int pu, int pw, int fa, int fb,
@@ -315,7 +329,7 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
     load_cell<D, NC>(q, off_in + c * st, P, cR);
     const double b = ld<NC>(bn + off_in + c * st);
     double gt[7];
-    if (!face_system(cL, cR, b, dtdx, P, rec[cur], gt)) {
+    if (!face_system<EZ>(cL, cR, b, dtdx, P, rec[cur], gt)) {
       ++bad;  // unphysical Roe state: counted, the flux is poisoned with NaN
       poison(rec[cur], gt);
     }
@@ -327,7 +341,7 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
       if (f >= fa + 1) {
         // flux of face f-1 (zones f-2, f-1): g_{i} = g_p (zone f-2), g_{i+1} = gz
         double out[7];
-        face_flux(rec[cur ^ 1], g_p, gz, dx_2dt, P, out);
+        face_flux<EZ>(rec[cur ^ 1], g_p, gz, dx_2dt, P, out);
         const long long o = off_out + (c - 1) * st;
         F[F_RHO][o] = out[0];
         F[F_MX + D][o] = out[1];
