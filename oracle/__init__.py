@@ -67,10 +67,13 @@ def lib():
             L.or_stage.restype = ctypes.c_longlong
             L.or_stage.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ctypes.c_longlong]
             L.or_face_eigen.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
+            L.or_set_protection.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
             L.or_flux_pencil.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, dp, ctypes.c_double, dp]
+                                         ctypes.c_double, dp, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, dp]
             L.or_step_1d.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_double, dp, ctypes.c_double]
+                                     ctypes.c_double, ctypes.c_double, dp, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int]
             _lib = L
     return _lib
 
@@ -171,9 +174,15 @@ class Grid:
         return lib().or_divb_max(self._h)
 
     def counters(self):
-        out = (ctypes.c_longlong * 2)()
+        """(floor hits, unphysical zones, HLL faces) over all steps."""
+        out = (ctypes.c_longlong * 3)()
         lib().or_counters(self._h, out)
-        return int(out[0]), int(out[1])
+        return int(out[0]), int(out[1]), int(out[2])
+
+    def set_protection(self, prot_rho: float = 0.0, prot_p: float = 0.0):
+        """Protection floors of App. A (faces next to a zone below them use HLL)."""
+        if lib().or_set_protection(self._h, float(prot_rho), float(prot_p)):
+            raise ValueError("oracle: invalid protection floors")
 
     def stage(self, which: int):
         nx, ny, nz = self.n
@@ -193,24 +202,31 @@ def face_eigen(qL, qR, b, gamma):
     return lam, alpha, R.reshape(7, 7), L.reshape(7, 7)
 
 
-def flux_pencil(cells, bface, dtdx, dx_over_2dt, gamma, eps=DEFAULT_EPS, sweby=1.0):
+def flux_pencil(cells, bface, dtdx, dx_over_2dt, gamma, eps=DEFAULT_EPS, sweby=1.0,
+                prot_rho=0.0, prot_p=0.0, with_hll=False):
+    """Face fluxes of one pencil; with_hll also returns the number of output
+    faces that took the HLL flux."""
     cells = np.ascontiguousarray(cells, dtype=np.float64)
     bface = np.ascontiguousarray(bface, dtype=np.float64)
     n = cells.shape[0]
     out = np.full((n + 1, 7), np.nan)
     epsa = np.ascontiguousarray(eps, dtype=np.float64)
-    rc = lib().or_flux_pencil(n, _p(cells), _p(bface), float(dtdx), float(dx_over_2dt),
-                              float(gamma), _p(epsa), float(sweby), _p(out))
-    if rc:
-        raise ValueError(f"flux pencil rc={rc}")
-    return out
+    nh = lib().or_flux_pencil(n, _p(cells), _p(bface), float(dtdx), float(dx_over_2dt),
+                              float(gamma), _p(epsa), float(sweby), float(prot_rho),
+                              float(prot_p), _p(out))
+    if nh < 0:
+        raise ValueError("flux pencil: invalid arguments")
+    return (out, nh) if with_hll else out
 
 
-def step_1d(q, b, dt, dx, gamma, eps=DEFAULT_EPS, sweby=1.0):
+def step_1d(q, b, dt, dx, gamma, eps=DEFAULT_EPS, sweby=1.0, prot_rho=0.0, prot_p=0.0,
+            outflow=False, with_hll=False):
+    """One 1D step (periodic or zero-gradient ends); with_hll also returns the
+    number of faces that took the HLL flux."""
     q = np.ascontiguousarray(q, dtype=np.float64).copy()
     epsa = np.ascontiguousarray(eps, dtype=np.float64)
-    rc = lib().or_step_1d(q.shape[0], _p(q), float(b), float(dt), float(dx), float(gamma),
-                          _p(epsa), float(sweby))
-    if rc:
-        raise ValueError(f"1d step rc={rc}")
-    return q
+    nh = lib().or_step_1d(q.shape[0], _p(q), float(b), float(dt), float(dx), float(gamma),
+                          _p(epsa), float(sweby), float(prot_rho), float(prot_p), int(outflow))
+    if nh < 0:
+        raise ValueError("1d step: invalid arguments")
+    return (q, nh) if with_hll else q

@@ -16,6 +16,8 @@
 //   transverse_state          Steps 5 and 7 incl. the div B source term
 //   ghost fill                Sec. "MHD in Two Dimensions": 5 boundary zones,
 //                             one exchange per step
+//   hll_flux, protection      App. A, the protection floor and the HLL flux
+//                             (Eqs. for u-bar of the HLL scheme, b+ and b-)
 // Readings where the paper is silent are tagged R1..R21 as in the design notes.
 
 #include "mhd_oracle.h"
@@ -36,6 +38,7 @@ const double NaN = std::numeric_limits<double>::quiet_NaN();
 
 struct Params {
   double gamma, cfl, eps[7], sweby, rho_floor, p_floor;
+  double prot_rho = 0.0, prot_p = 0.0;  // protection floors (App. A)
 };
 
 // 3D array over the padded box [-NG, n+NG) per dimension, x fastest.
@@ -117,6 +120,7 @@ struct Eigen {
   double lam[7];
   double R[7][7];  // R[m][k]: conserved component m of right eigenvector k
   double L[7][7];  // L[k][m]: left eigenvector k
+  double rrho[7], rp[7];  // density and pressure rows of the primitive r_k
   bool bad;
 };
 
@@ -263,6 +267,10 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
   l[3][0] = 1.0;
   l[3][6] = -1.0 / a2;
 
+  for (int k = 0; k < 7; ++k) {
+    e->rrho[k] = r[0][k];
+    e->rp[k] = r[6][k];
+  }
   // W: conserved (rho, Mn, Mt1, Mt2, Bt1, Bt2, E) -> w
   double W[7][7];
   for (int m = 0; m < 7; ++m)
@@ -343,18 +351,84 @@ inline double sweby(double gp, double gm, double beta) {
   return s * m;
 }
 
+// Fast magnetosonic speed of one zone along the sweep normal (Sec. 3):
+// c_f^2 = [a^2 + B^2/rho + sqrt((a^2 + B^2/rho)^2 - 4 a^2 Bn^2/rho)] / 2,
+// a^2 = gamma P / rho, zone-centred B.
+inline double fast_speed(const Prim& p, double gamma) {
+  double a2 = gamma * p.p / p.rho;
+  double b2 = (p.bn * p.bn + p.bt1 * p.bt1 + p.bt2 * p.bt2) / p.rho;
+  double s = a2 + b2;
+  double disc = s * s - 4.0 * a2 * p.bn * p.bn / p.rho;
+  if (disc < 0.0) disc = 0.0;  // reading R2
+  return std::sqrt(0.5 * (s + std::sqrt(disc)));
+}
+
+// Protection floor (App. A, reading R22): active when a floor is > 0.  A face
+// takes the HLL flux when one of the states of its linearised (Roe) Riemann
+// problem has a density or pressure below the floors: the two zone states
+// and the intermediate states w_L + sum_{j<=k} alpha_j r_j, k = 1..6, in the
+// primitive variables of the linearisation (Roe-type fluxes fail exactly when
+// these states are unphysical).
+inline bool protection_active(const Params& P) { return P.prot_rho > 0.0 || P.prot_p > 0.0; }
+
+bool protection_hit(const Prim& pL, const Prim& pR, const Eigen& e, const double alpha[7],
+                    const Params& P) {
+  if (pL.rho < P.prot_rho || pL.p < P.prot_p) return true;
+  if (pR.rho < P.prot_rho || pR.p < P.prot_p) return true;
+  double rho = pL.rho, p = pL.p;
+  for (int k = 0; k < 6; ++k) {
+    rho += alpha[k] * e.rrho[k];
+    p += alpha[k] * e.rp[k];
+    if (rho < P.prot_rho || p < P.prot_p) return true;
+  }
+  return false;
+}
+
+// HLL flux of App. A between zones L = i and R = i+1 (reading R22):
+//   b+ = max(a_max, v_R + c_f,R, 0),  b- = min(a_min, v_L - c_f,L, 0),
+//   u = (b+ F(q_L) - b- F(q_R) + b+ b- (q_R - q_L)) / (b+ - b-),
+// a_max, a_min the largest and smallest Roe eigenvalues when the Roe state
+// exists (roe == nullptr otherwise).  The printed numerator has +b- F(q_R),
+// which is not consistent (u != F for q_L = q_R); the Einfeldt form used here
+// is.  If both speeds vanish (no Roe state and both zones moving
+// supersonically into the face) the bounds are +-max(|v| + c_f).
+void hll_flux(const Cell& L, const Cell& R, const Prim& pL, const Prim& pR, const double FL[7],
+              const double FR[7], const Eigen* roe, double gamma, double out[7]) {
+  double cfL = fast_speed(pL, gamma), cfR = fast_speed(pR, gamma);
+  double bp = std::fmax(pR.vn + cfR, 0.0);
+  double bm = std::fmin(pL.vn - cfL, 0.0);
+  if (roe) {
+    bp = std::fmax(bp, roe->lam[6]);
+    bm = std::fmin(bm, roe->lam[0]);
+  }
+  if (!(bp - bm > 0.0)) {
+    double s = std::fmax(std::fabs(pL.vn) + cfL, std::fabs(pR.vn) + cfR);
+    bp = s;
+    bm = -s;
+  }
+  double dq[7];
+  cons_diff(L, R, dq);
+  for (int m = 0; m < 7; ++m)
+    out[m] = (bp * FL[m] - bm * FR[m] + bp * bm * dq[m]) / (bp - bm);
+}
+
 struct Face {
   Eigen e;
   double alpha[7], nu[7], gt[7], Favg[7];
+  bool hll;
+  double Fhll[7];
 };
 
 // MHDTVD flux on one pencil.  cells[c] for c in [0, ncell), face f between
 // cells f-1 and f, bface[f] for f in [0, ncell].  Faces f in [2, ncell-2] get
 // a flux (they need g at cells f-1 and f, i.e. g-tilde at faces f-1..f+1,
-// i.e. cells f-2..f+1).  Returns the number of unphysical interfaces.
+// i.e. cells f-2..f+1).  A face whose Roe state has no real sound speed, or
+// next to a zone below the protection floor, takes the HLL flux instead and
+// contributes g-tilde = 0 to the limiter of its neighbours (reading R22).
+// Returns the number of output faces that took the HLL flux.
 int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
                 double dx_2dt, const Params& P, double (*out)[7]) {
-  int bad = 0;
+  int nhll = 0;
   std::vector<Prim> prim(ncell);
   std::vector<double> Fc((size_t)ncell * 7);
   for (int c = 0; c < ncell; ++c) {
@@ -367,17 +441,27 @@ int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
     const Cell& L = cells[f - 1];
     const Cell& R = cells[f];
     roe_state(prim[f - 1], prim[f], bface[f], P.gamma, &F.e);
-    if (F.e.bad) {
-      ++bad;
-      for (int k = 0; k < 7; ++k) F.alpha[k] = F.nu[k] = F.gt[k] = NaN;
+    F.hll = F.e.bad;
+    if (!F.hll) {
+      double dq[7];
+      cons_diff(L, R, dq);
+      for (int k = 0; k < 7; ++k) {
+        double s = 0.0;
+        for (int m = 0; m < 7; ++m) s += F.e.L[k][m] * dq[m];
+        F.alpha[k] = s;                       // alpha_k = L_k . (q_{i+1} - q_i)
+      }
+      if (protection_active(P)) F.hll = protection_hit(prim[f - 1], prim[f], F.e, F.alpha, P);
+    }
+    if (F.hll) {
+      for (int k = 0; k < 7; ++k) {
+        F.alpha[k] = F.nu[k] = NaN;
+        F.gt[k] = 0.0;
+      }
+      hll_flux(L, R, prim[f - 1], prim[f], &Fc[(size_t)(f - 1) * 7], &Fc[(size_t)f * 7],
+               F.e.bad ? nullptr : &F.e, P.gamma, F.Fhll);
       continue;
     }
-    double dq[7];
-    cons_diff(L, R, dq);
     for (int k = 0; k < 7; ++k) {
-      double s = 0.0;
-      for (int m = 0; m < 7; ++m) s += F.e.L[k][m] * dq[m];
-      F.alpha[k] = s;                       // alpha_k = L_k . (q_{i+1} - q_i)
       F.nu[k] = dtdx * F.e.lam[k];          // (dt/dx) a_k
       F.gt[k] = 0.5 * (Qk(F.nu[k], P.eps[k]) - F.nu[k] * F.nu[k]) * F.alpha[k];
     }
@@ -391,6 +475,11 @@ int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
       g[(size_t)c * 7 + k] = sweby(face[c + 1].gt[k], face[c].gt[k], P.sweby);
   for (int f = 2; f <= ncell - 2; ++f) {
     const Face& F = face[f];
+    if (F.hll) {
+      ++nhll;
+      for (int m = 0; m < 7; ++m) out[f][m] = F.Fhll[m];
+      continue;
+    }
     double fsum[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < 7; ++k) {
       double gi = g[(size_t)(f - 1) * 7 + k];   // g_{k,i}, i = left cell
@@ -401,7 +490,7 @@ int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
     }
     for (int m = 0; m < 7; ++m) out[f][m] = F.Favg[m] - dx_2dt * fsum[m];
   }
-  return bad;
+  return nhll;
 }
 
 // ---------------------------------------------------------------------------
@@ -424,7 +513,7 @@ struct or_grid {
   Arr bh[3];                      // b^{n+1/2}
   Arr qh[3][8];                   // q^{n+1/2}_d
   Arr Erefh[3], Eedgeh[3];        // half-step reference, corrector edge EMFs
-  long long floor_hits = 0, unphysical = 0;
+  long long floor_hits = 0, unphysical = 0, hll_faces = 0;
 };
 
 namespace {
@@ -482,6 +571,7 @@ inline void load_cell(const or_grid* g, const Arr* q, int d, int i, int j, int k
 // Sweep along d over faces [r.lo[d], r.hi[d]] and transverse cells r (other
 // dims).  Input state qin (8 comps, zone-centred B), normal face field bn.
 // Output flux arrays out[8] (global component order, normal-B flux = 0).
+// Returns the number of faces that took the HLL flux.
 int sweep(or_grid* g, int d, const Arr* qin, const Arr& bn, double dt, const Range& r, Arr* out) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   double dtdx = dt / g->dxv[d];
@@ -898,15 +988,15 @@ int or_step(or_grid* g, double dt) {
   if (!g || !(dt > 0.0)) return 1;
   const int* n = g->n;
   const int N0 = n[0], N1 = n[1], N2 = n[2];
-  int bad = 0;
+  long long nhll = 0;
   // Step 1: predictor fluxes from q^n over the regions the later steps read.
   {
     Range rx = box(-3, N0 + 3, -4, N1 + 3, -4, N2 + 3);
     Range ry = box(-4, N0 + 3, -3, N1 + 3, -4, N2 + 3);
     Range rz = box(-4, N0 + 3, -4, N1 + 3, -3, N2 + 3);
-    bad += sweep(g, 0, g->q, g->b[0], dt, rx, g->Fp[0]);
-    bad += sweep(g, 1, g->q, g->b[1], dt, ry, g->Fp[1]);
-    bad += sweep(g, 2, g->q, g->b[2], dt, rz, g->Fp[2]);
+    nhll += sweep(g, 0, g->q, g->b[0], dt, rx, g->Fp[0]);
+    nhll += sweep(g, 1, g->q, g->b[1], dt, ry, g->Fp[1]);
+    nhll += sweep(g, 2, g->q, g->b[2], dt, rz, g->Fp[2]);
   }
   // Step 2: reference EMF from q^n
   reference_emf(&g->q[RHO], &g->q[MX], &g->q[BX], g->Eref,
@@ -926,9 +1016,9 @@ int or_step(or_grid* g, double dt) {
   transverse_state(g, 1, dt, box(-1, N0, -3, N1 + 2, -1, N2));
   transverse_state(g, 2, dt, box(-1, N0, -1, N1, -3, N2 + 2));
   // Steps 6 and 7: corrector fluxes, normal Roe field = b^{n+1/2}
-  bad += sweep(g, 0, g->qh[0], g->bh[0], dt, box(-1, N0 + 1, -1, N1, -1, N2), g->Fc[0]);
-  bad += sweep(g, 1, g->qh[1], g->bh[1], dt, box(-1, N0, -1, N1 + 1, -1, N2), g->Fc[1]);
-  bad += sweep(g, 2, g->qh[2], g->bh[2], dt, box(-1, N0, -1, N1, -1, N2 + 1), g->Fc[2]);
+  nhll += sweep(g, 0, g->qh[0], g->bh[0], dt, box(-1, N0 + 1, -1, N1, -1, N2), g->Fc[0]);
+  nhll += sweep(g, 1, g->qh[1], g->bh[1], dt, box(-1, N0, -1, N1 + 1, -1, N2), g->Fc[1]);
+  nhll += sweep(g, 2, g->qh[2], g->bh[2], dt, box(-1, N0, -1, N1, -1, N2 + 1), g->Fc[2]);
   // Step 8: half-step reference EMF
   half_reference_emf(g, dt, box(-1, N0, -1, N1, -1, N2));
   // Step 9: corner EMFs from the corrector fluxes
@@ -963,10 +1053,11 @@ int or_step(or_grid* g, double dt) {
     ct_update(g, g->b, g->Eedgeh, dt, tmp, rr);
     for (int d = 0; d < 3; ++d) g->b[d].d.swap(tmp[d].d);
   }
+  long long unph0 = g->unphysical;
   apply_floors_and_ccb(g);
-  g->unphysical += bad;
+  g->hll_faces += nhll;
   ghost_fill(g);
-  return (bad > 0 || g->unphysical > 0) ? 4 : 0;
+  return g->unphysical > unph0 ? 4 : 0;
 }
 
 int or_totals(const or_grid* g, double tot[8]) {
@@ -1003,9 +1094,17 @@ double or_divb_max(const or_grid* g) {
   return m;
 }
 
-int or_counters(const or_grid* g, long long out[2]) {
+int or_counters(const or_grid* g, long long out[3]) {
   out[0] = g->floor_hits;
   out[1] = g->unphysical;
+  out[2] = g->hll_faces;
+  return 0;
+}
+
+int or_set_protection(or_grid* g, double prot_rho, double prot_p) {
+  if (!g || !(prot_rho >= 0.0) || !(prot_p >= 0.0)) return 1;
+  g->P.prot_rho = prot_rho;
+  g->P.prot_p = prot_p;
   return 0;
 }
 
@@ -1065,39 +1164,40 @@ int or_face_eigen(const double qL[8], const double qR[8], double b, double gamma
 
 int or_flux_pencil(int ncell, const double* cells, const double* bface, double dtdx,
                    double dx_over_2dt, double gamma, const double eps[7], double sweby,
-                   double* out) {
-  if (ncell < 4) return 1;
+                   double prot_rho, double prot_p, double* out) {
+  if (ncell < 4) return -1;
   Params P;
   P.gamma = gamma;
   P.cfl = 0.0;
   for (int k = 0; k < 7; ++k) P.eps[k] = eps[k];
   P.sweby = sweby;
   P.rho_floor = P.p_floor = 0.0;
+  P.prot_rho = prot_rho;
+  P.prot_p = prot_p;
   std::vector<Cell> c(ncell);
   for (int i = 0; i < ncell; ++i) {
     const double* q = cells + (size_t)i * 8;
     c[i] = Cell{q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7]};
   }
-  int bad = pencil_flux(ncell, c.data(), bface, dtdx, dx_over_2dt, P,
-                        reinterpret_cast<double(*)[7]>(out));
-  return bad ? 4 : 0;
+  return pencil_flux(ncell, c.data(), bface, dtdx, dx_over_2dt, P,
+                     reinterpret_cast<double(*)[7]>(out));
 }
 
 // Independent 1D driver (the RJ95 one-dimensional scheme, App. A Eq.
 // mhd_finite): periodic ghosts, the same interface flux, q -= dt/dx du.
 int or_step_1d(int n, double* q, double b, double dt, double dx, double gamma,
-               const double eps[7], double sweby) {
-  if (n < 1) return 1;
+               const double eps[7], double sweby, double prot_rho, double prot_p, int outflow) {
+  if (n < 1) return -1;
   const int G = 3;  // a face flux needs two zones on each side
   int ncell = n + 2 * G;
   std::vector<double> cells((size_t)ncell * 8), bface(ncell + 1, b);
   for (int c = 0; c < ncell; ++c) {
-    int src = wrap(c - G, n);
+    int src = outflow ? std::min(std::max(c - G, 0), n - 1) : wrap(c - G, n);
     for (int v = 0; v < 8; ++v) cells[(size_t)c * 8 + v] = q[(size_t)src * 8 + v];
   }
   std::vector<double> flux((size_t)(ncell + 1) * 7, NaN);
   int rc = or_flux_pencil(ncell, cells.data(), bface.data(), dt / dx, dx / (2.0 * dt), gamma,
-                          eps, sweby, flux.data());
+                          eps, sweby, prot_rho, prot_p, flux.data());
   // system order (rho, Mn, Mt1, Mt2, Bt1, Bt2, E) -> cell order (rho, Mn, Mt1, Mt2, E, Bn, Bt1, Bt2)
   const int map[7] = {0, 1, 2, 3, 6, 7, 4};
   for (int i = 0; i < n; ++i) {

@@ -15,6 +15,10 @@
  *   bx [nz][ny][nx+1], by [nz][ny+1][nx], bz [nz+1][ny][nx]
  *   B  [3][nz][ny][nx]  zone-centred field (read only)
  * Return codes: 0 ok, 1 invalid argument, 4 unphysical state met.
+ * HLL flux (App. A): faces whose Roe state has no real sound speed take the
+ * HLL flux; with protection floors set (> 0), so do faces where a zone state
+ * or an intermediate state of the linearised Riemann problem has
+ * rho < prot_rho or P < prot_p.
  */
 #ifndef MHD_ORACLE_H
 #define MHD_ORACLE_H
@@ -46,8 +50,10 @@ int or_step(or_grid* g, double dt);
 /* Conserved totals x cell volume: rho, Mx, My, Mz, E, bx, by, bz. */
 int or_totals(const or_grid* g, double tot[8]);
 double or_divb_max(const or_grid* g);
-/* floor hits, unphysical count accumulated over all steps */
-int or_counters(const or_grid* g, long long out[2]);
+/* floor hits, unphysical zones, HLL faces accumulated over all steps */
+int or_counters(const or_grid* g, long long out[3]);
+/* Protection floors (>= 0; 0 and 0, the default, turn protection off). */
+int or_set_protection(or_grid* g, double prot_rho, double prot_p);
 int or_set_threads(int n);
 
 /* Stage dump: copy an intermediate of the last step, on interior cells
@@ -72,16 +78,19 @@ int or_face_eigen(const double qL[8], const double qR[8], double b, double gamma
 /* One MHDTVD flux pencil (pins): ncell cells (sweep frame 8-vectors,
  * row-major [ncell][8]) and ncell+1 face fields bface (face f between cells
  * f-1 and f).  Fluxes at faces [2, ncell-2] are written to out[(ncell+1)][7]
- * (other faces untouched). */
+ * (other faces untouched).  Returns the number of those faces that took the
+ * HLL flux, or -1 for invalid arguments. */
 int or_flux_pencil(int ncell, const double* cells, const double* bface,
                    double dtdx, double dx_over_2dt, double gamma, const double eps[7],
-                   double sweby, double* out);
+                   double sweby, double prot_rho, double prot_p, double* out);
 
-/* Independent 1D MHDTVD (RJ95-type) step on a periodic line of n cells:
- * q[n][8] conserved sweep-frame vectors (B_n constant = b), updated in place
- * by q -= dt/dx (u_{i+1/2} - u_{i-1/2}) for all components. */
+/* Independent 1D MHDTVD (RJ95-type) step on a line of n cells, periodic
+ * (outflow = 0) or zero-gradient (outflow = 1) ends: q[n][8] conserved
+ * sweep-frame vectors (B_n constant = b), updated in place by
+ * q -= dt/dx (u_{i+1/2} - u_{i-1/2}) for all components.  Returns the number
+ * of HLL faces, or -1 for invalid arguments. */
 int or_step_1d(int n, double* q, double b, double dt, double dx, double gamma,
-               const double eps[7], double sweby);
+               const double eps[7], double sweby, double prot_rho, double prot_p, int outflow);
 
 #ifdef __cplusplus
 }

@@ -60,7 +60,7 @@ def test_conservation_and_divb(oracle_mod):
     scale = np.array([np.abs(U0[0]).sum(), mom, mom, mom, np.abs(U0[4]).sum(), bmax * U0[0].size,
                       bmax * U0[0].size, bmax * U0[0].size])
     assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
-    assert g.counters() == (0, 0)
+    assert g.counters() == (0, 0, 0)
 
 
 def x_only_state(n, ny, nz, seed):
