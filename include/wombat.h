@@ -59,7 +59,14 @@ extern "C" {
  *              ordered (v-cf, v-ca, v-cs, v, v+cs, v+ca, v+cf)
  *  sweby_beta  SWEBY limiter parameter, 1 <= beta <= 2 (1 = minmod)
  *  rho_floor, p_floor  floors applied to the updated state (App. A)
- *  batch_patches  patches processed together per pipeline pass (0 = all) */
+ *  batch_patches  patches processed together per pipeline pass (0 = all)
+ *  prot_rho, prot_p  protection floors of App. A (>= 0; both 0 = off).  With
+ *              a floor set, a face takes the HLL flux (App. A, Eqs. for the
+ *              HLL u-bar, b+ and b-) when a zone state next to it, or an
+ *              intermediate state of its linearised Riemann problem
+ *              w_L + sum_{j<=k} alpha_j r_j, has rho < prot_rho or
+ *              P < prot_p.  Independently of the floors, a face whose Roe
+ *              state has no real sound speed always takes the HLL flux. */
 typedef struct wb_desc {
   int n[3];
   int patches[3];
@@ -72,14 +79,17 @@ typedef struct wb_desc {
   double rho_floor;
   double p_floor;
   int batch_patches;
+  double prot_rho;
+  double prot_p;
 } wb_desc;
 
 typedef struct wb_counters_t {
   long long steps;          /* steps taken since load */
   long long floor_hits;     /* zones where a floor was applied */
-  long long unphysical;     /* interfaces or zones found unphysical */
+  long long unphysical;     /* updated zones found non-finite or with rho <= 0 */
   double t;                 /* simulated time since load */
   double last_dt;           /* dt of the last step */
+  long long hll_faces;      /* faces whose flux came from the HLL fallback */
 } wb_counters_t;
 
 typedef struct wb_grid wb_grid;

@@ -46,6 +46,8 @@ class WbDesc(ctypes.Structure):
         ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double),
         ("batch_patches", ctypes.c_int),
+        ("prot_rho", ctypes.c_double),
+        ("prot_p", ctypes.c_double),
     ]
 
 
@@ -56,6 +58,7 @@ class WbCounters(ctypes.Structure):
         ("unphysical", ctypes.c_longlong),
         ("t", ctypes.c_double),
         ("last_dt", ctypes.c_double),
+        ("hll_faces", ctypes.c_longlong),
     ]
 
 
@@ -137,7 +140,8 @@ def lib(build: bool = True):
 
 
 def make_desc(n, patches=(1, 1, 1), length=None, gamma=5.0 / 3.0, cfl=0.8, bc=(0, 0, 0),
-              eps=DEFAULT_EPS, sweby=1.0, rho_floor=1e-20, p_floor=1e-20, batch_patches=0):
+              eps=DEFAULT_EPS, sweby=1.0, rho_floor=1e-20, p_floor=1e-20, batch_patches=0,
+              prot_rho=0.0, prot_p=0.0):
     d = WbDesc()
     lib().wb_desc_default(ctypes.byref(d), int(n[0]), int(n[1]), int(n[2]))
     for a in range(3):
@@ -149,6 +153,7 @@ def make_desc(n, patches=(1, 1, 1), length=None, gamma=5.0 / 3.0, cfl=0.8, bc=(0
     d.gamma, d.cfl, d.sweby_beta = float(gamma), float(cfl), float(sweby)
     d.rho_floor, d.p_floor = float(rho_floor), float(p_floor)
     d.batch_patches = int(batch_patches)
+    d.prot_rho, d.prot_p = float(prot_rho), float(prot_p)
     return d
 
 
@@ -280,7 +285,7 @@ class Grid:
         c = WbCounters()
         self._check(lib().wb_counters(self._h, ctypes.byref(c)))
         return {"steps": c.steps, "floor_hits": c.floor_hits, "unphysical": c.unphysical,
-                "t": c.t, "last_dt": c.last_dt}
+                "t": c.t, "last_dt": c.last_dt, "hll_faces": c.hll_faces}
 
     def profile_sweeps(self, enable: bool):
         self._check(lib().wb_profile_sweeps(self._h, int(bool(enable))))
@@ -387,7 +392,7 @@ class Batch:
         c = WbCounters()
         self._check(lib().wb_batch_counters(self._h, int(box), ctypes.byref(c)))
         return {"steps": c.steps, "floor_hits": c.floor_hits, "unphysical": c.unphysical,
-                "t": c.t, "last_dt": c.last_dt}
+                "t": c.t, "last_dt": c.last_dt, "hll_faces": c.hll_faces}
 
     def autotune(self, trial_steps=1):
         ms = ctypes.c_double(0.0)

@@ -209,15 +209,16 @@ __device__ __forceinline__ int sweep_item(const BoxInfo& bi, bool corr, const Wb
 
 __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, int box,
                                           const BoxInfo& bi, long long item, double dt,
-                                          const wbu::Rec rec[2], double* wmax, int* hits, int* bad) {
+                                          const wbu::Rec rec[2], double* wmax, int* hits, int* bad,
+                                          int* hll) {
   const WbView& v = bi.v;
   const int* n = v.geo.n;
   if (stage_is_sweep(s)) {
     const WbBox b = stage_box(s, d, n);
     const bool corr = s == BS_CORR;
-    if (d == 0) *bad += sweep_item<0>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
-    else if (d == 1) *bad += sweep_item<1>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
-    else *bad += sweep_item<2>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    if (d == 0) *hll += sweep_item<0>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    else if (d == 1) *hll += sweep_item<1>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    else *hll += sweep_item<2>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
     return;
   }
   if (s == BS_HALO) {
@@ -329,12 +330,13 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
           long long i1 = i0 + ipc;
           if (i1 > nitems) i1 = nitems;
           double wmax = 0.0;
-          int hits = 0, bad = 0;
+          int hits = 0, bad = 0, hll = 0;
           for (long long it = i0 + threadIdx.x; it < i1; it += kB)
-            unit_item(B, s, sub, box, bi, it, dt, rec, &wmax, &hits, &bad);
+            unit_item(B, s, sub, box, bi, it, dt, rec, &wmax, &hits, &bad, &hll);
           if (s == BS_FINAL) warp_max_atomic(wmax, &B.scal[box].wmax_next);
           if (hits) atomicAdd((unsigned long long*)&B.scal[box].floor_hits, (unsigned long long)hits);
           if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
+          if (hll) atomicAdd((unsigned long long*)&B.scal[box].hll_faces, (unsigned long long)hll);
         }
         if (!grid_barrier(B, nblocks)) return;
       }
@@ -631,6 +633,7 @@ bool phys_ok(const wb_desc& d) {
   if (!(d.gamma > 1.0) || d.gamma > 2.0 || !(d.cfl > 0.0)) return false;
   for (int k = 0; k < 7; ++k)
     if (!(d.eps[k] >= 0.0) || !(d.eps[k] < 0.5)) return false;
+  if (!(d.prot_rho >= 0.0) || !(d.prot_p >= 0.0)) return false;
   return d.sweby_beta >= 1.0 && d.sweby_beta <= 2.0;
 }
 
@@ -1026,6 +1029,7 @@ int wb_batch_counters(wb_batch* b, int box, wb_counters_t* c) {
   c->steps = sc.steps;
   c->floor_hits = sc.floor_hits;
   c->unphysical = sc.unphysical;
+  c->hll_faces = sc.hll_faces;
   c->t = sc.t;
   c->last_dt = sc.dt;
   return WB_OK;

@@ -76,6 +76,10 @@ bool valid_desc(const wb_desc* d, std::string* why) {
     if (!(d->eps[k] >= 0.0) || !(d->eps[k] < 0.5)) { *why = "eps_k must be in [0, 0.5)"; return false; }
   if (!(d->sweby_beta >= 1.0) || d->sweby_beta > 2.0) { *why = "sweby_beta must be in [1, 2]"; return false; }
   if (d->batch_patches < 0) { *why = "batch_patches must be >= 0"; return false; }
+  if (!(d->prot_rho >= 0.0) || !(d->prot_p >= 0.0)) {
+    *why = "protection floors must be >= 0";
+    return false;
+  }
   return true;
 }
 
@@ -135,6 +139,9 @@ WbPhys wb_phys_of(const wb_desc* d) {
   p.minmod = d->sweby_beta == 1.0 ? 1 : 0;
   p.rho_floor = d->rho_floor;
   p.p_floor = d->p_floor;
+  p.prot_rho = d->prot_rho;
+  p.prot_p = d->prot_p;
+  p.prot = (d->prot_rho > 0.0 || d->prot_p > 0.0) ? 1 : 0;
   return p;
 }
 
@@ -586,6 +593,7 @@ int wb_counters(wb_grid* g, wb_counters_t* c) {
   c->steps = sc.steps;
   c->floor_hits = sc.floor_hits;
   c->unphysical = sc.unphysical;
+  c->hll_faces = sc.hll_faces;
   c->t = sc.t;
   c->last_dt = sc.dt;
   return WB_OK;

@@ -17,6 +17,8 @@ struct WbPhys {
   double sweby;
   int minmod;  // sweby == 1
   double rho_floor, p_floor;
+  double prot_rho, prot_p;  // protection floors (App. A)
+  int prot;                 // a protection floor is > 0
 };
 
 // Geometry of one patch and its padded storage (x fastest).
@@ -52,6 +54,7 @@ struct WbScalars {
   long long floor_hits;
   long long unphysical;
   long long timeouts;
+  long long hll_faces;
 };
 
 

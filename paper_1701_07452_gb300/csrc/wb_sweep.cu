@@ -45,7 +45,7 @@ using wbu::kBlock;
 // waves 2, 4, 6 (Alfven, entropy, Alfven) have eps = 0
 constexpr int kEpsZeroLD = (1 << 1) | (1 << 3) | (1 << 5);
 
-template <int D, int EZ>
+template <int D, int EZ, bool PROT>
 __global__ void __launch_bounds__(wbu::kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs A) {
   constexpr int U = (D == 0) ? 1 : 0;  // fastest transverse axis of the thread map
   constexpr int W = (D == 2) ? 1 : 2;
@@ -66,18 +66,19 @@ __global__ void __launch_bounds__(wbu::kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(Swee
   if (fb > A.box.hi[D]) fb = A.box.hi[D];
   if (fa > fb) return;
   const wbu::Rec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
-  const int bad = wbu::sweep_segment<D, true, EZ>(A.geo, A.q, A.bn, A.F, slot * A.slot_in, slot * A.slot_out,
+  const int nhll = wbu::sweep_segment<D, true, EZ, PROT>(A.geo, A.q, A.bn, A.F, slot * A.slot_in, slot * A.slot_out,
                                         A.box.lo[U] + (int)(pen % nu_), A.box.lo[W] + (int)(pen / nu_),
                                         fa, fb, dt, A.phys, rec);
-  if (bad) atomicAdd((unsigned long long*)&A.scal->unphysical, (unsigned long long)bad);
+  if (nhll) atomicAdd((unsigned long long*)&A.scal->hll_faces, (unsigned long long)nhll);
 }
 
-template <int D, int EZ>
+template <int D, int EZ, bool PROT>
 int blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<D, EZ>, kBlock, 0) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<D, EZ, PROT>, kBlock, 0) != cudaSuccess ||
+        nb < 1)
       nb = 1;
     cached = nb;
   }
@@ -113,30 +114,38 @@ int choose_segments(long long pencils, int len, int resident) {
 
 }  // namespace
 
-template <int D, int EZ>
+template <int D, int EZ, bool PROT>
 static void launch_sweep(SweepArgs a, int nslots, cudaStream_t s) {
   constexpr int U = (D == 0) ? 1 : 0;
   constexpr int W = (D == 2) ? 1 : 2;
   long long npen = (long long)(a.box.hi[U] - a.box.lo[U] + 1) * (a.box.hi[W] - a.box.lo[W] + 1);
   int len = a.box.hi[D] - a.box.lo[D] + 1;
-  int resident = blocks_per_sm<D, EZ>() * sm_count() * kBlock;
+  int resident = blocks_per_sm<D, EZ, PROT>() * sm_count() * kBlock;
   int nseg = a.nseg > 0 ? a.nseg : choose_segments(npen * nslots, len, resident);
   a.nseg = nseg;
   a.seg_len = (len + nseg - 1) / nseg;
   dim3 grid((unsigned)((npen * nseg + kBlock - 1) / kBlock), (unsigned)nslots);
-  k_sweep<D, EZ><<<grid, kBlock, 0, s>>>(a);
+  k_sweep<D, EZ, PROT><<<grid, kBlock, 0, s>>>(a);
 }
 
-template <int EZ>
+template <int EZ, bool PROT>
 static void launch_sweep_dir(int dir, const SweepArgs& a, int nslots, cudaStream_t s) {
-  if (dir == 0) launch_sweep<0, EZ>(a, nslots, s);
-  else if (dir == 1) launch_sweep<1, EZ>(a, nslots, s);
-  else launch_sweep<2, EZ>(a, nslots, s);
+  if (dir == 0) launch_sweep<0, EZ, PROT>(a, nslots, s);
+  else if (dir == 1) launch_sweep<1, EZ, PROT>(a, nslots, s);
+  else launch_sweep<2, EZ, PROT>(a, nslots, s);
 }
 
+// Kernel variants: eps_k = 0 on the linearly degenerate waves (the default)
+// or general eps; protection floors off (the default) or on.
 void wb_launch_sweep(int dir, const SweepArgs& a, int nslots, cudaStream_t s) {
-  if ((a.phys.eps_zero & kEpsZeroLD) == kEpsZeroLD) launch_sweep_dir<kEpsZeroLD>(dir, a, nslots, s);
-  else launch_sweep_dir<0>(dir, a, nslots, s);
+  const bool ez = (a.phys.eps_zero & kEpsZeroLD) == kEpsZeroLD;
+  if (a.phys.prot) {
+    if (ez) launch_sweep_dir<kEpsZeroLD, true>(dir, a, nslots, s);
+    else launch_sweep_dir<0, true>(dir, a, nslots, s);
+  } else {
+    if (ez) launch_sweep_dir<kEpsZeroLD, false>(dir, a, nslots, s);
+    else launch_sweep_dir<0, false>(dir, a, nslots, s);
+  }
 }
 
 // Self-test of the FP64 reciprocal helpers against the library division and

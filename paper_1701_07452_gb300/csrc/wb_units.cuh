@@ -104,10 +104,85 @@ __device__ __forceinline__ double Qk_m_nu2(double nu, int k, const WbPhys& P) {
   return (wb_abs_less(nu, P.two_eps[k]) ? fma(n2, P.inv4eps[k], P.eps[k]) : fabs(nu)) - n2;
 }
 
-// Roe state, eigen-system, alpha_k, nu_k and g-tilde_k of one interface
-template <int EZ>
-__device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double b, double dtdx,
-                                            const WbPhys& P, const Rec& f, double gt[7]) {
+// Gas pressure of a zone from its sweep-frame fields (Sec. 3, Eq. totenergy)
+__device__ __forceinline__ double zone_pressure(const Cell& c, const WbPhys& P) {
+  return P.gm1 * (c.eref - 0.5 * (c.mn * c.vn + c.mt1 * c.vt1 + c.mt2 * c.vt2) -
+                  0.5 * (c.bt1 * c.bt1 + c.bt2 * c.bt2));
+}
+
+// Protection floor of App. A: true when a zone state, or an intermediate
+// state w_L + sum_{j<=k} alpha_j r_j of the linearised Riemann problem, has a
+// density or pressure below the floors.  The density / pressure rows of r_k
+// (k = 1..6) are rho_ af / rho_ a^2 af, 0 / 0, rho_ as / rho_ a^2 as, 1 / 0,
+// rho_ as / rho_ a^2 as, 0 / 0.
+__device__ __forceinline__ bool protection_hit(const Cell& L, const Cell& R, double rho, double ra2,
+                                               double af, double as, const double al[7],
+                                               const WbPhys& P) {
+  const double pL = zone_pressure(L, P), pR = zone_pressure(R, P);
+  if (L.rho < P.prot_rho || pL < P.prot_p || R.rho < P.prot_rho || pR < P.prot_p) return true;
+  const double r1 = L.rho + al[0] * (rho * af), p1 = pL + al[0] * (ra2 * af);
+  if (r1 < P.prot_rho || p1 < P.prot_p) return true;
+  const double r3 = r1 + al[2] * (rho * as), p3 = p1 + al[2] * (ra2 * as);
+  if (r3 < P.prot_rho || p3 < P.prot_p) return true;
+  const double r4 = r3 + al[3];
+  if (r4 < P.prot_rho) return true;
+  const double r5 = r4 + al[4] * (rho * as), p5 = p3 + al[4] * (ra2 * as);
+  return r5 < P.prot_rho || p5 < P.prot_p;
+}
+
+// Fast speed of one zone along the sweep axis with its own zone field (Sec. 3)
+__device__ __forceinline__ double zone_fast_speed(const Cell& c, double bn, const WbPhys& P) {
+  const double a2 = P.gamma * zone_pressure(c, P) / c.rho;
+  const double b2 = (bn * bn + c.bt1 * c.bt1 + c.bt2 * c.bt2) / c.rho;
+  const double s = a2 + b2;
+  double disc = s * s - 4.0 * a2 * bn * bn / c.rho;
+  if (disc < 0.0) disc = 0.0;
+  return sqrt(0.5 * (s + sqrt(disc)));
+}
+
+// Marker of a face record that holds a finished HLL flux (a Roe density is > 0)
+constexpr double kHllFace = -1.0;
+
+// HLL flux of App. A into the record of one face:
+//   b+ = max(a_max, vR + cfR, 0), b- = min(a_min, vL - cfL, 0),
+//   u = (b+ F_L - b- F_R + b+ b- (q_R - q_L)) / (b+ - b-),
+// with a_max, a_min = vn_ +- cf_ of the Roe state when it exists (roe), the
+// Einfeldt sign of the F_R term (the printed +b- F_R is not consistent), and
+// bounds +-max(|v| + c_f) if both speeds vanish.  Rare path.
+__device__ __forceinline__ void hll_face(const Cell& L, const Cell& R, double bnL, double bnR, bool roe,
+                                      const WbPhys& P, const Rec& f) {
+  const double cfL = zone_fast_speed(L, bnL, P), cfR = zone_fast_speed(R, bnR, P);
+  double bp = fmax(R.vn + cfR, 0.0);
+  double bm = fmin(L.vn - cfL, 0.0);
+  if (roe) {
+    bp = fmax(bp, f[R_VN] + f[R_CF]);
+    bm = fmin(bm, f[R_VN] - f[R_CF]);
+  }
+  if (!(bp - bm > 0.0)) {
+    const double sp = fmax(fabs(L.vn) + cfL, fabs(R.vn) + cfR);
+    bp = sp;
+    bm = -sp;
+  }
+  const double dq[7] = {R.rho - L.rho, R.mn - L.mn, R.mt1 - L.mt1, R.mt2 - L.mt2,
+                        R.bt1 - L.bt1, R.bt2 - L.bt2, R.eref - L.eref};
+  const double inv = 1.0 / (bp - bm);
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    // the zone fluxes hold F/2
+    const double FL = 2.0 * L.F[m], FR = 2.0 * R.F[m];
+    f[R_FAVG + m] = (bp * FL - bm * FR + bp * bm * dq[m]) * inv;
+  }
+  f[R_RHO] = kHllFace;
+}
+
+// Roe state, eigen-system, alpha_k, nu_k and g-tilde_k of one interface.
+// Returns 0 for an MHDTVD face, 1 when the protection floor asks for the HLL
+// flux (the record holds the Roe state), 2 when the Roe state has no real
+// sound speed (HLL without Roe speeds).  The protection test is compiled in
+// only when PROT is set.
+template <int EZ, bool PROT>
+__device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double b, double dtdx,
+                                           const WbPhys& P, const Rec& f, double gt[7]) {
   const double iD = wb_rcp(L.sr + R.sr);
   const double wL = L.sr * iD, wR = R.sr * iD;
   const double rho = L.sr * R.sr;
@@ -125,7 +200,7 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
   const double hv2 = 0.5 * (vn * vn + vt1 * vt1 + vt2 * vt2);
   const double bt2s = bt1 * bt1 + bt2 * bt2;
   const double a2 = P.gm1 * (H - hv2 - (b2 + bt2s) * irho) - gX;
-  if (!wb_pos(a2)) return false;
+  if (!wb_pos(a2)) return 2;
   const double isrho = wb_rsqrt(rho);
   const double srho = rho * isrho;
   const double ca2 = b2 * irho, ct2 = bt2s * irho;
@@ -226,7 +301,8 @@ __device__ __forceinline__ bool face_system(const Cell& L, const Cell& R, double
   f[R_KX] = fma(gX, P.inv_gm1, hv2);
 #pragma unroll
   for (int m = 0; m < 7; ++m) f[R_FAVG + m] = L.F[m] + R.F[m];
-  return true;
+  if (PROT && P.prot && protection_hit(L, R, rho, ra2, af, as, al, P)) return 1;
+  return 0;
 }
 
 // beta_k of App. A without forming gamma_k: Q(nu + gamma) alpha equals
@@ -288,19 +364,14 @@ __device__ __forceinline__ void face_flux(const Rec& f, const double gi[7], cons
   out[6] = f[R_FAVG + 6] - dx_2dt * u6;
 }
 
-__device__ __forceinline__ void poison(const Rec& f, double gt[7]) {
-  const double nan = __longlong_as_double(0x7ff8000000000000LL);
-#pragma unroll
-  for (int k = 0; k < 7; ++k) gt[k] = nan;
-  for (int w = 0; w < R_WORDS; ++w) f[w] = nan;
-}
-
 // One pencil segment of an MHDTVD sweep along D: fluxes of faces [fa, fb]
 // at transverse position (pos[U], pos[W]) of the input fields q (zone B),
 // normal face field bn; outputs F.  qo / wo: slot offsets of the input and
 // output arrays.  rec: two shared-memory face records of this thread.
-// Returns the number of unphysical interfaces met.
-template <int D, bool NC, int EZ = 0>
+// Faces without a Roe state or below the protection floor take the HLL flux
+// and give g-tilde = 0 to the limiters of their neighbours.  Returns the
+// number of HLL faces among [fa, fb].
+template <int D, bool NC, int EZ = 0, bool PROT = true>
 __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const* q,
                                              const double* bn, double* const* F, long long qo,
                                              long long wo, int pu, int pw, int fa, int fb,
@@ -321,7 +392,7 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
   Cell cL, cR;
   load_cell<D, NC>(q, off_in, P, cL);
   double gt_p[7], g_p[7];  // g-tilde of face f-1; g of zone f-2
-  int bad = 0;
+  int nhll = 0;
   int cur = 0;
   // faces f = fa-1 .. fb+1; face f lies between zones f-1 and f
   for (int f = fa - 1; f <= fb + 1; ++f) {
@@ -329,9 +400,13 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
     load_cell<D, NC>(q, off_in + c * st, P, cR);
     const double b = ld<NC>(bn + off_in + c * st);
     double gt[7];
-    if (!face_system<EZ>(cL, cR, b, dtdx, P, rec[cur], gt)) {
-      ++bad;  // unphysical Roe state: counted, the flux is poisoned with NaN
-      poison(rec[cur], gt);
+    const int code = face_system<EZ, PROT>(cL, cR, b, dtdx, P, rec[cur], gt);
+    if (code) {
+      const double bnL = ld<NC>(q[F_BX + D] + off_in + (c - 1) * st);
+      const double bnR = ld<NC>(q[F_BX + D] + off_in + c * st);
+      hll_face(cL, cR, bnL, bnR, code == 1, P, rec[cur]);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) gt[k] = 0.0;
     }
     if (f >= fa) {
       // g of zone f-1 from g-tilde of faces f (i+1/2) and f-1 (i-1/2)
@@ -341,7 +416,14 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
       if (f >= fa + 1) {
         // flux of face f-1 (zones f-2, f-1): g_{i} = g_p (zone f-2), g_{i+1} = gz
         double out[7];
-        face_flux<EZ>(rec[cur ^ 1], g_p, gz, dx_2dt, P, out);
+        const Rec& fr = rec[cur ^ 1];
+        if (wb_neg(fr[R_RHO])) {
+#pragma unroll
+          for (int m = 0; m < 7; ++m) out[m] = fr[R_FAVG + m];
+          ++nhll;
+        } else {
+          face_flux<EZ>(fr, g_p, gz, dx_2dt, P, out);
+        }
         const long long o = off_out + (c - 1) * st;
         F[F_RHO][o] = out[0];
         F[F_MX + D][o] = out[1];
@@ -359,7 +441,7 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
     cur ^= 1;
     cL = cR;
   }
-  return bad;
+  return nhll;
 }
 
 // ---------------------------------------------------------------- stages ---

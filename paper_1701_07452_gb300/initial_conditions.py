@@ -21,7 +21,8 @@ import math
 
 import numpy as np
 
-__all__ = ["random_box", "turbulence_box", "turbulence_box_device", "mode_table", "curl_faces", "State"]
+__all__ = ["random_box", "turbulence_box", "turbulence_box_device", "expansion_box", "mode_table",
+           "curl_faces", "State"]
 
 
 class State(dict):
@@ -65,6 +66,28 @@ def random_box(n, seed, b0=1.0 / math.sqrt(4.0 * math.pi), a_amp=0.05):
     bx, by, bz = curl_faces(Ax, Ay, Az, 1.0, 1.0, 1.0)
     bx = bx + b0
     return State(W=W, bx=bx, by=by, bz=bz, length=(float(nx), float(ny), float(nz)))
+
+
+def expansion_box(n, seed, speed=2.0, gamma=5.0 / 3.0):
+    """Strong 3D expansion on a periodic unit box: v_x = -speed on the low
+    half and +speed on the high half (a double rarefaction at the middle, a
+    collision at the wrap, Mach ~2.4 each way), transverse shear
+    0.3 sin(2 pi x), 5 % random noise, P = 0.4, field (0.3, 0.2, 0.1) plus
+    the curl of a random edge potential.  A Roe-type flux meets unphysical
+    intermediate states here; the input for the protection-floor path."""
+    n = int(n)
+    rng = np.random.default_rng(seed)
+    shape = (n, n, n)
+    x = (np.arange(n) + 0.5) / n
+    W = np.empty((5,) + shape)
+    W[0] = 1.0 + 0.05 * rng.uniform(-1.0, 1.0, shape)
+    W[1] = np.where(x[None, None, :] < 0.5, -speed, speed) + 0.05 * rng.uniform(-1.0, 1.0, shape)
+    W[2] = 0.3 * np.sin(2.0 * np.pi * x)[:, None, None] + 0.05 * rng.uniform(-1.0, 1.0, shape)
+    W[3] = 0.3 * np.sin(2.0 * np.pi * x)[None, :, None] + 0.05 * rng.uniform(-1.0, 1.0, shape)
+    W[4] = 0.4
+    A = [0.02 / n * rng.uniform(-1.0, 1.0, shape) for _ in range(3)]
+    bx, by, bz = curl_faces(*A, 1.0 / n, 1.0 / n, 1.0 / n)
+    return State(W=W, bx=bx + 0.3, by=by + 0.2, bz=bz + 0.1, length=(1.0, 1.0, 1.0))
 
 
 def mode_table(seed, kmin, kmax, slope=-2.0):
