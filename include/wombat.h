@@ -125,9 +125,13 @@ int wb_compute_dt(wb_grid* g, double* dt);
 
 /* Advance nsteps CTU+CT steps, each with the CFL dt of its start state,
  * clipped so that the time since load does not pass t_end (t_end <= 0: no
- * limit; steps past t_end do nothing).  If t_out != NULL the stream is
- * synchronised, *t_out receives the time since load and an unphysical state
- * met during these steps returns WB_ERR_UNPHYSICAL. */
+ * limit; steps past t_end do nothing).  The step that reaches t_end lands
+ * on it exactly, and a step within 1e-10 of a CFL step of t_end is
+ * stretched to it.  With t_end > 0 the call reads the device time back
+ * every 64 steps (host synchronisation) and stops launching once t_end is
+ * reached.  If t_out != NULL the stream is synchronised, *t_out receives
+ * the time since load and an unphysical state met during these steps
+ * returns WB_ERR_UNPHYSICAL. */
 int wb_advance(wb_grid* g, int nsteps, double t_end, double* t_out);
 
 /* Read back the state (any pointer may be NULL); on_device as for load. */
@@ -248,7 +252,7 @@ int wb_batch_steps_left(wb_batch* b, int* out);
 
 /* Self-test of the library's FP64 reciprocal and reciprocal-square-root
  * helpers (PTX approximations refined by a third-order correction) against
- * the CUDA library division and rsqrt on n inputs spread over [1e-40, 1e40]:
+ * the CUDA library division and rsqrt on n inputs spread over [1e-300, 1e300]:
  * worst[0] = max |rcp(x) x - 1|, worst[1] = max |rsqrt_ours / rsqrt_cuda - 1|.
  * Uses the grid's reduction words; synchronises the grid's stream. */
 int wb_selftest_math(wb_grid* g, int n, double worst[2]);

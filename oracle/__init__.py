@@ -155,14 +155,19 @@ class Grid:
         t = 0.0
         for _ in range(int(nsteps)):
             h = self.dt() if dt is None else float(dt)
+            last = False
             if t_end is not None:
-                if t >= t_end:
+                rem = t_end - t
+                if not rem > 0.0:
                     break
-                h = min(h, t_end - t)
+                # the step that reaches t_end lands on it and leaves no
+                # sliver below 1e-10 of a step
+                if h >= rem * (1.0 - 1e-10):
+                    h, last = rem, True
             rc = self.step(h)
             if rc:
                 raise RuntimeError(f"oracle step returned {rc}")
-            t += h
+            t = t_end if last else t + h
         return t
 
     def totals(self):

@@ -150,7 +150,7 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
   double v2 = e->vn * e->vn + e->vt1 * e->vt1 + e->vt2 * e->vt2;
   double bt2sum = e->bt1 * e->bt1 + e->bt2 * e->bt2;
   e->a2 = (gamma - 1.0) * (H - 0.5 * v2 - (b * b + bt2sum) / e->rho) - (gamma - 2.0) * e->X;
-  if (!(e->a2 > 0.0)) {
+  if (!(e->a2 >= std::numeric_limits<double>::min())) {  // no real sound speed
     e->bad = true;
     return;
   }

@@ -471,7 +471,17 @@ int wb_advance(wb_grid* g, int nsteps, double t_end, double* t_out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return check_cuda(g, e, "advance");
   }
+  // With a time limit, the device clock is read back every kStepsPerCheck
+  // steps and the remaining steps (which would do nothing) are not launched.
+  constexpr int kStepsPerCheck = 64;
   for (int st = 0; st < nsteps; ++st) {
+    if (t_end > 0.0 && st > 0 && st % kStepsPerCheck == 0) {
+      double t_now = 0.0;
+      e = cudaMemcpyAsync(&t_now, &g->scal->t, sizeof(t_now), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return check_cuda(g, e, "advance");
+      if (t_now >= t_end) break;
+    }
     wb_launch_dt_step(g->scal, g->d.cfl, t_end, s);
     for (long long p0 = 0; p0 < g->npatch; p0 += g->S) {
       int ns = (int)std::min<long long>(g->S, g->npatch - p0);

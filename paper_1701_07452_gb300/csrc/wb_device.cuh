@@ -80,7 +80,8 @@ __device__ __forceinline__ double wb_minmod(double a, double b) {
 //   1/x:       e = 1 - x y,    y <- y (1 + e + e^2)
 //   1/sqrt(x): e = 1 - x y^2,  y <- y (1 + e/2 + 3 e^2 / 8)
 // The truncation error is O(e^3) ~ 1e-18, below one ulp.  Inputs must be
-// positive, finite and normal (the callers guarantee or guard this).
+// positive, finite and normal: the approximations flush subnormal inputs to
+// zero (callers test with wb_normal_pos or know the range).
 __device__ __forceinline__ double wb_rcp(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -109,6 +110,12 @@ __device__ __forceinline__ bool wb_pos(double x) {
 __device__ __forceinline__ bool wb_neg(double x) {
   const long long b = __double_as_longlong(x);
   return b < 0 && (b & 0x7fffffffffffffffLL) != 0 && (b & 0x7fffffffffffffffLL) <= 0x7ff0000000000000LL;
+}
+// x is a positive normal finite double (>= 2^-1022; false for subnormals,
+// zero, negatives, inf and NaN)
+__device__ __forceinline__ bool wb_normal_pos(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0x0010000000000000LL && b < 0x7ff0000000000000LL;
 }
 // x == 0 (either sign)
 __device__ __forceinline__ bool wb_zero(double x) {

@@ -187,10 +187,14 @@ __global__ void k_dt_step(WbScalars* s, double cfl, double t_end) {
   double w = __longlong_as_double((long long)s->wmax_next);
   double dt = cfl / w;
   bool ok = (w > 0.0) && isfinite(w) && isfinite(dt) && dt > 0.0;
+  bool last = false;
   if (t_end > 0.0) {
     double rem = t_end - s->t;
     if (!(rem > 0.0)) { s->dt = 0.0; return; }  // past t_end: skip, keep the rate
-    if (ok && dt > rem) dt = rem;
+    // the step that reaches t_end lands on it exactly and leaves no sliver
+    // below 1e-10 of a step (a near-zero dt still carries the eps_k
+    // dissipation of Q_k and dx/(2 dt) overflows the flux scale)
+    if (ok && dt >= rem * (1.0 - 1e-10)) { dt = rem; last = true; }
   }
   if (!ok) {
     s->dt = 0.0;
@@ -198,7 +202,7 @@ __global__ void k_dt_step(WbScalars* s, double cfl, double t_end) {
     return;
   }
   s->dt = dt;
-  s->t += dt;
+  s->t = last ? t_end : s->t + dt;
   s->steps += 1;
   s->wmax_next = 0ULL;
 }

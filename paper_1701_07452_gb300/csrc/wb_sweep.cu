@@ -149,7 +149,7 @@ void wb_launch_sweep(int dir, const SweepArgs& a, int nslots, cudaStream_t s) {
 }
 
 // Self-test of the FP64 reciprocal helpers against the library division and
-// reciprocal square root on n inputs spread over [1e-40, 1e40].
+// reciprocal square root on n inputs spread over [1e-300, 1e300].
 namespace {
 __global__ void k_math_selftest(int n, unsigned long long seed, unsigned long long* worst) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -160,7 +160,7 @@ __global__ void k_math_selftest(int n, unsigned long long seed, unsigned long lo
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
     z ^= z >> 31;
     double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
-    double x = exp((u - 0.5) * 184.2);
+    double x = exp((u - 0.5) * 1381.55);
     e_rcp = fabs(wb_rcp(x) * x - 1.0);
     e_rsq = fabs(wb_rsqrt(x) / rsqrt(x) - 1.0);
   }

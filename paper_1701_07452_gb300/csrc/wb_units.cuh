@@ -200,7 +200,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   const double hv2 = 0.5 * (vn * vn + vt1 * vt1 + vt2 * vt2);
   const double bt2s = bt1 * bt1 + bt2 * bt2;
   const double a2 = P.gm1 * (H - hv2 - (b2 + bt2s) * irho) - gX;
-  if (!wb_pos(a2)) return 2;
+  if (!wb_normal_pos(a2)) return 2;
   const double isrho = wb_rsqrt(rho);
   const double srho = rho * isrho;
   const double ca2 = b2 * irho, ct2 = bt2s * irho;
@@ -208,7 +208,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   const double disc = dac * dac + ct2 * (ct2 + 2.0 * (a2 + ca2));
   const double sum = a2 + ca2 + ct2;
   double rsd = 0.0, sd = 0.0;
-  if (wb_pos(disc)) {
+  if (wb_normal_pos(disc)) {  // a subnormal discriminant is degenerate (sd ~ 0)
     rsd = wb_rsqrt(disc);
     sd = disc * rsd;
   }
@@ -240,8 +240,9 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
     const double cf2_ca2 = n2 ? qd : 0.5 * (t2 + sd);
     const double af2 = wb_clamp01(a2 * cf2_ca2 * (icf * icf) * rsd);
     const double as2 = wb_clamp01(cf2_a2 * rsd);
-    af = wb_zero(af2) ? 0.0 : af2 * wb_rsqrt(af2);
-    as = wb_zero(as2) ? 0.0 : as2 * wb_rsqrt(as2);
+    // subnormal squares (from underflowing transverse fields) count as 0
+    af = wb_normal_pos(af2) ? af2 * wb_rsqrt(af2) : 0.0;
+    as = wb_normal_pos(as2) ? as2 * wb_rsqrt(as2) : 0.0;
   }
   const double ra2 = rho * a2;
   double b1n, b2n;
@@ -655,7 +656,10 @@ __device__ __forceinline__ void eref_half(const WbView& v, long long qo, long lo
   v.Erefh[2][w] = vy * B[0] - vx * B[1];
 }
 
-__device__ __forceinline__ double wb_sqrt_fast(double x) { return x > 0.0 ? x * wb_rsqrt(x) : 0.0; }
+// sqrt for the CFL rate; inputs below the normal range (or not > 0) give 0
+__device__ __forceinline__ double wb_sqrt_fast(double x) {
+  return wb_normal_pos(x) ? x * wb_rsqrt(x) : 0.0;
+}
 
 // CFL signal rate sum_d (|v_d| + c_f,d)/dx_d of one zone (Sec. 3 fast speed).
 __device__ __forceinline__ double signal_rate(double rho, double mx, double my, double mz, double e,
@@ -678,7 +682,7 @@ __device__ __forceinline__ double signal_rate(double rho, double mx, double my, 
     const double cf = wb_sqrt_fast(0.5 * (a2 + cn2 + ct2 + wb_sqrt_fast(disc)));
     w += (fabs(vv[d]) + cf) * g.idx[d];
   }
-  if (!(p > 0.0) || !(rho > 0.0)) w = __longlong_as_double(0x7ff8000000000000LL);
+  if (!(rho > 0.0)) w = __longlong_as_double(0x7ff8000000000000LL);
   return w;
 }
 

@@ -22,7 +22,8 @@ import math
 import numpy as np
 
 __all__ = ["random_box", "turbulence_box", "turbulence_box_device", "expansion_box", "mode_table",
-           "curl_faces", "State"]
+           "curl_faces", "cpaw_box", "field_loop_box", "shock_tube_1d", "blast_box", "SHOCK_TUBES",
+           "State"]
 
 
 class State(dict):
@@ -88,6 +89,146 @@ def expansion_box(n, seed, speed=2.0, gamma=5.0 / 3.0):
     A = [0.02 / n * rng.uniform(-1.0, 1.0, shape) for _ in range(3)]
     bx, by, bz = curl_faces(*A, 1.0 / n, 1.0 / n, 1.0 / n)
     return State(W=W, bx=bx + 0.3, by=by + 0.2, bz=bz + 0.1, length=(1.0, 1.0, 1.0))
+
+
+# Rotated frame of the oblique tests (Sec. "Linear Wave Convergence", 3D): the
+# wave normal n = (1, 2, 2)/3 makes every box of shape (3, 3/2, 3/2) with
+# 2N x N x N zones periodic for one wavelength 1 along n.
+OBLIQUE_N = np.array([1.0, 2.0, 2.0]) / 3.0
+OBLIQUE_E2 = np.array([-2.0, 1.0, 0.0]) / math.sqrt(5.0)
+OBLIQUE_E3 = np.cross(OBLIQUE_N, OBLIQUE_E2)
+
+
+def _oblique_coords(n):
+    """Zone-centre and edge-centre coordinates x1 = n . x of a 2N x N x N box
+    of size (3, 3/2, 3/2); edges as in curl_faces."""
+    nx, ny, nz = 2 * n, n, n
+    d = 1.5 / n
+    i = np.arange(nx)[None, None, :]
+    j = np.arange(ny)[None, :, None]
+    k = np.arange(nz)[:, None, None]
+    nv = OBLIQUE_N
+
+    def x1(xo, yo, zo):
+        return nv[0] * (i + xo) * d + nv[1] * (j + yo) * d + nv[2] * (k + zo) * d
+
+    return (nx, ny, nz), d, x1(0.5, 0.5, 0.5), x1(0.5, 0.0, 0.0), x1(0.0, 0.5, 0.0), x1(0.0, 0.0, 0.5)
+
+
+def _oblique_state(n, rho, p, v_of, b_par, a2_of, a3_of):
+    """State of a 2N x N x N oblique box whose fields depend on x1 = n . x
+    only: v(x1) in grid axes, B = b_par n + curl(A2(x1) e2 + A3(x1) e3)."""
+    shape, d, xc, xex, xey, xez = _oblique_coords(n)
+    W = np.empty((5,) + shape[::-1])
+    W[0] = rho(xc)
+    v = v_of(xc)
+    W[1], W[2], W[3] = v[0], v[1], v[2]
+    W[4] = p(xc)
+    e2, e3 = OBLIQUE_E2, OBLIQUE_E3
+    A = []
+    for ax, xe in enumerate((xex, xey, xez)):
+        A.append(a2_of(xe) * e2[ax] + a3_of(xe) * e3[ax])
+    bx, by, bz = curl_faces(A[0], A[1], A[2], d, d, d)
+    bx = bx + b_par * OBLIQUE_N[0]
+    by = by + b_par * OBLIQUE_N[1]
+    bz = bz + b_par * OBLIQUE_N[2]
+    return State(W=W, bx=bx, by=by, bz=bz, length=(3.0, 1.5, 1.5))
+
+
+def cpaw_box(n, amp=0.1, p=0.1):
+    """Circularly polarised Alfven wave (Sec. "Circularly Polarized Alfven
+    Wave"), an exact nonlinear solution: rho = 1, P = 0.1, v_par = 0,
+    B_par = 1, v_2 = B_2 = amp sin(2 pi x1), v_3 = B_3 = amp cos(2 pi x1), on
+    the oblique 2N x N x N box of size (3, 3/2, 3/2).  With v_perp = B_perp the
+    wave moves along -n at the Alfven speed 1 and returns after t = 1."""
+    tp = 2.0 * math.pi
+    e2, e3 = OBLIQUE_E2, OBLIQUE_E3
+
+    def v_of(x1):
+        s, c = amp * np.sin(tp * x1), amp * np.cos(tp * x1)
+        return [s * e2[a] + c * e3[a] for a in range(3)]
+
+    return _oblique_state(n, lambda x: np.ones_like(x), lambda x: np.full_like(x, p), v_of, 1.0,
+                          lambda x: amp * np.sin(tp * x) / tp, lambda x: amp * np.cos(tp * x) / tp)
+
+
+def field_loop_box(n, amp=1e-3, r0=0.3, v=(2.0, 0.5)):
+    """Advection of a weak field loop (Sec. "Advection of a Field Loop"), 2D:
+    a 2N x N x 1 periodic box [-1, 1] x [-1/2, 1/2] (thin in z), rho = 1,
+    P = 1, v = (2, 0.5, 0), A_z = max(amp (r0 - r), 0) at zone corners."""
+    nx, ny = 2 * n, n
+    dx = 2.0 / nx
+    x = -1.0 + np.arange(nx) * dx
+    y = -0.5 + np.arange(ny) * dx
+    r = np.sqrt(x[None, :] ** 2 + y[:, None] ** 2)
+    Az = np.maximum(amp * (r0 - r), 0.0)[None, :, :]
+    zero = np.zeros((1, ny, nx))
+    dz = 1e3
+    bx, by, bz = curl_faces(zero, zero, Az, dx, dx, dz)
+    W = np.empty((5, 1, ny, nx))
+    W[0] = 1.0
+    W[1] = v[0]
+    W[2] = v[1]
+    W[3] = 0.0
+    W[4] = 1.0
+    return State(W=W, bx=bx, by=by, bz=bz, length=(2.0, 1.0, dz))
+
+
+# Shock-tube states (rho, vx, vy, vz, By, Bz, P) and the normal field Bx
+# (Secs. "RJ95 2a", "RJ95 4a", "Brio & Wu Shock-tube").
+_S4PI = math.sqrt(4.0 * math.pi)
+SHOCK_TUBES = {
+    # the printed 2a left state lists six numbers for seven variables; the
+    # missing one is v_z = 0.5 of the RJ95 problem it reproduces
+    "rj2a": dict(left=(1.08, 1.2, 0.01, 0.5, 3.6 / _S4PI, 2.0 / _S4PI, 0.95),
+                 right=(1.0, 0.0, 0.0, 0.0, 4.0 / _S4PI, 2.0 / _S4PI, 1.0),
+                 bx=2.0 / _S4PI, gamma=5.0 / 3.0, t=0.2),
+    "rj4a": dict(left=(1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 1.0),
+                 right=(0.2, 0.0, 0.0, 0.0, 0.0, 0.0, 0.1),
+                 bx=1.0, gamma=5.0 / 3.0, t=0.15),
+    "briowu": dict(left=(1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 1.0),
+                   right=(0.125, 0.0, 0.0, 0.0, -1.0, 0.0, 0.1),
+                   bx=0.75, gamma=2.0, t=0.08),
+}
+
+
+def shock_tube_1d(name, n):
+    """n x 1 x 1 box on [0, 1] (outflow along x, thin in y and z) with the
+    named shock-tube states on either side of x = 1/2."""
+    st = SHOCK_TUBES[name]
+    x = (np.arange(n) + 0.5) / n
+    left = x < 0.5
+    W = np.empty((5, 1, 1, n))
+    for c, idx in enumerate((0, 1, 2, 3, 6)):
+        W[c, 0, 0] = np.where(left, st["left"][idx], st["right"][idx])
+    by_z = np.where(left, st["left"][4], st["right"][4])
+    bz_z = np.where(left, st["left"][5], st["right"][5])
+    bx = np.full((1, 1, n + 1), st["bx"])
+    by = np.repeat(by_z[None, None, :], 2, axis=1)
+    bz = np.repeat(bz_z[None, None, :], 2, axis=0)
+    return State(W=W, bx=bx, by=by, bz=bz, length=(1.0, 1e3, 1e3))
+
+
+def blast_box(nx, ny, nz, b0=10.0, p_in=100.0, r0=0.125, shift=(0.0, 0.0, 0.0)):
+    """Magnetised strong blast wave (Sec. "MHD Blast Wave"): periodic box of
+    size (1, 3/2, 1) with nx x ny x nz zones, rho = 1 at rest,
+    B = (b0/sqrt2, b0/sqrt2, 0), P = 1 except P = p_in within r0 of the
+    centre.  shift moves the centre by that many zones per axis (an exactly
+    centred blast has symmetry planes on faces, where the mass flux is zero
+    in exact arithmetic)."""
+    L = (1.0, 1.5, 1.0)
+    d = [L[0] / nx, L[1] / ny, L[2] / nz]
+    x = (np.arange(nx) + 0.5 - shift[0]) * d[0] - 0.5 * L[0]
+    y = (np.arange(ny) + 0.5 - shift[1]) * d[1] - 0.5 * L[1]
+    z = (np.arange(nz) + 0.5 - shift[2]) * d[2] - 0.5 * L[2]
+    r = np.sqrt(x[None, None, :] ** 2 + y[None, :, None] ** 2 + z[:, None, None] ** 2)
+    W = np.zeros((5, nz, ny, nx))
+    W[0] = 1.0
+    W[4] = np.where(r < r0, p_in, 1.0)
+    bx = np.full((nz, ny, nx + 1), b0 / math.sqrt(2.0))
+    by = np.full((nz, ny + 1, nx), b0 / math.sqrt(2.0))
+    bz = np.zeros((nz + 1, ny, nx))
+    return State(W=W, bx=bx, by=by, bz=bz, length=L)
 
 
 def mode_table(seed, kmin, kmax, slope=-2.0):

@@ -29,3 +29,31 @@ def state_err(gs, os_):
         else:
             worst = max(worst, rel_err(a, b))
     return worst
+
+
+def vec_err(g, o, guard=1e-3):
+    """rel_err for the components of a vector field (leading axis), the guard
+    taken against the largest component anywhere: a component that is zero
+    in exact arithmetic is then held to the field's scale."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    top = max(np.abs(o).max(), 1e-300)
+    worst = 0.0
+    for c in range(o.shape[0]):
+        scale = np.maximum(np.abs(o[c]), guard * max(np.abs(o[c]).max(), 1e-300))
+        scale = np.maximum(scale, guard * top)
+        worst = max(worst, float(np.max(np.abs(g[c] - o[c]) / scale)))
+    return worst
+
+
+def state_err_vec(gs, os_):
+    """state_err with momentum and zone field compared as vectors (vec_err)
+    and the face fields against the largest face field."""
+    U1, U2 = gs[0], os_[0]
+    worst = max(rel_err(U1[0], U2[0]), rel_err(U1[4], U2[4]), vec_err(U1[1:4], U2[1:4]),
+                vec_err(gs[4], os_[4]))
+    top = max(np.abs(b).max() for b in os_[1:4])
+    for a, b in zip(gs[1:4], os_[1:4]):
+        scale = np.maximum(np.abs(b), 1e-3 * top)
+        worst = max(worst, float(np.max(np.abs(a - b) / scale)))
+    return worst
