@@ -49,7 +49,12 @@ extern "C" {
 
 /* Grid of equal patches (Sec. "Domain Decomposition": a Patch is a
  * self-contained sub-grid with its own 5 boundary zones).
- *  n[d]        global interior zones per axis
+ *  n[d]        global interior zones per axis.  n[2] = 1 with one patch
+ *              along z and periodic z is the 2D problem (Sec. "MHD in Two
+ *              Dimensions"): it is stored as one z plane (z stride 0), so z
+ *              differences vanish exactly and the z sweep is one face per
+ *              column; the zones equal those of the 11-plane 3D storage
+ *              (outflow z) bit for bit.
  *  patches[d]  patches per axis; n[d] must be a multiple of patches[d]
  *  length[d]   box size; dx_d = length[d] / n[d]
  *  gamma       adiabatic index, 1 < gamma <= 2 (Sec. 3)
@@ -66,7 +71,11 @@ extern "C" {
  *              intermediate state of its linearised Riemann problem
  *              w_L + sum_{j<=k} alpha_j r_j, has rho < prot_rho or
  *              P < prot_p.  Independently of the floors, a face whose Roe
- *              state has no real sound speed always takes the HLL flux. */
+ *              state has no real sound speed always takes the HLL flux.
+ *  dt_lag      0: each step's dt comes from its start state; 1: from the
+ *              previous step's start state (the paper delays the dt
+ *              reduction by one step to overlap it with work, Sec. on the
+ *              MPI-RMA engine); the first two steps use the loaded state. */
 typedef struct wb_desc {
   int n[3];
   int patches[3];
@@ -81,6 +90,7 @@ typedef struct wb_desc {
   int batch_patches;
   double prot_rho;
   double prot_p;
+  int dt_lag;
 } wb_desc;
 
 typedef struct wb_counters_t {
@@ -89,7 +99,10 @@ typedef struct wb_counters_t {
   long long unphysical;     /* updated zones found non-finite or with rho <= 0 */
   double t;                 /* simulated time since load */
   double last_dt;           /* dt of the last step */
-  long long hll_faces;      /* faces whose flux came from the HLL fallback */
+  long long hll_faces;      /* face evaluations whose flux came from the HLL
+                               fallback, ghost-zone recomputation included
+                               (so the count depends on patching and on the
+                               one-plane storage of a thin periodic z axis) */
 } wb_counters_t;
 
 typedef struct wb_grid wb_grid;

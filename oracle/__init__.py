@@ -90,7 +90,9 @@ class Grid:
     """One periodic/outflow box evolved by the oracle (single grid, 5 ghosts)."""
 
     def __init__(self, n, length, gamma=5.0 / 3.0, cfl=0.8, bc=(0, 0, 0), eps=DEFAULT_EPS,
-                 sweby=1.0, rho_floor=1e-20, p_floor=1e-20):
+                 sweby=1.0, rho_floor=1e-20, p_floor=1e-20, dt_lag=False):
+        self.dt_lag = bool(dt_lag)
+        self._lag_dt = None   # lagged dt: CFL dt of the previous step's start state
         self.n = tuple(int(x) for x in n)
         self.length = tuple(float(x) for x in length)
         self.gamma = float(gamma)
@@ -119,6 +121,7 @@ class Grid:
         rc = lib().or_load(self._h, _p(U), _p(bx), _p(by), _p(bz))
         if rc:
             raise RuntimeError(f"oracle load failed rc={rc}")
+        self._lag_dt = None
 
     def load_primitive(self, W, bx, by, bz):
         nx, ny, nz = self.n
@@ -130,6 +133,7 @@ class Grid:
         rc = lib().or_load_primitive(self._h, _p(W), _p(bx), _p(by), _p(bz))
         if rc:
             raise RuntimeError(f"oracle load failed rc={rc}")
+        self._lag_dt = None
 
     def load_state(self, st):
         self.load_primitive(st["W"], st["bx"], st["by"], st["bz"])
@@ -151,10 +155,20 @@ class Grid:
         return lib().or_step(self._h, float(dt))
 
     def advance(self, nsteps: int, t_end: float | None = None, dt: float | None = None):
-        """nsteps CFL (or fixed-dt) steps; stops at t_end if given. Returns t."""
+        """nsteps CFL (or fixed-dt) steps; stops at t_end (measured from this
+        call) if given.  With dt_lag each step takes the CFL dt of the previous
+        step's start state (the first two steps after a load both take the
+        loaded state's).  Returns t."""
         t = 0.0
         for _ in range(int(nsteps)):
-            h = self.dt() if dt is None else float(dt)
+            if dt is not None:
+                h = float(dt)
+            else:
+                h = self.dt()
+                if self.dt_lag:
+                    h_now = h
+                    if self._lag_dt is not None:
+                        h = self._lag_dt
             last = False
             if t_end is not None:
                 rem = t_end - t
@@ -167,6 +181,8 @@ class Grid:
             rc = self.step(h)
             if rc:
                 raise RuntimeError(f"oracle step returned {rc}")
+            if dt is None and self.dt_lag:
+                self._lag_dt = h_now
             t = t_end if last else t + h
         return t
 

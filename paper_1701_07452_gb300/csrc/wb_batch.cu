@@ -137,6 +137,7 @@ struct BatchParams {
   unsigned* sync;             // [0] arrivals, [1] generation, [2] error, [3..4] chunk counters
   WbPhys phys;
   double cfl;
+  int dt_lag;                 // dt from the previous step's start state
   int seg_len;
   long long budget;           // barrier wait budget in SM clock cycles
 };
@@ -270,9 +271,14 @@ __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, in
 __device__ void box_dt(const BatchParams& B, int box) {
   WbScalars* s = B.scal + box;
   if (B.steps_left[box] <= 0) { s->dt = 0.0; return; }
-  const double w = __longlong_as_double((long long)s->wmax_next);
+  const double w_now = __longlong_as_double((long long)s->wmax_next);
+  double w = w_now;
+  if (B.dt_lag) {
+    const double wl = __longlong_as_double((long long)s->wmax_lag);
+    if (wl > 0.0) w = wl;
+  }
   const double dt = B.cfl / w;
-  if (!((w > 0.0) && isfinite(w) && isfinite(dt) && dt > 0.0)) {
+  if (!((w > 0.0) && isfinite(w) && isfinite(dt) && dt > 0.0 && w_now > 0.0 && isfinite(w_now))) {
     s->dt = 0.0;
     s->unphysical += 1;
     B.steps_left[box] = 0;
@@ -281,6 +287,7 @@ __device__ void box_dt(const BatchParams& B, int box) {
   s->dt = dt;
   s->t += dt;
   s->steps += 1;
+  if (B.dt_lag) s->wmax_lag = s->wmax_next;
   s->wmax_next = 0ULL;
   B.steps_left[box] -= 1;
 }
@@ -389,6 +396,7 @@ struct wb_batch {
   wb_desc phys_desc;
   WbPhys phys;
   double cfl;
+  int dt_lag = 0;
   cudaStream_t stream;
   char* mem;
   size_t bytes;
@@ -588,6 +596,7 @@ BatchParams params(const wb_batch* b) {
   p.sync = b->d_sync;
   p.phys = b->phys;
   p.cfl = b->cfl;
+  p.dt_lag = b->dt_lag;
   p.seg_len = b->seg_len;
   p.budget = b->budget;
   return p;
@@ -687,6 +696,7 @@ int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes
   b->phys_desc = *physics;
   b->phys = wb_phys_of(physics);
   b->cfl = physics->cfl;
+  b->dt_lag = physics->dt_lag ? 1 : 0;
   b->stream = reinterpret_cast<cudaStream_t>(stream);
   b->mem = reinterpret_cast<char*>(dev_mem);
   b->bytes = bytes;

@@ -83,6 +83,15 @@ bool valid_desc(const wb_desc* d, std::string* why) {
   return true;
 }
 
+// A box one zone thick along z with periodic z is the 2D problem of
+// Sec. "MHD in Two Dimensions": every z layer, ghosts included, holds the
+// same values, so it is stored as one plane with z stride 0.  Reads at
+// k +- 1 then see that plane, z flux and EMF differences vanish exactly, and
+// the z sweep reduces to one face per pencil (the flux of a z-uniform state).
+bool flat_z(const wb_desc* d) {
+  return d->n[2] == 1 && d->patches[2] == 1 && d->bc[2] == WB_BC_PERIODIC;
+}
+
 WbGeo make_geo(const wb_desc* d) {
   WbGeo g;
   for (int a = 0; a < 3; ++a) {
@@ -93,7 +102,11 @@ WbGeo make_geo(const wb_desc* d) {
   }
   g.sy = g.pd[0];
   g.sz = (long long)g.pd[0] * g.pd[1];
-  g.V = g.sz * g.pd[2];
+  if (flat_z(d)) {
+    g.pd[2] = 1;
+    g.sz = 0;
+  }
+  g.V = (long long)g.pd[0] * g.pd[1] * g.pd[2];
   return g;
 }
 
@@ -223,6 +236,11 @@ void enqueue_pass(wb_grid* g, long long p0, int nslots) {
   cudaStream_t s = g->stream;
   StageArgs A = stage_args(g, p0, nslots);
   const int N0 = g->geo.n[0], N1 = g->geo.n[1], N2 = g->geo.n[2];
+  // one plane for a flat-z (2D) box: every region's z range is layer 0
+  const bool flat = g->geo.sz == 0;
+  auto box = [flat](int l0, int h0, int l1, int h1, int l2, int h2) {
+    return flat ? ::box(l0, h0, l1, h1, 0, 0) : ::box(l0, h0, l1, h1, l2, h2);
+  };
   // Step 1: predictor fluxes from q^n
   sweep(g, 0, sweep_args(g, A, 0, false, box(-3, N0 + 3, -4, N1 + 3, -4, N2 + 3)), nslots);
   sweep(g, 1, sweep_args(g, A, 1, false, box(-4, N0 + 3, -3, N1 + 3, -4, N2 + 3)), nslots);
@@ -482,7 +500,7 @@ int wb_advance(wb_grid* g, int nsteps, double t_end, double* t_out) {
       if (e != cudaSuccess) return check_cuda(g, e, "advance");
       if (t_now >= t_end) break;
     }
-    wb_launch_dt_step(g->scal, g->d.cfl, t_end, s);
+    wb_launch_dt_step(g->scal, g->d.cfl, t_end, g->d.dt_lag, s);
     for (long long p0 = 0; p0 < g->npatch; p0 += g->S) {
       int ns = (int)std::min<long long>(g->S, g->npatch - p0);
       enqueue_pass(g, p0, ns);
@@ -817,7 +835,7 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
   wb_launch_ccb(g.q, g.b, g.geo, 1, s);
   wb_launch_halo(g.q, g.b, g.geo, g.map, s);
   wb_launch_dt_init(g.q, g.geo, 1, g.phys, g.scal, s);
-  wb_launch_dt_step(g.scal, one.cfl, 0.0, s);
+  wb_launch_dt_step(g.scal, one.cfl, 0.0, 0, s);
   enqueue_pass(&g, 0, 1);
   wb_launch_halo(g.q, g.b, g.geo, g.map, s);
   double* outs[3] = {bx_out, by_out, bz_out};

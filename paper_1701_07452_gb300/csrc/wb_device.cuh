@@ -48,7 +48,7 @@ struct WbBox {
 struct WbScalars {
   double dt;              // dt of the current step (0 = skip)
   double t;               // time since load
-  unsigned long long wmax_bits;  // max signal rate of the state (bits of a double >= 0)
+  unsigned long long wmax_lag;   // lagged dt: signal rate of the previous step's start state (0: none)
   unsigned long long wmax_next;  // accumulated by the final update for the next step
   long long steps;
   long long floor_hits;

@@ -54,7 +54,7 @@ void wb_launch_halo(double* const q[8], double* const b[3], const WbGeo& geo, co
                     cudaStream_t s);
 void wb_launch_dt_init(double* const q[8], const WbGeo& geo, long long npatch, const WbPhys& ph,
                        WbScalars* scal, cudaStream_t s);
-void wb_launch_dt_step(WbScalars* scal, double cfl, double t_end, cudaStream_t s);
+void wb_launch_dt_step(WbScalars* scal, double cfl, double t_end, int lag, cudaStream_t s);
 void wb_launch_ccb(double* const q[8], double* const b[3], const WbGeo& geo, long long npatch,
                    cudaStream_t s);
 void wb_launch_prim_to_cons(double* const q[8], const WbGeo& geo, long long npatch,

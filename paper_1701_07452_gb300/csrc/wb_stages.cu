@@ -134,7 +134,7 @@ __global__ void k_halo(StageArgs A, GridMap m) {
   int i = (int)(t % g.pd[0]) - WB_NG;
   long long r = t / g.pd[0];
   int j = (int)(r % g.pd[1]) - WB_NG;
-  int k = (int)(r / g.pd[1]) - WB_NG;
+  int k = g.sz == 0 ? 0 : (int)(r / g.pd[1]) - WB_NG;  // a flat-z box has one plane
   int loc[3] = {i, j, k};
   if (i >= 0 && i < g.n[0] && j >= 0 && j < g.n[1] && k >= 0 && k < g.n[2]) return;
   long long pc[3];
@@ -182,11 +182,19 @@ __global__ void k_dt_init(StageArgs A, long long npatch) {
   block_max_atomic(w, &A.v.scal->wmax_next);
 }
 
-// dt of the next step from the signal rate of its start state (reading R3)
-__global__ void k_dt_step(WbScalars* s, double cfl, double t_end) {
-  double w = __longlong_as_double((long long)s->wmax_next);
+// dt of the next step from the signal rate of its start state (reading R3),
+// or with lag from the rate of the previous step's start state (the paper
+// delays the dt reduction by one step to overlap it with work; the first two
+// steps both use the loaded state's rate)
+__global__ void k_dt_step(WbScalars* s, double cfl, double t_end, int lag) {
+  const double w_now = __longlong_as_double((long long)s->wmax_next);
+  double w = w_now;
+  if (lag) {
+    const double wl = __longlong_as_double((long long)s->wmax_lag);
+    if (wl > 0.0) w = wl;
+  }
   double dt = cfl / w;
-  bool ok = (w > 0.0) && isfinite(w) && isfinite(dt) && dt > 0.0;
+  bool ok = (w > 0.0) && isfinite(w) && isfinite(dt) && dt > 0.0 && (w_now > 0.0) && isfinite(w_now);
   bool last = false;
   if (t_end > 0.0) {
     double rem = t_end - s->t;
@@ -203,6 +211,7 @@ __global__ void k_dt_step(WbScalars* s, double cfl, double t_end) {
   }
   s->dt = dt;
   s->t = last ? t_end : s->t + dt;
+  if (lag) s->wmax_lag = s->wmax_next;
   s->steps += 1;
   s->wmax_next = 0ULL;
 }
@@ -375,8 +384,8 @@ void wb_launch_dt_init(double* const q[8], const WbGeo& geo, long long npatch, c
   k_dt_init<<<grid_for(n, 1, 256), 256, 0, s>>>(a, npatch);
 }
 
-void wb_launch_dt_step(WbScalars* scal, double cfl, double t_end, cudaStream_t s) {
-  k_dt_step<<<1, 1, 0, s>>>(scal, cfl, t_end);
+void wb_launch_dt_step(WbScalars* scal, double cfl, double t_end, int lag, cudaStream_t s) {
+  k_dt_step<<<1, 1, 0, s>>>(scal, cfl, t_end, lag);
 }
 
 void wb_launch_ccb(double* const q[8], double* const b[3], const WbGeo& geo, long long npatch,

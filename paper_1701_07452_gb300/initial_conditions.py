@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = ["random_box", "turbulence_box", "turbulence_box_device", "expansion_box", "mode_table",
            "curl_faces", "cpaw_box", "field_loop_box", "shock_tube_1d", "blast_box", "SHOCK_TUBES",
-           "State"]
+           "orszag_tang_box", "random_box_2d", "State"]
 
 
 class State(dict):
@@ -172,6 +172,43 @@ def field_loop_box(n, amp=1e-3, r0=0.3, v=(2.0, 0.5)):
     W[3] = 0.0
     W[4] = 1.0
     return State(W=W, bx=bx, by=by, bz=bz, length=(2.0, 1.0, dz))
+
+
+def orszag_tang_box(n, v0=1.0):
+    """Orszag-Tang vortex (Sec. "Orszag-Tang Vortex"), 2D: periodic unit box
+    [-1/2, 1/2]^2 with n x n x 1 zones (thin in z), rho = 25/(36 pi),
+    P = 5/(12 pi), v = v0 (-sin 2 pi y, sin 2 pi x, 0), field from the corner
+    potential A_z = B0 [cos(4 pi x)/2 + cos(2 pi y)] / (2 pi), B0 = 1/sqrt(4 pi)."""
+    d = 1.0 / n
+    xc = -0.5 + (np.arange(n) + 0.5) * d
+    x = -0.5 + np.arange(n) * d
+    b0 = 1.0 / math.sqrt(4.0 * math.pi)
+    Az = b0 * (np.cos(4.0 * math.pi * x)[None, :] / 2.0 + np.cos(2.0 * math.pi * x)[:, None]) / (2.0 * math.pi)
+    zero = np.zeros((1, n, n))
+    dz = 1e3
+    bx, by, bz = curl_faces(zero, zero, Az[None, :, :], d, d, dz)
+    W = np.empty((5, 1, n, n))
+    W[0] = 25.0 / (36.0 * math.pi)
+    W[1] = -v0 * np.sin(2.0 * math.pi * xc)[None, :, None]
+    W[2] = v0 * np.sin(2.0 * math.pi * xc)[None, None, :]
+    W[3] = 0.0
+    W[4] = 5.0 / (12.0 * math.pi)
+    return State(W=W, bx=bx, by=by, bz=bz, length=(1.0, 1.0, dz))
+
+
+def random_box_2d(nx, ny, seed):
+    """2.5D random box, one zone thick in z: every field, v_z and B_z
+    included, varies in x and y only (dx = 1)."""
+    rng = np.random.default_rng(seed)
+    shape = (1, ny, nx)
+    W = np.empty((5,) + shape)
+    W[0] = 1.0 + 0.1 * rng.uniform(-1.0, 1.0, shape)
+    for c in (1, 2, 3):
+        W[c] = rng.uniform(-0.2, 0.2, shape)
+    W[4] = 0.6 + 0.05 * rng.uniform(-1.0, 1.0, shape)
+    A = [0.05 * rng.uniform(-1.0, 1.0, shape) for _ in range(3)]
+    bx, by, bz = curl_faces(A[0], A[1], A[2], 1.0, 1.0, 1.0)
+    return State(W=W, bx=bx + 0.3, by=by + 0.2, bz=bz + 0.25, length=(float(nx), float(ny), 1.0))
 
 
 # Shock-tube states (rho, vx, vy, vz, By, Bz, P) and the normal field Bx

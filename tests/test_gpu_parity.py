@@ -152,3 +152,16 @@ def test_fp64_reciprocal_helpers_match_cuda(wb):
     e_rcp, e_rsq = g.selftest_math(1 << 22)
     assert e_rcp < 4.5e-16, e_rcp
     assert e_rsq < 4.5e-16, e_rsq
+
+
+def test_lagged_dt_parity(wb, oracle_mod):
+    from paper_1701_07452_gb300.initial_conditions import random_box
+    st = random_box(12, seed=21)
+    g, o = make_pair(wb, oracle_mod, st, (12, 12, 12), dt_lag=True)
+    d0 = o.dt()
+    g.advance(2)
+    o.advance(2)
+    assert abs(g.counters()["last_dt"] - d0) <= 1e-14 * d0
+    g.advance(18)
+    o.advance(18)
+    assert state_err(g.read(), o.read()) < 1e-10

@@ -217,3 +217,21 @@ def test_linear_wave_second_order_1d(oracle_mod, mode):
     slope = math.log2(errs[1] / errs[2])
     assert errs[0] > errs[1] > errs[2]
     assert slope > 1.7, (errs, slope)
+
+
+def test_lagged_dt_sequence(oracle_mod):
+    """dt_lag: step n takes the CFL dt of the start state of step n-1 (the
+    paper delays the dt reduction by one step); steps 0 and 1 both take the
+    loaded state's."""
+    from paper_1701_07452_gb300.initial_conditions import random_box
+    st = random_box(8, seed=9)
+    g = oracle_mod.Grid((8, 8, 8), st["length"], dt_lag=True)
+    g.load_state(st)
+    cfl_dts, used = [], []
+    for _ in range(5):
+        cfl_dts.append(g.dt())
+        used.append(g.advance(1))
+    assert used[0] == cfl_dts[0] and used[1] == cfl_dts[0]
+    for n in range(2, 5):
+        assert used[n] == cfl_dts[n - 1]
+    assert len(set(cfl_dts)) == 5   # the state's rate changes, so the lag matters
