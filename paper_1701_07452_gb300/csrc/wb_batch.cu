@@ -46,7 +46,7 @@ __host__ __device__ inline WbBox bxx(int l0, int h0, int l1, int h1, int l2, int
 
 __host__ __device__ inline int stage_nsub(int s) {
   return (s == BS_PRED || s == BS_CORR || s == BS_EDGE_P || s == BS_EDGE_C || s == BS_CT_H ||
-          s == BS_CT_F || s == BS_TRANS) ? 3 : 1;
+          s == BS_CT_F) ? 3 : 1;
 }
 
 __host__ __device__ inline bool stage_is_sweep(int s) { return s == BS_PRED || s == BS_CORR; }
@@ -68,10 +68,8 @@ __host__ __device__ inline WbBox stage_box(int s, int d, const int* n) {
       if (d == 0) return bxx(-3, N0 + 3, -1, N1, -1, N2);
       if (d == 1) return bxx(-1, N0, -3, N1 + 3, -1, N2);
       return bxx(-1, N0, -1, N1, -3, N2 + 3);
-    case BS_TRANS:
-      if (d == 0) return bxx(-3, N0 + 2, -1, N1, -1, N2);
-      if (d == 1) return bxx(-1, N0, -3, N1 + 2, -1, N2);
-      return bxx(-1, N0, -1, N1, -3, N2 + 2);
+    case BS_TRANS:  // union of the three directions' boxes; trans_mask picks per zone
+      return bxx(-3, N0 + 2, -3, N1 + 2, -3, N2 + 2);
     case BS_CORR:
       if (d == 0) return bxx(-1, N0 + 1, -1, N1, -1, N2);
       if (d == 1) return bxx(-1, N0, -1, N1 + 1, -1, N2);
@@ -89,6 +87,20 @@ __host__ __device__ inline WbBox stage_box(int s, int d, const int* n) {
     case BS_HALO: return bxx(-WB_NG, N0 + WB_NG - 1, -WB_NG, N1 + WB_NG - 1, -WB_NG, N2 + WB_NG - 1);
     default: return bxx(0, 0, 0, 0, 0, 0);
   }
+}
+
+// Directions whose transverse-predictor state (Steps 5, 7) zone (i,j,k)
+// needs: bit d when the zone lies in [-3, N_d + 2] along d and [-1, N_e] along
+// the other axes e (the grid path's boxes).
+__host__ __device__ inline int trans_mask(const int* n, int i, int j, int k) {
+  const int x[3] = {i, j, k};
+  bool core[3], wide[3];
+  for (int a = 0; a < 3; ++a) {
+    core[a] = x[a] >= -1 && x[a] <= n[a];
+    wide[a] = x[a] >= -3 && x[a] <= n[a] + 2;
+  }
+  return ((wide[0] && core[1] && core[2]) ? 1 : 0) | ((core[0] && wide[1] && core[2]) ? 2 : 0) |
+         ((core[0] && core[1] && wide[2]) ? 4 : 0);
 }
 
 __host__ __device__ inline long long box_cnt(const WbBox& b) {
@@ -250,11 +262,11 @@ __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, in
       else wbu::ct<2>(v, 0, 0, fin, dt, i, j, k);
       break;
     }
-    case BS_TRANS:
-      if (d == 0) wbu::transverse<0>(v, 0, 0, dt, i, j, k);
-      else if (d == 1) wbu::transverse<1>(v, 0, 0, dt, i, j, k);
-      else wbu::transverse<2>(v, 0, 0, dt, i, j, k);
+    case BS_TRANS: {
+      const int mask = trans_mask(n, i, j, k);
+      if (mask) wbu::transverse_set(v, 0, 0, dt, mask, i, j, k);
       break;
+    }
     case BS_EREF_H: wbu::eref_half(v, 0, 0, dt, i, j, k); break;
     case BS_FINAL: {
       const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, hits, bad);

@@ -85,18 +85,18 @@ __device__ __forceinline__ double wb_minmod(double a, double b) {
 __device__ __forceinline__ double wb_rcp(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  double p = fma(e, e, e);
-  return fma(y, p, y);
+  double e = __fma_rn(-x, y, 1.0);
+  double p = __fma_rn(e, e, e);
+  return __fma_rn(y, p, y);
 }
 
 __device__ __forceinline__ double wb_rsqrt(double x) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double h = x * y;
-  double e = fma(-h, y, 1.0);
-  double p = fma(0.375, e, 0.5);
-  return fma(y * e, p, y);
+  double h = __dmul_rn(x, y);
+  double e = __fma_rn(-h, y, 1.0);
+  double p = __fma_rn(0.375, e, 0.5);
+  return __fma_rn(__dmul_rn(y, e), p, y);
 }
 
 // Comparisons on the IEEE bit patterns (integer pipe; the FP64 pipe is the
@@ -131,6 +131,30 @@ __device__ __forceinline__ double wb_clamp01(double x) {
   if (b <= 0) return 0.0;                                 // negative or zero
   return b > 0x3ff0000000000000LL ? 1.0 : x;              // above 1 (or NaN -> 1)
 }
+
+// x / 2^s for s = 1, 2 on the integer pipe: the exponent field is lowered by
+// s, which is exact for every normal x whose quotient is normal.  Inputs
+// below 2^(s-1022) in magnitude (zero, subnormals, the lowest binades) give a
+// zero of the same sign instead of a subnormal; inf and NaN pass unchanged.
+template <int S>
+__device__ __forceinline__ double wb_pow2_div(double x) {
+  const int hi = __double2hiint(x);
+  const int lo = __double2loint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  int h = hi & (int)0x80000000;
+  int l = 0;
+  if (ex > S) {
+    h = hi - (S << 20);
+    l = lo;
+  }
+  if (ex == 0x7ff) {
+    h = hi;
+    l = lo;
+  }
+  return __hiloint2double(h, l);
+}
+__device__ __forceinline__ double wb_half(double x) { return wb_pow2_div<1>(x); }
+__device__ __forceinline__ double wb_quarter(double x) { return wb_pow2_div<2>(x); }
 
 // +1 for x >= 0 (including -0.0), -1 for x < 0
 __device__ __forceinline__ double wb_sgn(double x) { return wb_neg(x) ? -1.0 : 1.0; }

@@ -46,6 +46,10 @@ __device__ __forceinline__ double ld(const double* p) {
   return *p;
 }
 
+// Zone state of a sweep.  The arithmetic is written with explicit rounding
+// (no contraction left to the compiler): a zone is loaded both before and
+// inside the march over a segment, and the two inlined copies must round
+// identically, or a face's flux would depend on where a segment starts.
 template <int D, bool NC>
 __device__ __forceinline__ void load_cell(const double* const* q, long long off, const WbPhys& P,
                                           Cell& c) {
@@ -59,34 +63,36 @@ __device__ __forceinline__ void load_cell(const double* const* q, long long off,
   c.bt1 = ld<NC>(q[F_BX + T1] + off);
   c.bt2 = ld<NC>(q[F_BX + T2] + off);
   c.isr = wb_rsqrt(c.rho);
-  c.ir = c.isr * c.isr;
-  c.sr = c.rho * c.isr;
-  c.vn = c.mn * c.ir;
-  c.vt1 = c.mt1 * c.ir;
-  c.vt2 = c.mt2 * c.ir;
-  const double ke = 0.5 * (c.mn * c.vn + c.mt1 * c.vt1 + c.mt2 * c.vt2);
-  const double bt2 = c.bt1 * c.bt1 + c.bt2 * c.bt2;
-  const double bn2 = bn * bn;
-  const double me = 0.5 * (bn2 + bt2);
-  const double p = P.gm1 * (e - ke - me);
-  const double pstar = p + me;
-  c.eref = e - 0.5 * bn2;
-  c.hr = (P.g_over_gm1 * p + ke + bt2) * c.ir;
+  c.ir = __dmul_rn(c.isr, c.isr);
+  c.sr = __dmul_rn(c.rho, c.isr);
+  c.vn = __dmul_rn(c.mn, c.ir);
+  c.vt1 = __dmul_rn(c.mt1, c.ir);
+  c.vt2 = __dmul_rn(c.mt2, c.ir);
+  const double ke = wb_half(__fma_rn(c.mt2, c.vt2, __fma_rn(c.mt1, c.vt1, __dmul_rn(c.mn, c.vn))));
+  const double bt2 = __fma_rn(c.bt2, c.bt2, __dmul_rn(c.bt1, c.bt1));
+  const double bn2 = __dmul_rn(bn, bn);
+  const double me = wb_half(__dadd_rn(bn2, bt2));
+  const double p = __dmul_rn(P.gm1, __dsub_rn(__dsub_rn(e, ke), me));
+  const double pstar = __dadd_rn(p, me);
+  c.eref = __dsub_rn(e, wb_half(bn2));
+  c.hr = __dmul_rn(__dadd_rn(__fma_rn(P.g_over_gm1, p, ke), bt2), c.ir);
   // half fluxes: the face needs (F_L + F_R) / 2
-  const double hmn = 0.5 * c.mn, hvn = 0.5 * c.vn, hbn = 0.5 * bn;
+  const double hmn = wb_half(c.mn), hvn = wb_half(c.vn), hbn = wb_half(bn);
   c.F[0] = hmn;
-  c.F[1] = fma(hmn, c.vn, 0.5 * (pstar - bn2));
-  c.F[2] = hmn * c.vt1 - hbn * c.bt1;
-  c.F[3] = hmn * c.vt2 - hbn * c.bt2;
-  c.F[4] = c.bt1 * hvn - hbn * c.vt1;
-  c.F[5] = c.bt2 * hvn - hbn * c.vt2;
-  c.F[6] = (e + pstar) * hvn - hbn * (bn * c.vn + c.bt1 * c.vt1 + c.bt2 * c.vt2);
+  c.F[1] = __fma_rn(hmn, c.vn, wb_half(__dsub_rn(pstar, bn2)));
+  c.F[2] = __fma_rn(hmn, c.vt1, __dmul_rn(-hbn, c.bt1));
+  c.F[3] = __fma_rn(hmn, c.vt2, __dmul_rn(-hbn, c.bt2));
+  c.F[4] = __fma_rn(c.bt1, hvn, __dmul_rn(-hbn, c.vt1));
+  c.F[5] = __fma_rn(c.bt2, hvn, __dmul_rn(-hbn, c.vt2));
+  const double bv = __fma_rn(c.bt2, c.vt2, __fma_rn(c.bt1, c.vt1, __dmul_rn(bn, c.vn)));
+  c.F[6] = __fma_rn(__dadd_rn(e, pstar), hvn, __dmul_rn(-hbn, bv));
 }
 
 // Per-face record (shared memory, structure of arrays over the block).
-// R_PG = rho a^2 / (gamma-1); R_KX = v^2/2 + (gamma-2)/(gamma-1) X.
+// R_PG = rho a^2 / (gamma-1); R_KX = v^2/2 + (gamma-2)/(gamma-1) X;
+// R_AFCF = alpha_f c_f, R_ASCS = alpha_s c_s.
 enum {
-  R_AL = 0, R_NU = 7, R_RHO = 14, R_SRHO, R_A, R_PG, R_CF, R_CS, R_AF, R_AS, R_B1, R_B2, R_S,
+  R_AL = 0, R_NU = 7, R_RHO = 14, R_SRHO, R_A, R_PG, R_CF, R_ASCS, R_AFCF, R_AF, R_AS, R_B1, R_B2, R_S,
   R_VN, R_VT1, R_VT2, R_BT1, R_BT2, R_KX, R_FAVG, R_WORDS = R_FAVG + 7
 };
 
@@ -197,7 +203,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   const double H = fma(b2, irho, wL * L.hr + wR * R.hr);
   const double dbt1 = R.bt1 - L.bt1, dbt2 = R.bt2 - L.bt2;
   const double gX = P.hgm2 * ((dbt1 * dbt1 + dbt2 * dbt2) * (iD * iD));  // (gamma-2) X
-  const double hv2 = 0.5 * (vn * vn + vt1 * vt1 + vt2 * vt2);
+  const double hv2 = wb_half(vn * vn + vt1 * vt1 + vt2 * vt2);
   const double bt2s = bt1 * bt1 + bt2 * bt2;
   const double a2 = P.gm1 * (H - hv2 - (b2 + bt2s) * irho) - gX;
   if (!wb_normal_pos(a2)) return 2;
@@ -212,7 +218,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
     rsd = wb_rsqrt(disc);
     sd = disc * rsd;
   }
-  const double cf2 = 0.5 * (sum + sd);
+  const double cf2 = wb_half(sum + sd);
   const double icf = wb_rsqrt(cf2);
   const double ia = wb_rsqrt(a2);
   const double a = a2 * ia;
@@ -236,8 +242,8 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
       const double den = n1 ? sd - t1 : sd - t2;
       qd = num * wb_rcp(den);
     }
-    const double cf2_a2 = n1 ? qd : 0.5 * (t1 + sd);
-    const double cf2_ca2 = n2 ? qd : 0.5 * (t2 + sd);
+    const double cf2_a2 = n1 ? qd : wb_half(t1 + sd);
+    const double cf2_ca2 = n2 ? qd : wb_half(t2 + sd);
     const double af2 = wb_clamp01(a2 * cf2_ca2 * (icf * icf) * rsd);
     const double as2 = wb_clamp01(cf2_a2 * rsd);
     // subnormal squares (from underflowing transverse fields) count as 0
@@ -268,7 +274,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   const double dvbS = wb_xsgn(b1n * dvt1 + b2n * dvt2, S), dvp = -b2n * dvt1 + b1n * dvt2;
   const double dbb = b1n * dbt1 + b2n * dbt2, dbpS = wb_xsgn(-b2n * dbt1 + b1n * dbt2, S);
   const double ia2 = ia * ia;
-  const double hir = 0.5 * irho, hisr = 0.5 * isrho;
+  const double hir = wb_half(irho), hisr = wb_half(isrho);
   const double i2ra = hisr * ia;         // 1 / (2 sqrt(rho) a)
   const double ri2a2 = hir * ia2;        // 1 / (2 rho a^2)
   const double dpr = dp * ri2a2;
@@ -294,10 +300,10 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
     const double nu = nuk[k];
     f[R_AL + k] = al[k];
     f[R_NU + k] = nu;
-    gt[k] = Qk_m_nu2<EZ>(nu, k, P) * (0.5 * al[k]);
+    gt[k] = Qk_m_nu2<EZ>(nu, k, P) * wb_half(al[k]);
   }
   f[R_RHO] = rho; f[R_SRHO] = srho; f[R_A] = a; f[R_PG] = ra2 * P.inv_gm1; f[R_CF] = cf;
-  f[R_CS] = cs; f[R_AF] = af; f[R_AS] = as; f[R_B1] = b1n; f[R_B2] = b2n; f[R_S] = S;
+  f[R_ASCS] = ascs; f[R_AFCF] = afcf; f[R_AF] = af; f[R_AS] = as; f[R_B1] = b1n; f[R_B2] = b2n; f[R_S] = S;
   f[R_VN] = vn; f[R_VT1] = vt1; f[R_VT2] = vt2; f[R_BT1] = bt1; f[R_BT2] = bt2;
   f[R_KX] = fma(gX, P.inv_gm1, hv2);
 #pragma unroll
@@ -333,14 +339,14 @@ __device__ __forceinline__ void face_flux(const Rec& f, const double gi[7], cons
   double be[7];
 #pragma unroll
   for (int k = 0; k < 7; ++k) be[k] = beta_k<EZ>(f[R_AL + k], f[R_NU + k], gi[k], gi1[k], k, P);
-  const double rho = f[R_RHO], af = f[R_AF], as = f[R_AS], cf = f[R_CF], cs = f[R_CS];
+  const double rho = f[R_RHO], af = f[R_AF], as = f[R_AS];
   const double S = f[R_S], b1 = f[R_B1], b2 = f[R_B2];
   // sum_k beta_k r_k in w = (rho, vn, vt, Bt, p)
   const double sf = be[0] + be[6], df = be[6] - be[0];
   const double ss = be[2] + be[4], ds = be[4] - be[2];
   const double tfs = af * sf + as * ss;
   const double wr = rho * tfs + be[3];
-  const double afcf = af * cf, ascs = as * cs;
+  const double afcf = f[R_AFCF], ascs = f[R_ASCS];
   const double wvn = afcf * df + ascs * ds;
   const double vb = wb_xsgn(afcf * ds - ascs * df, S);   // along beta
   const double vp = be[1] + be[5];                       // along beta-perp
@@ -463,11 +469,18 @@ __device__ __forceinline__ void eref(const WbView& v, long long qo, long long wo
   v.Eref[2][w] = vy * bx - vx * by;
 }
 
-// value upwind of the mass flux m: from the minus-side zone if m > 0, the
-// plus-side zone if m < 0, their mean if m = 0 (rare: a branch, not a select)
-__device__ __forceinline__ double upwind(double m, double xm, double x0) {
-  double d = wb_neg(m) ? x0 : xm;
-  if (wb_zero(m)) d = 0.5 * (xm + x0);
+// Difference x - y upwind of the mass flux m: (xm - ym) from the minus-side
+// zone if m > 0, (x0 - y0) from the plus-side zone if m < 0, the mean of both
+// if m = 0.  The operands are selected first (integer pipe), so one FP64
+// subtraction is spent; the mean is taken only by warps in which some lane
+// has a zero mass flux, so the common case carries none of its arithmetic.
+__device__ __forceinline__ double upwind_diff(double m, double xm, double ym, double x0, double y0) {
+  const bool minus = wb_neg(m);
+  double d = (minus ? x0 : xm) - (minus ? y0 : ym);
+  const bool zero = wb_zero(m);
+  if (__any_sync(__activemask(), zero)) {
+    if (zero) d = 0.5 * ((xm - ym) + (x0 - y0));
+  }
   return d;
 }
 
@@ -494,12 +507,12 @@ __device__ __forceinline__ void edge(const WbView& v, long long wo, bool corr, i
   const double ma_0 = Fa[F_RHO][o], ma_m = Fa[F_RHO][o - sb];
   const double mb_0 = Fb[F_RHO][o], mb_m = Fb[F_RHO][o - sa];
   const double R00 = Er[o], Rm0 = Er[o - sa], R0m = Er[o - sb], Rmm = Er[o - sa - sb];
-  const double db_hi = upwind(ma_0, Rm0 - Eb_m, R00 - Eb_0);
-  const double db_lo = upwind(ma_m, Eb_m - Rmm, Eb_0 - R0m);
-  const double da_hi = upwind(mb_0, R0m - Ea_m, R00 - Ea_0);
-  const double da_lo = upwind(mb_m, Ea_m - Rmm, Ea_0 - Rm0);
+  const double db_hi = upwind_diff(ma_0, Rm0, Eb_m, R00, Eb_0);
+  const double db_lo = upwind_diff(ma_m, Eb_m, Rmm, Eb_0, R0m);
+  const double da_hi = upwind_diff(mb_0, R0m, Ea_m, R00, Ea_0);
+  const double da_lo = upwind_diff(mb_m, Ea_m, Rmm, Ea_0, Rm0);
   double* out = corr ? v.Eedgeh[C] : v.Eedge[C];
-  out[o] = 0.25 * ((Ea_0 + Ea_m) + (Eb_0 + Eb_m) + (db_lo - db_hi) + (da_lo - da_hi));
+  out[o] = wb_quarter((Ea_0 + Ea_m) + (Eb_0 + Eb_m) + (db_lo - db_hi) + (da_lo - da_hi));
 }
 
 // Steps 4 and 11: b_out = b_in - tau curl E on the faces normal to D.
@@ -515,7 +528,7 @@ __device__ __forceinline__ void ct(const WbView& v, long long qo, long long wo, 
   const long long sb = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
   const double* Eb = fin ? v.Eedgeh[b] : v.Eedge[b];
   const double* Ea = fin ? v.Eedgeh[a] : v.Eedge[a];
-  const double tau = fin ? dt : 0.5 * dt;
+  const double tau = fin ? dt : wb_half(dt);
   const double curl = (Eb[w + sa] - Eb[w]) * g.idx[a] - (Ea[w + sb] - Ea[w]) * g.idx[b];
   const double bn = v.b[D][q] - tau * curl;
   if (fin) v.b[D][q] = bn;
@@ -525,106 +538,81 @@ __device__ __forceinline__ void ct(const WbView& v, long long qo, long long wo, 
 // Steps 5 and 7: q^{n+1/2}_D = q^n - dt/2 (transverse flux divergence)
 // + dt/2 S_D, zone B_D := mean of b_D^{n+1/2}, with the GS08-type div B
 // source S_D built from face differences of b^n and minmod pairings.
-template <int D>
-__device__ __forceinline__ void transverse(const WbView& v, long long qo, long long wo, double dt,
-                                           int i, int j, int k) {
-  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
-  const WbGeo& g = v.geo;
-  const long long q = qo + wb_at(g, i, j, k);
-  const long long w = wo + wb_at(g, i, j, k);
-  const long long s[3] = {1, g.sy, g.sz};
-  const double hdt = 0.5 * dt;
-  const double ir = wb_rcp(v.q[F_RHO][q]);
-  double vv[3], B[3], db[3];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    vv[e] = v.q[F_MX + e][q] * ir;
-    B[e] = v.q[F_BX + e][q];
-    db[e] = (v.b[e][q + s[e]] - v.b[e][q]) * g.idx[e];
-  }
-  const double m2 = wb_minmod(db[D], -db[t1]);  // for the t2 field component
-  const double m1 = wb_minmod(db[D], -db[t2]);  // for the t1 field component
-  double S[8];
-  S[F_RHO] = 0.0;
-#pragma unroll
-  for (int e = 0; e < 3; ++e) S[F_MX + e] = B[e] * db[D];
-  S[F_EN] = B[D] * vv[D] * db[D] + B[t1] * vv[t1] * m1 + B[t2] * vv[t2] * m2;
-  S[F_BX + D] = 0.0;
-  S[F_BX + t1] = vv[t1] * m1;
-  S[F_BX + t2] = vv[t2] * m2;
-  const double c1 = hdt * g.idx[t1], c2 = hdt * g.idx[t2];
-  // rho: no source; momentum and energy: both transverse fluxes and the
-  // source; B_t1 (B_t2): only the t2 (t1) sweep carries it
-  v.qh[D][F_RHO][w] = v.q[F_RHO][q] - ((v.Fp[t1][F_RHO][w + s[t1]] - v.Fp[t1][F_RHO][w]) * c1 +
-                                       (v.Fp[t2][F_RHO][w + s[t2]] - v.Fp[t2][F_RHO][w]) * c2);
-#pragma unroll
-  for (int c = F_MX; c <= F_EN; ++c) {
-    const double d1 = (v.Fp[t1][c][w + s[t1]] - v.Fp[t1][c][w]) * c1;
-    const double d2 = (v.Fp[t2][c][w + s[t2]] - v.Fp[t2][c][w]) * c2;
-    v.qh[D][c][w] = v.q[c][q] - (d1 + d2) + hdt * S[c];
-  }
-  v.qh[D][F_BX + t1][w] = v.q[F_BX + t1][q] - (v.Fp[t2][F_BX + t1][w + s[t2]] - v.Fp[t2][F_BX + t1][w]) * c2 +
-                          hdt * S[F_BX + t1];
-  v.qh[D][F_BX + t2][w] = v.q[F_BX + t2][q] - (v.Fp[t1][F_BX + t2][w + s[t1]] - v.Fp[t1][F_BX + t2][w]) * c1 +
-                          hdt * S[F_BX + t2];
-  v.qh[D][F_BX + D][w] = 0.5 * (v.bh[D][w] + v.bh[D][w + s[D]]);
-}
-
-// Steps 5 and 7 for the directions in mask (bit d) at one zone, sharing the
-// zone's velocity, field, face differences and each transverse flux
-// difference between the two states that use it.  Same arithmetic as
-// transverse<D> for every direction.
-__device__ __forceinline__ void transverse_set(const WbView& v, long long qo, long long wo, double dt,
-                                               int mask, int i, int j, int k) {
-  const WbGeo& g = v.geo;
-  const long long q = qo + wb_at(g, i, j, k);
-  const long long w = wo + wb_at(g, i, j, k);
-  const long long s[3] = {1, g.sy, g.sz};
-  const double hdt = 0.5 * dt;
-  const double ir = wb_rcp(v.q[F_RHO][q]);
-  double vv[3], B[3], db[3];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    vv[e] = v.q[F_MX + e][q] * ir;
-    B[e] = v.q[F_BX + e][q];
-    db[e] = (v.b[e][q + s[e]] - v.b[e][q]) * g.idx[e];
-  }
-  // flux differences (times dt/2 / dx_e) of every direction some state needs
+//
+// Zone quantities shared by the directions: velocity v, zone field B, B_e v_e,
+// the face-field differences scaled by dt/2 (h db_e = dt/2 (b_e+ - b_e)/dx_e;
+// minmod commutes with the positive factor dt/2), the flux-difference factors
+// c_e = dt/2 / dx_e and the transverse flux differences dF_e = F_e+ - F_e.
+struct TransZone {
+  double qn[8];
+  double vv[3], B[3], Bv[3], hdb[3], c[3];
   double dF[3][8];
+};
+
+__device__ __forceinline__ void trans_zone(const WbView& v, long long q, long long w, double dt,
+                                           int need, TransZone& z) {
+  const WbGeo& g = v.geo;
+  const long long s[3] = {1, g.sy, g.sz};
+  const double hdt = wb_half(dt);
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) z.qn[cc] = v.q[cc][q];
+  const double ir = wb_rcp(z.qn[F_RHO]);
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    const bool need = (mask & ~(1 << e)) != 0;
-    const double c = hdt * g.idx[e];
+    z.vv[e] = z.qn[F_MX + e] * ir;
+    z.B[e] = z.qn[F_BX + e];
+    z.Bv[e] = z.B[e] * z.vv[e];
+    z.c[e] = hdt * g.idx[e];
+    z.hdb[e] = (v.b[e][q + s[e]] - v.b[e][q]) * z.c[e];
+  }
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
 #pragma unroll
     for (int cc = 0; cc < 8; ++cc) {
-      if (cc == F_BX + e || !need) { dF[e][cc] = 0.0; continue; }
-      dF[e][cc] = (v.Fp[e][cc][w + s[e]] - v.Fp[e][cc][w]) * c;
+      if (cc == F_BX + e || !(need & (1 << e))) { z.dF[e][cc] = 0.0; continue; }
+      z.dF[e][cc] = v.Fp[e][cc][w + s[e]] - v.Fp[e][cc][w];
     }
   }
-  double qn[8];
+}
+
+// q^{n+1/2}_D of one zone from its shared quantities.  The t1 (t2) field
+// component is carried only by the t2 (t1) sweep; density has no source.
+template <int D>
+__device__ __forceinline__ void trans_dir(const WbView& v, long long w, const TransZone& z) {
+  constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+  const long long sD = D == 0 ? 1 : (D == 1 ? v.geo.sy : v.geo.sz);
+  const double hm2 = wb_minmod(z.hdb[D], -z.hdb[t1]);  // for the t2 field component
+  const double hm1 = wb_minmod(z.hdb[D], -z.hdb[t2]);  // for the t1 field component
+  double hS[8];
 #pragma unroll
-  for (int cc = 0; cc < 8; ++cc) qn[cc] = v.q[cc][q];
+  for (int e = 0; e < 3; ++e) hS[F_MX + e] = z.B[e] * z.hdb[D];
+  hS[F_EN] = fma(z.Bv[D], z.hdb[D], fma(z.Bv[t1], hm1, z.Bv[t2] * hm2));
+  const double c1 = z.c[t1], c2 = z.c[t2];
+  v.qh[D][F_RHO][w] = fma(-c2, z.dF[t2][F_RHO], fma(-c1, z.dF[t1][F_RHO], z.qn[F_RHO]));
 #pragma unroll
-  for (int D = 0; D < 3; ++D) {
-    if (!(mask & (1 << D))) continue;
-    const int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
-    const double m2 = wb_minmod(db[D], -db[t1]);
-    const double m1 = wb_minmod(db[D], -db[t2]);
-    double S[8];
-    S[F_RHO] = 0.0;
+  for (int cc = F_MX; cc <= F_EN; ++cc)
+    v.qh[D][cc][w] = fma(-c2, z.dF[t2][cc], fma(-c1, z.dF[t1][cc], z.qn[cc])) + hS[cc];
+  v.qh[D][F_BX + t1][w] = fma(-c2, z.dF[t2][F_BX + t1], z.qn[F_BX + t1]) + z.vv[t1] * hm1;
+  v.qh[D][F_BX + t2][w] = fma(-c1, z.dF[t1][F_BX + t2], z.qn[F_BX + t2]) + z.vv[t2] * hm2;
+  v.qh[D][F_BX + D][w] = wb_half(v.bh[D][w] + v.bh[D][w + sD]);
+}
+
+// The directions in mask (bit d) at one zone, sharing the zone quantities and
+// each transverse flux difference between the two states that use it.
+__device__ __forceinline__ void transverse_set(const WbView& v, long long qo, long long wo, double dt,
+                                               int mask, int i, int j, int k) {
+  const long long q = qo + wb_at(v.geo, i, j, k);
+  const long long w = wo + wb_at(v.geo, i, j, k);
+  // flux differences of every direction some state needs
+  int need = 0;
 #pragma unroll
-    for (int e = 0; e < 3; ++e) S[F_MX + e] = B[e] * db[D];
-    S[F_EN] = B[D] * vv[D] * db[D] + B[t1] * vv[t1] * m1 + B[t2] * vv[t2] * m2;
-    S[F_BX + D] = 0.0;
-    S[F_BX + t1] = vv[t1] * m1;
-    S[F_BX + t2] = vv[t2] * m2;
-    v.qh[D][F_RHO][w] = qn[F_RHO] - (dF[t1][F_RHO] + dF[t2][F_RHO]);
-#pragma unroll
-    for (int cc = F_MX; cc <= F_EN; ++cc) v.qh[D][cc][w] = qn[cc] - (dF[t1][cc] + dF[t2][cc]) + hdt * S[cc];
-    v.qh[D][F_BX + t1][w] = qn[F_BX + t1] - dF[t2][F_BX + t1] + hdt * S[F_BX + t1];
-    v.qh[D][F_BX + t2][w] = qn[F_BX + t2] - dF[t1][F_BX + t2] + hdt * S[F_BX + t2];
-    v.qh[D][F_BX + D][w] = 0.5 * (v.bh[D][w] + v.bh[D][w + s[D]]);
-  }
+  for (int e = 0; e < 3; ++e)
+    if (mask & ~(1 << e)) need |= 1 << e;
+  TransZone z;
+  trans_zone(v, q, w, dt, need, z);
+  if (mask & 1) trans_dir<0>(v, w, z);
+  if (mask & 2) trans_dir<1>(v, w, z);
+  if (mask & 4) trans_dir<2>(v, w, z);
 }
 
 // Step 8: reference EMF at n+1/2 from v of q^n - dt/2 div F* and B = mean of
@@ -635,7 +623,7 @@ __device__ __forceinline__ void eref_half(const WbView& v, long long qo, long lo
   const long long q = qo + wb_at(g, i, j, k);
   const long long w = wo + wb_at(g, i, j, k);
   const long long s[3] = {1, g.sy, g.sz};
-  const double hdt = 0.5 * dt;
+  const double hdt = wb_half(dt);
   double u[4];
   const int comps[4] = {F_RHO, F_MX, F_MY, F_MZ};
 #pragma unroll
@@ -650,7 +638,7 @@ __device__ __forceinline__ void eref_half(const WbView& v, long long qo, long lo
   const double vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
   double B[3];
 #pragma unroll
-  for (int e = 0; e < 3; ++e) B[e] = 0.5 * (v.bh[e][w] + v.bh[e][w + s[e]]);
+  for (int e = 0; e < 3; ++e) B[e] = wb_half(v.bh[e][w] + v.bh[e][w + s[e]]);
   v.Erefh[0][w] = vz * B[1] - vy * B[2];
   v.Erefh[1][w] = vx * B[2] - vz * B[0];
   v.Erefh[2][w] = vy * B[0] - vx * B[1];
@@ -661,27 +649,48 @@ __device__ __forceinline__ double wb_sqrt_fast(double x) {
   return wb_normal_pos(x) ? x * wb_rsqrt(x) : 0.0;
 }
 
-// CFL signal rate sum_d (|v_d| + c_f,d)/dx_d of one zone (Sec. 3 fast speed).
+// CFL signal rate sum_d (|v_d| + c_f,d)/dx_d of one zone (Sec. 3 fast speed)
+// from 1/rho, the velocity, the gas pressure and the zone field.  The fast
+// speed along d: c_f^2 = (S + sqrt(disc_d))/2 with S = a^2 + |B|^2/rho and
+// disc_d = (a^2 - c_n^2)^2 + c_t^2 (c_t^2 + 2 (a^2 + c_n^2)) (the sum of
+// non-negative terms), c_n^2 = B_d^2/rho, c_t^2 = |B|^2/rho - c_n^2.
+__device__ __forceinline__ double signal_rate_core(double ir, const double vv[3], double p,
+                                                   const double B[3], const WbPhys& P,
+                                                   const WbGeo& g) {
+  const double a2 = P.gamma * p * ir;
+  double cn2[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) cn2[d] = (B[d] * B[d]) * ir;
+  const double bbi = (cn2[0] + cn2[1]) + cn2[2];
+  const double S = a2 + bbi;
+  double w = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double ct2 = bbi - cn2[d];
+    const double dd = a2 - cn2[d];
+    const double disc = fma(dd, dd, ct2 * fma(2.0, a2 + cn2[d], ct2));
+    const double cf = wb_sqrt_fast(wb_half(S + wb_sqrt_fast(disc)));
+    w = fma(fabs(vv[d]) + cf, g.idx[d], w);
+  }
+  return w;
+}
+
+// kinetic energy density rho v^2 / 2 from the momentum and the velocity
+__device__ __forceinline__ double kinetic(const double m[3], const double vv[3]) {
+  return wb_half(fma(m[2], vv[2], fma(m[1], vv[1], m[0] * vv[0])));
+}
+
+// The signal rate of one stored zone (conserved state and zone field).
 __device__ __forceinline__ double signal_rate(double rho, double mx, double my, double mz, double e,
                                               double bx, double by, double bz, const WbPhys& P,
                                               const WbGeo& g) {
   const double ir = wb_rcp(rho);
+  const double m[3] = {mx, my, mz};
   const double vv[3] = {mx * ir, my * ir, mz * ir};
   const double B[3] = {bx, by, bz};
-  const double ke = 0.5 * (mx * vv[0] + my * vv[1] + mz * vv[2]);
-  const double bb = bx * bx + by * by + bz * bz;
-  const double p = P.gm1 * (e - ke - 0.5 * bb);
-  const double a2 = P.gamma * p * ir;
-  double w = 0.0;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const double cn2 = B[d] * B[d] * ir;
-    const double ct2 = (bb - B[d] * B[d]) * ir;
-    const double dd = a2 - cn2;
-    const double disc = dd * dd + ct2 * (ct2 + 2.0 * (a2 + cn2));
-    const double cf = wb_sqrt_fast(0.5 * (a2 + cn2 + ct2 + wb_sqrt_fast(disc)));
-    w += (fabs(vv[d]) + cf) * g.idx[d];
-  }
+  const double me = wb_half(fma(bz, bz, fma(by, by, bx * bx)));
+  const double p = P.gm1 * (e - kinetic(m, vv) - me);
+  double w = signal_rate_core(ir, vv, p, B, P, g);
   if (!(rho > 0.0)) w = __longlong_as_double(0x7ff8000000000000LL);
   return w;
 }
@@ -689,7 +698,8 @@ __device__ __forceinline__ double signal_rate(double rho, double mx, double my, 
 // Step 10 (+ the zone field of Step 11, floors and the next step's signal
 // rate): U^{n+1} = ((U^n - dt/dx dF*) - dt/dy dG*) - dt/dz dH* at one interior
 // zone, zone B = mean of b^{n+1}.  Returns the zone's signal rate (NaN if the
-// state is unphysical); floor hits are added to *hits.
+// state is unphysical); floor hits are added to *hits.  The rate is the one
+// signal_rate gives for the stored result.
 __device__ __forceinline__ double final_update(const WbView& v, long long qo, long long wo,
                                                double dt, const WbPhys& P, int i, int j, int k,
                                                int* hits, int* bad) {
@@ -710,14 +720,21 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
   double B[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    B[e] = 0.5 * (v.b[e][q] + v.b[e][q + s[e]]);
+    B[e] = wb_half(v.b[e][q] + v.b[e][q + s[e]]);
     v.q[F_BX + e][q] = B[e];
   }
   if (u[0] < P.rho_floor) { u[0] = P.rho_floor; ++*hits; }
-  const double ke = 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * wb_rcp(u[0]);
-  const double me = 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
-  const double p = P.gm1 * (u[4] - ke - me);
-  if (p < P.p_floor) { u[4] = P.p_floor * P.inv_gm1 + ke + me; ++*hits; }
+  const double ir = wb_rcp(u[0]);
+  const double m[3] = {u[1], u[2], u[3]};
+  const double vv[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
+  const double ke = kinetic(m, vv);
+  const double me = wb_half(fma(B[2], B[2], fma(B[1], B[1], B[0] * B[0])));
+  double p = P.gm1 * (u[4] - ke - me);
+  if (p < P.p_floor) {
+    u[4] = P.p_floor * P.inv_gm1 + ke + me;
+    p = P.gm1 * (u[4] - ke - me);
+    ++*hits;
+  }
   const bool fin = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]) &&
                    isfinite(u[4]) && u[0] > 0.0 && isfinite(p);
 #pragma unroll
@@ -726,7 +743,7 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
     ++*bad;
     return __longlong_as_double(0x7ff8000000000000LL);
   }
-  return signal_rate(u[0], u[1], u[2], u[3], u[4], B[0], B[1], B[2], P, g);
+  return signal_rate_core(ir, vv, p, B, P, g);
 }
 
 // Ghost fill of a box that is its own periodic/outflow domain (no patches):
