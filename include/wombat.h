@@ -99,10 +99,9 @@ typedef struct wb_counters_t {
   long long unphysical;     /* updated zones found non-finite or with rho <= 0 */
   double t;                 /* simulated time since load */
   double last_dt;           /* dt of the last step */
-  long long hll_faces;      /* face evaluations whose flux came from the HLL
-                               fallback, ghost-zone recomputation included
-                               (so the count depends on patching and on the
-                               one-plane storage of a thin periodic z axis) */
+  long long hll_faces;      /* interior faces (the low faces of interior
+                               zones, per predictor and per corrector sweep)
+                               whose flux came from the HLL fallback */
 } wb_counters_t;
 
 typedef struct wb_grid wb_grid;
@@ -224,7 +223,18 @@ const char* wb_noalloc_last_error(void);
  * wb_batch_autotune: times trial_steps real steps per candidate segment
  * length and blocks per SM, keeps the fastest (cached per box-size mix).
  * wb_batch_config: set them explicitly (0 = keep); barrier_budget_cycles is
- * the per-barrier wait limit in SM clock cycles (default 20 s worth). */
+ * the per-barrier wait limit in SM clock cycles (default 20 s worth).
+ * wb_batch_stage_timer: on != 0 zeroes and starts the per-stage timer (one
+ * block stamps the GPU global timer at the barrier closing every stage), 0
+ * stops it; either drops a captured graph.  wb_batch_stage_times copies up to
+ * n accumulated stage times in milliseconds, in the order: dt, predictor
+ * sweeps (Step 1), reference EMF (2), images of both, corner EMFs (3), their
+ * images, half CT (4), its images, transverse states (5, 7), their images,
+ * corrector sweeps (6, 7), their images, half-step EMF (8), its images,
+ * corner EMFs (9), their images, final CT (11), update (10), ghost fill;
+ * *count = the number of stages (19).  The image stages copy periodic
+ * images of intermediates for boxes periodic on every axis, whose other
+ * stages then cover the interior only.  It synchronises the stream. */
 typedef struct wb_batch wb_batch;
 int wb_batch_bytes(int nbox, const wb_desc* descs, size_t work_budget, size_t* bytes);
 int wb_batch_create(int nbox, const wb_desc* descs, size_t work_budget, void* dev_mem,
@@ -240,6 +250,8 @@ int wb_batch_counters(wb_batch* b, int box, wb_counters_t* c);
 int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms);
 int wb_batch_config(wb_batch* b, int seg_len, int blocks_per_sm, long long barrier_budget_cycles);
 int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* groups);
+int wb_batch_stage_timer(wb_batch* b, int on);
+int wb_batch_stage_times(wb_batch* b, double* ms, int n, int* count);
 const char* wb_batch_last_error(const wb_batch* b);
 
 /* ---- serving: a batch as a pool boxes join and leave between launches ----

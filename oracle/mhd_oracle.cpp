@@ -425,9 +425,13 @@ struct Face {
 // i.e. cells f-2..f+1).  A face whose Roe state has no real sound speed, or
 // next to a zone below the protection floor, takes the HLL flux instead and
 // contributes g-tilde = 0 to the limiter of its neighbours (reading R22).
-// Returns the number of output faces that took the HLL flux.
+// Returns the number of output faces that took the HLL flux; if hll_flag is
+// given, hll_flag[f] = 1 marks those faces (0 elsewhere).
 int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
-                double dx_2dt, const Params& P, double (*out)[7]) {
+                double dx_2dt, const Params& P, double (*out)[7],
+                unsigned char* hll_flag = nullptr) {
+  if (hll_flag)
+    for (int f = 0; f <= ncell; ++f) hll_flag[f] = 0;
   int nhll = 0;
   std::vector<Prim> prim(ncell);
   std::vector<double> Fc((size_t)ncell * 7);
@@ -477,6 +481,7 @@ int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
     const Face& F = face[f];
     if (F.hll) {
       ++nhll;
+      if (hll_flag) hll_flag[f] = 1;
       for (int m = 0; m < 7; ++m) out[f][m] = F.Fhll[m];
       continue;
     }
@@ -571,7 +576,9 @@ inline void load_cell(const or_grid* g, const Arr* q, int d, int i, int j, int k
 // Sweep along d over faces [r.lo[d], r.hi[d]] and transverse cells r (other
 // dims).  Input state qin (8 comps, zone-centred B), normal face field bn.
 // Output flux arrays out[8] (global component order, normal-B flux = 0).
-// Returns the number of faces that took the HLL flux.
+// Returns the number of interior faces (faces [0, n_d) along d, zones [0, n)
+// across) that took the HLL flux: the count of distinct faces, independent of
+// how far the region reaches into the ghost zones.
 int sweep(or_grid* g, int d, const Arr* qin, const Arr& bn, double dt, const Range& r, Arr* out) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   double dtdx = dt / g->dxv[d];
@@ -588,6 +595,7 @@ int sweep(or_grid* g, int d, const Arr* qin, const Arr& bn, double dt, const Ran
       std::vector<Cell> cells(ncell);
       std::vector<double> bface(ncell + 1);
       std::vector<double> flux((size_t)(ncell + 1) * 7, NaN);
+      std::vector<unsigned char> hflag(ncell + 1);
       for (int c = 0; c < ncell; ++c) {
         int idx[3];
         idx[d] = c0 + c; idx[t1] = a; idx[t2] = bb;
@@ -599,8 +607,11 @@ int sweep(or_grid* g, int d, const Arr* qin, const Arr& bn, double dt, const Ran
         bface[f] = bn(idx[0], idx[1], idx[2]);
       }
       bface[0] = NaN;
-      bad += pencil_flux(ncell, cells.data(), bface.data(), dtdx, dx_2dt, g->P,
-                         reinterpret_cast<double(*)[7]>(flux.data()));
+      pencil_flux(ncell, cells.data(), bface.data(), dtdx, dx_2dt, g->P,
+                  reinterpret_cast<double(*)[7]>(flux.data()), hflag.data());
+      const bool across = a >= 0 && a < g->n[t1] && bb >= 0 && bb < g->n[t2];
+      for (int f = 2; f <= ncell - 2; ++f)
+        if (hflag[f] && across && c0 + f >= 0 && c0 + f < g->n[d]) ++bad;
       for (int f = 2; f <= ncell - 2; ++f) {
         int idx[3];
         idx[d] = c0 + f; idx[t1] = a; idx[t2] = bb;

@@ -50,7 +50,8 @@ int or_step(or_grid* g, double dt);
 /* Conserved totals x cell volume: rho, Mx, My, Mz, E, bx, by, bz. */
 int or_totals(const or_grid* g, double tot[8]);
 double or_divb_max(const or_grid* g);
-/* floor hits, unphysical zones, HLL faces accumulated over all steps */
+/* floor hits, unphysical zones, and the interior faces (per predictor and
+ * corrector sweep) that took the HLL flux, accumulated over all steps */
 int or_counters(const or_grid* g, long long out[3]);
 /* Protection floors (>= 0; 0 and 0, the default, turn protection off). */
 int or_set_protection(or_grid* g, double prot_rho, double prot_p);

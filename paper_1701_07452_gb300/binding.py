@@ -29,7 +29,7 @@ EXPORTED = (
     "wb_batch_set_steps", "wb_batch_advance", "wb_batch_read", "wb_batch_counters",
     "wb_batch_autotune", "wb_batch_config", "wb_batch_get_config", "wb_batch_last_error",
     "wb_pool_bytes", "wb_pool_create", "wb_pool_admit", "wb_pool_release", "wb_pool_free_bytes",
-    "wb_batch_steps_left",
+    "wb_batch_steps_left", "wb_batch_stage_timer", "wb_batch_stage_times",
 )
 
 
@@ -122,6 +122,8 @@ def lib(build: bool = True):
             L.wb_batch_counters.argtypes = [vp, ctypes.c_int, ctypes.POINTER(WbCounters)]
             L.wb_batch_autotune.argtypes = [vp, ctypes.c_int, dp]
             L.wb_batch_config.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
+            L.wb_batch_stage_timer.argtypes = [vp, ctypes.c_int]
+            L.wb_batch_stage_times.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
             L.wb_batch_get_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]
             L.wb_batch_last_error.argtypes = [vp]
@@ -404,6 +406,19 @@ class Batch:
     def config(self, seg_len=0, blocks_per_sm=0, barrier_budget_cycles=0):
         self._check(lib().wb_batch_config(self._h, int(seg_len), int(blocks_per_sm),
                                           ctypes.c_longlong(int(barrier_budget_cycles))))
+
+    def stage_timer(self, on=True):
+        self._check(lib().wb_batch_stage_timer(self._h, int(bool(on))))
+
+    def stage_times(self):
+        """Accumulated milliseconds per stage (see wb_batch_stage_times)."""
+        ms = (ctypes.c_double * 32)()
+        cnt = ctypes.c_int(0)
+        self._check(lib().wb_batch_stage_times(self._h, ms, 32, ctypes.byref(cnt)))
+        names = ["dt", "pred_sweeps", "eref", "wrap_fp", "edges_pred", "wrap_edges", "ct_half",
+                 "wrap_bh", "transverse", "wrap_qh", "corr_sweeps", "wrap_fc", "eref_half",
+                 "wrap_erefh", "edges_corr", "wrap_edgesh", "ct_final", "update", "halo"]
+        return {names[i] if i < len(names) else str(i): ms[i] for i in range(cnt.value)}
 
     def get_config(self):
         a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)

@@ -30,10 +30,18 @@
 
 namespace {
 
+// Stages of a step.  BS_W* fill the periodic images of intermediates for
+// boxes periodic on every axis, whose other stages then run on the interior
+// only (the grid path's enqueue_pass_wrap); they have no work for other boxes.
 enum {
-  BS_DT = 0, BS_PRED, BS_EREF, BS_EDGE_P, BS_CT_H, BS_TRANS, BS_CORR, BS_EREF_H, BS_EDGE_C,
-  BS_CT_F, BS_FINAL, BS_HALO, BS_COUNT
+  BS_DT = 0, BS_PRED, BS_EREF, BS_W_FP, BS_EDGE_P, BS_W_EE, BS_CT_H, BS_W_BH, BS_TRANS, BS_W_QH,
+  BS_CORR, BS_W_FC, BS_EREF_H, BS_W_ERH, BS_EDGE_C, BS_W_EEH, BS_CT_F, BS_FINAL, BS_HALO, BS_COUNT
 };
+
+__host__ __device__ inline bool stage_is_wrap(int s) {
+  return s == BS_W_FP || s == BS_W_EE || s == BS_W_BH || s == BS_W_QH || s == BS_W_FC ||
+         s == BS_W_ERH || s == BS_W_EEH;
+}
 
 constexpr int kB = wbu::kBlock;        // threads per block
 constexpr int kItemsPerThread = 8;     // items per thread in a chunk of a cheap stage
@@ -51,9 +59,11 @@ __host__ __device__ inline int stage_nsub(int s) {
 
 __host__ __device__ inline bool stage_is_sweep(int s) { return s == BS_PRED || s == BS_CORR; }
 
-// Index boxes of every stage (the same regions as the grid path, wb_capi.cu).
-__host__ __device__ inline WbBox stage_box(int s, int d, const int* n) {
+// Index boxes of every stage (the same regions as the grid path, wb_capi.cu);
+// wrap: the box is periodic on every axis (interior-only regions).
+__host__ __device__ inline WbBox stage_box(int s, int d, const int* n, bool wrap) {
   const int N0 = n[0], N1 = n[1], N2 = n[2];
+  if (wrap && s != BS_CT_F && s != BS_HALO) return bxx(0, N0 - 1, 0, N1 - 1, 0, N2 - 1);
   switch (s) {
     case BS_PRED:
       if (d == 0) return bxx(-3, N0 + 3, -4, N1 + 3, -4, N2 + 3);
@@ -116,9 +126,10 @@ __host__ __device__ inline void sweep_shape(const WbBox& b, int d, int seg_len, 
   *nseg = (len + seg_len - 1) / seg_len;
 }
 
-__host__ __device__ inline long long stage_items(int s, int d, const int* n, int seg_len) {
+__host__ __device__ inline long long stage_items(int s, int d, const WbGeo& g, bool wrap, int seg_len) {
   if (s == BS_DT) return 1;
-  WbBox b = stage_box(s, d, n);
+  if (stage_is_wrap(s)) return wrap ? wbu::wrap_shell_count(g, s == BS_W_QH ? 2 : 1) : 0;
+  WbBox b = stage_box(s, d, g.n, wrap);
   if (stage_is_sweep(s)) {
     long long np;
     int ns;
@@ -135,6 +146,7 @@ __host__ __device__ inline int items_per_chunk(int s) {
 struct BoxInfo {
   WbView v;
   int bc[3];
+  int wrap;  // periodic on every axis: interior-only stages + periodic images
 };
 
 struct BatchParams {
@@ -147,6 +159,7 @@ struct BatchParams {
   const long long* pre_off;   // [ngroups * BS_COUNT] start of each prefix array in pre
   int ngroups;
   unsigned* sync;             // [0] arrivals, [1] generation, [2] error, [3..4] chunk counters
+  unsigned long long* prof;   // per-stage nanoseconds, or null (stage timer off)
   WbPhys phys;
   double cfl;
   int dt_lag;                 // dt from the previous step's start state
@@ -198,7 +211,7 @@ __device__ __forceinline__ void warp_max_atomic(double w, unsigned long long* ds
   if ((threadIdx.x & 31) == 0 && bits) atomicMax(dst, bits);
 }
 
-template <int D>
+template <int D, int EZ, bool PROT>
 __device__ __forceinline__ int sweep_item(const BoxInfo& bi, bool corr, const WbBox& b, long long item,
                                           int seg_len, double dt, const WbPhys& P,
                                           const wbu::Rec rec[2]) {
@@ -216,29 +229,71 @@ __device__ __forceinline__ int sweep_item(const BoxInfo& bi, bool corr, const Wb
   const double* const* q = corr ? v.qh[D] : v.q;
   const double* bn = corr ? v.bh[D] : v.b[D];
   double* const* F = corr ? v.Fc[D] : v.Fp[D];
-  return wbu::sweep_segment<D, false>(v.geo, q, bn, F, 0, 0, b.lo[U] + (int)(pen % nu), b.lo[W] + (int)(pen / nu),
+  return wbu::sweep_segment<D, false, EZ, PROT>(v.geo, q, bn, F, 0, 0, b.lo[U] + (int)(pen % nu), b.lo[W] + (int)(pen / nu),
                                fa, fb, dt, P, rec);
 }
 
+// One shell point of a periodic-image stage: copy every array the stage fills
+// (the arrays the grid path's enqueue_pass_wrap lists at the same point).
+__device__ __forceinline__ void wrap_item(const WbView& v, int s, long long item) {
+  long long dst, src;
+  wbu::wrap_shell_point(v.geo, s == BS_W_QH ? 2 : 1, item, &dst, &src);
+  switch (s) {
+    case BS_W_FP:
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c != F_BX + d) v.Fp[d][c][dst] = v.Fp[d][c][src];
+        v.Eref[d][dst] = v.Eref[d][src];
+      }
+      break;
+    case BS_W_FC:
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c != F_BX + d) v.Fc[d][c][dst] = v.Fc[d][c][src];
+      break;
+    case BS_W_QH:
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v.qh[d][c][dst] = v.qh[d][c][src];
+      break;
+    default: {
+      double* const* a = s == BS_W_EE ? v.Eedge : (s == BS_W_BH ? v.bh : (s == BS_W_ERH ? v.Erefh : v.Eedgeh));
+#pragma unroll
+      for (int d = 0; d < 3; ++d) a[d][dst] = a[d][src];
+    }
+  }
+}
+
+template <int EZ, bool PROT>
 __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, int box,
                                           const BoxInfo& bi, long long item, double dt,
                                           const wbu::Rec rec[2], double* wmax, int* hits, int* bad,
                                           int* hll) {
   const WbView& v = bi.v;
   const int* n = v.geo.n;
+  const bool wrap = bi.wrap != 0;
   if (stage_is_sweep(s)) {
-    const WbBox b = stage_box(s, d, n);
+    const WbBox b = stage_box(s, d, n, wrap);
     const bool corr = s == BS_CORR;
-    if (d == 0) *hll += sweep_item<0>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
-    else if (d == 1) *hll += sweep_item<1>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
-    else *hll += sweep_item<2>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    if (d == 0) *hll += sweep_item<0, EZ, PROT>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    else if (d == 1) *hll += sweep_item<1, EZ, PROT>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
+    else *hll += sweep_item<2, EZ, PROT>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
     return;
   }
   if (s == BS_HALO) {
     wbu::halo_self(v, 0, bi.bc, item);
     return;
   }
-  const WbBox b = stage_box(s, d, n);
+  if (stage_is_wrap(s)) {
+    wrap_item(v, s, item);
+    return;
+  }
+  const WbBox b = stage_box(s, d, n, wrap);
   const int nx = b.hi[0] - b.lo[0] + 1, ny = b.hi[1] - b.lo[1] + 1;
   const int i = b.lo[0] + (int)(item % nx);
   const long long r = item / nx;
@@ -304,12 +359,25 @@ __device__ void box_dt(const BatchParams& B, int box) {
   B.steps_left[box] -= 1;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// EZ: compile-time mask of waves with eps_k = 0 (their Q-branch arithmetic is
+// dropped); PROT: the protection-floor test is compiled in.  The launch picks
+// the variant from the physics, as the grid path's sweep launches do.
+template <int EZ, bool PROT>
 __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nsteps) {
   __shared__ double srec[2][wbu::R_WORDS][wbu::kBlock];
   __shared__ long long s_chunk;
   const wbu::Rec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
   const unsigned nblocks = gridDim.x;
   unsigned stage_seq = 0;
+  // stage timer: block 0 stamps the end of every stage (after its barrier)
+  const bool timer = B.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long t_prev = timer ? global_ns() : 0ULL;
   for (int step = 0; step < nsteps; ++step) {
     for (int grp = 0; grp < B.ngroups; ++grp) {
       const int gb0 = B.gfirst[grp];
@@ -344,20 +412,25 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
           const double dt = *(volatile const double*)&B.scal[box].dt;
           if (!(dt > 0.0)) continue;
           const BoxInfo& bi = B.boxes[box];
-          const long long nitems = stage_items(s, sub, bi.v.geo.n, B.seg_len);
+          const long long nitems = stage_items(s, sub, bi.v.geo, bi.wrap != 0, B.seg_len);
           const long long i0 = (c - pre[lo]) * ipc;
           long long i1 = i0 + ipc;
           if (i1 > nitems) i1 = nitems;
           double wmax = 0.0;
           int hits = 0, bad = 0, hll = 0;
           for (long long it = i0 + threadIdx.x; it < i1; it += kB)
-            unit_item(B, s, sub, box, bi, it, dt, rec, &wmax, &hits, &bad, &hll);
+            unit_item<EZ, PROT>(B, s, sub, box, bi, it, dt, rec, &wmax, &hits, &bad, &hll);
           if (s == BS_FINAL) warp_max_atomic(wmax, &B.scal[box].wmax_next);
           if (hits) atomicAdd((unsigned long long*)&B.scal[box].floor_hits, (unsigned long long)hits);
           if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
           if (hll) atomicAdd((unsigned long long*)&B.scal[box].hll_faces, (unsigned long long)hll);
         }
         if (!grid_barrier(B, nblocks)) return;
+        if (timer) {
+          const unsigned long long t = global_ns();
+          B.prof[s] += t - t_prev;
+          t_prev = t;
+        }
       }
     }
   }
@@ -425,6 +498,8 @@ struct wb_batch {
   long long* d_pre;
   long long* d_pre_off;
   unsigned* d_sync;
+  unsigned long long* d_prof;  // per-stage nanoseconds (stage timer)
+  bool prof = false;
   double* staging;
   size_t pre_cap;
   // launch configuration
@@ -501,7 +576,8 @@ PoolSizes pool_sizes(size_t state_bytes, size_t work_bytes, int cap, int max_n) 
   P.pre_cap = (size_t)BS_COUNT * (4 * (size_t)cap + 2) + 16;
   P.tables = al(sizeof(BoxInfo) * cap) + al(sizeof(WbScalars) * cap) + al(sizeof(int) * cap) +
              al(sizeof(int) * cap) + al(sizeof(int) * (cap + 1)) + al(sizeof(long long) * P.pre_cap) +
-             al(sizeof(long long) * (size_t)cap * BS_COUNT) + al(sizeof(unsigned) * 8);
+             al(sizeof(long long) * (size_t)cap * BS_COUNT) + al(sizeof(unsigned) * 8) +
+             al(sizeof(unsigned long long) * BS_COUNT);
   P.staging = al(sizeof(double) * (size_t)(max_n + 1) * (max_n + 1) * (max_n + 1));
   P.total = P.state + P.work + P.tables + P.staging;
   return P;
@@ -521,7 +597,7 @@ void build_prefix(const wb_batch* b, std::vector<long long>& pre, std::vector<lo
         const int box = b->gbox[e];
         for (int sub = 0; sub < nsub; ++sub) {
           pre.push_back(acc);
-          const long long items = stage_items(s, sub, b->geo[box].n, b->seg_len);
+          const long long items = stage_items(s, sub, b->geo[box], b->info[box].wrap != 0, b->seg_len);
           acc += (items + items_per_chunk(s) - 1) / items_per_chunk(s);
         }
       }
@@ -606,12 +682,22 @@ BatchParams params(const wb_batch* b) {
   p.pre_off = b->d_pre_off;
   p.ngroups = (int)b->gfirst.size() - 1;
   p.sync = b->d_sync;
+  p.prof = b->prof ? b->d_prof : nullptr;
   p.phys = b->phys;
   p.cfl = b->cfl;
   p.dt_lag = b->dt_lag;
   p.seg_len = b->seg_len;
   p.budget = b->budget;
   return p;
+}
+
+// The k_batch variant for the physics: the default eps_k (zero on the Alfven
+// and entropy waves) without protection floors takes the specialised sweep;
+// anything else the general one (protection tested at run time).
+const void* batch_kernel(const WbPhys& ph) {
+  const bool ez = (ph.eps_zero & wbu::kEpsZeroLD) == wbu::kEpsZeroLD;
+  if (ez && !ph.prot) return (const void*)k_batch<wbu::kEpsZeroLD, false>;
+  return (const void*)k_batch<0, true>;
 }
 
 // enqueue one persistent launch of nsteps steps (no synchronisation)
@@ -631,7 +717,7 @@ cudaError_t enqueue_advance(wb_batch* b, int nsteps) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, (const void*)k_batch, args);
+  return cudaLaunchKernelExC(&cfg, batch_kernel(b->phys), args);
 }
 
 int read_sync_error(wb_batch* b) {
@@ -724,13 +810,14 @@ int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes
   b->d_pre = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * P.pre_cap);
   b->d_pre_off = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * (size_t)max_boxes * BS_COUNT);
   b->d_sync = reinterpret_cast<unsigned*>(t); t += al(sizeof(unsigned) * 8);
+  b->d_prof = reinterpret_cast<unsigned long long*>(t); t += al(sizeof(unsigned long long) * BS_COUNT);
   b->staging = reinterpret_cast<double*>(b->mem + P.state + P.work + P.tables);
   b->staging_elems = P.staging / sizeof(double);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch, kB, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel(b->phys), kB, 0);
   b->max_blocks_per_sm = nb > 0 ? nb : 1;
   b->blocks_per_sm = b->max_blocks_per_sm;
   b->seg_len = 32;
@@ -784,6 +871,7 @@ int wb_pool_admit(wb_batch* b, const wb_desc* d, int* box) {
   std::memset(&bi, 0, sizeof(bi));
   bi.v.geo = g;
   for (int a = 0; a < 3; ++a) bi.bc[a] = d->bc[a];
+  bi.wrap = d->bc[0] == WB_BC_PERIODIC && d->bc[1] == WB_BC_PERIODIC && d->bc[2] == WB_BC_PERIODIC;
   double* st = b->state_base + off;
   for (int c = 0; c < 8; ++c) bi.v.q[c] = st + (size_t)c * g.V;
   for (int c = 0; c < 3; ++c) bi.v.b[c] = st + (size_t)(8 + c) * g.V;
@@ -1065,6 +1153,28 @@ int wb_batch_config(wb_batch* b, int seg_len, int blocks_per_sm, long long barri
   drop_graph(b);
   b->dirty = true;
   return ensure_built(b);
+}
+
+int wb_batch_stage_timer(wb_batch* b, int on) {
+  if (!b) return WB_ERR_INVALID;
+  drop_graph(b);
+  b->prof = on != 0;
+  if (b->prof) {
+    cudaError_t e = cudaMemsetAsync(b->d_prof, 0, sizeof(unsigned long long) * BS_COUNT, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "stage timer");
+  }
+  return WB_OK;
+}
+
+int wb_batch_stage_times(wb_batch* b, double* ms, int n, int* count) {
+  if (!b || (!ms && n > 0)) return WB_ERR_INVALID;
+  if (count) *count = BS_COUNT;
+  unsigned long long ns[BS_COUNT];
+  cudaError_t e = cudaMemcpyAsync(ns, b->d_prof, sizeof(ns), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "stage times");
+  for (int i = 0; i < n && i < BS_COUNT; ++i) ms[i] = 1e-6 * (double)ns[i];
+  return WB_OK;
 }
 
 int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* groups) {

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <new>
 #include <string>
@@ -42,6 +43,9 @@ struct wb_grid {
   unsigned long long* red;
   std::string err;
   bool loaded;
+  // interior-only stages with periodic images of the intermediates (a single
+  // patch periodic on every axis, 3D storage)
+  bool wrap = false;
   // sweep timing (wb_profile_sweeps)
   bool prof;
   std::vector<cudaEvent_t> ev;
@@ -231,8 +235,77 @@ void sweep(wb_grid* g, int dir, const SweepArgs& a, int nslots) {
   }
 }
 
+WrapList wrap_list(std::initializer_list<double*> arrays) {
+  WrapList L;
+  std::memset(&L, 0, sizeof(L));
+  for (double* a : arrays)
+    if (a && L.n < 24) L.a[L.n++] = a;
+  return L;
+}
+
+// One step of a single-patch box periodic on every axis.  Every stage runs on
+// the interior index range only; between stages the ghost points a later
+// stage reads (1 deep, 2 for the preconditioned states the corrector sweeps
+// read) are filled with periodic images.  On one GPU the copies cost a small
+// fraction of recomputing the ghost rings, which the 5-zone scheme (one
+// exchange per step) otherwise does at every stage.
+void enqueue_pass_wrap(wb_grid* g) {
+  cudaStream_t s = g->stream;
+  StageArgs A = stage_args(g, 0, 1);
+  const WbGeo& G = g->geo;
+  const int N0 = G.n[0], N1 = G.n[1], N2 = G.n[2];
+  const WbBox in = box(0, N0 - 1, 0, N1 - 1, 0, N2 - 1);
+  const WbBox in3[3] = {in, in, in};
+  // Step 1: predictor fluxes on the interior faces (face N_d is face 0)
+  for (int d = 0; d < 3; ++d) sweep(g, d, sweep_args(g, A, d, false, in), 1);
+  // Step 2: reference EMF; then the images of both
+  wb_launch_eref(A, in, s);
+  wb_launch_wrap(wrap_list({g->Fp[0][0], g->Fp[0][1], g->Fp[0][2], g->Fp[0][3], g->Fp[0][4], g->Fp[0][6],
+                            g->Fp[0][7], g->Fp[1][0], g->Fp[1][1], g->Fp[1][2], g->Fp[1][3], g->Fp[1][4],
+                            g->Fp[1][5], g->Fp[1][7], g->Fp[2][0], g->Fp[2][1], g->Fp[2][2], g->Fp[2][3],
+                            g->Fp[2][4], g->Fp[2][5], g->Fp[2][6], g->Eref[0], g->Eref[1], g->Eref[2]}),
+                 G, 1, s);
+  // Step 3: corner EMFs; Step 4: b^{n+1/2}
+  wb_launch_edges(A, false, in3, s);
+  wb_launch_wrap(wrap_list({g->Eedge[0], g->Eedge[1], g->Eedge[2]}), G, 1, s);
+  wb_launch_ct(A, false, in3, s);
+  wb_launch_wrap(wrap_list({g->bh[0], g->bh[1], g->bh[2]}), G, 1, s);
+  // Steps 5, 7: preconditioned states (the corrector sweeps read 2 zones out)
+  wb_launch_transverse(A, in3, s);
+  {
+    WrapList L = wrap_list({});
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 8; ++c)
+        if (g->qh[d][c]) L.a[L.n++] = g->qh[d][c];
+    wb_launch_wrap(L, G, 2, s);
+  }
+  // Steps 6, 7: corrector fluxes
+  for (int d = 0; d < 3; ++d) sweep(g, d, sweep_args(g, A, d, true, in), 1);
+  wb_launch_wrap(wrap_list({g->Fc[0][0], g->Fc[0][1], g->Fc[0][2], g->Fc[0][3], g->Fc[0][4], g->Fc[0][6],
+                            g->Fc[0][7], g->Fc[1][0], g->Fc[1][1], g->Fc[1][2], g->Fc[1][3], g->Fc[1][4],
+                            g->Fc[1][5], g->Fc[1][7], g->Fc[2][0], g->Fc[2][1], g->Fc[2][2], g->Fc[2][3],
+                            g->Fc[2][4], g->Fc[2][5], g->Fc[2][6]}),
+                 G, 1, s);
+  // Step 8: half-step reference EMF; Step 9: corner EMFs
+  wb_launch_eref_half(A, in, s);
+  wb_launch_wrap(wrap_list({g->Erefh[0], g->Erefh[1], g->Erefh[2]}), G, 1, s);
+  wb_launch_edges(A, true, in3, s);
+  wb_launch_wrap(wrap_list({g->Eedgeh[0], g->Eedgeh[1], g->Eedgeh[2]}), G, 1, s);
+  // Step 11 (faces, the high boundary face included), then Step 10
+  {
+    WbBox bb[3] = {box(0, N0, 0, N1 - 1, 0, N2 - 1), box(0, N0 - 1, 0, N1, 0, N2 - 1),
+                   box(0, N0 - 1, 0, N1 - 1, 0, N2)};
+    wb_launch_ct(A, true, bb, s);
+  }
+  wb_launch_final(A, s);
+}
+
 // One pipeline pass (Steps 1-11) over patches [p0, p0 + nslots).
 void enqueue_pass(wb_grid* g, long long p0, int nslots) {
+  if (g->wrap) {
+    enqueue_pass_wrap(g);
+    return;
+  }
   cudaStream_t s = g->stream;
   StageArgs A = stage_args(g, p0, nslots);
   const int N0 = g->geo.n[0], N1 = g->geo.n[1], N2 = g->geo.n[2];
@@ -375,6 +448,8 @@ int wb_grid_create(const wb_desc* d, void* dev_mem, size_t bytes, void* stream, 
   }
   g->map.npatch = L.npatch;
   g->npatch = L.npatch;
+  g->wrap = L.npatch == 1 && !flat_z(d) && d->bc[0] == WB_BC_PERIODIC && d->bc[1] == WB_BC_PERIODIC &&
+            d->bc[2] == WB_BC_PERIODIC;
   g->S = L.S;
   g->phys = wb_phys_of(d);
   g->stream = reinterpret_cast<cudaStream_t>(stream);

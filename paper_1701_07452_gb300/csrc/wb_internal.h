@@ -52,6 +52,14 @@ void wb_launch_final(const StageArgs& a, cudaStream_t s);
 
 void wb_launch_halo(double* const q[8], double* const b[3], const WbGeo& geo, const GridMap& m,
                     cudaStream_t s);
+
+// Arrays whose ghost points a periodic wrap fills (null entries skipped by
+// the caller that builds the list).
+struct WrapList {
+  double* a[24];
+  int n;
+};
+void wb_launch_wrap(const WrapList& L, const WbGeo& geo, int depth, cudaStream_t s);
 void wb_launch_dt_init(double* const q[8], const WbGeo& geo, long long npatch, const WbPhys& ph,
                        WbScalars* scal, cudaStream_t s);
 void wb_launch_dt_step(WbScalars* scal, double cfl, double t_end, int lag, cudaStream_t s);

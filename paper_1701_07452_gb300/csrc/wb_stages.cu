@@ -94,6 +94,19 @@ __global__ void k_eref_half(StageArgs A, WbBox box) {
   wbu::eref_half(A.v, blockIdx.y * A.slot_q, blockIdx.y * A.slot_w, dt, i, j, k);
 }
 
+// Periodic images of intermediate arrays of a single-patch box that is
+// periodic on every axis: each ghost point within `depth` zones of the
+// interior takes the value computed at the interior point it is an image of
+// (the same function of the same inputs, so the copy equals a recomputation
+// bit for bit).  One thread per shell point.
+__global__ void k_wrap(WrapList L, WbGeo g, int depth, long long n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  long long dst, src;
+  wbu::wrap_shell_point(g, depth, t, &dst, &src);
+  for (int a = 0; a < L.n; ++a) L.a[a][dst] = L.a[a][src];
+}
+
 __device__ __forceinline__ void block_max_atomic(double w, unsigned long long* dst) {
   // warp-shuffle max, then one atomic per warp (exact, order independent)
   unsigned long long bits = (w >= 0.0) ? (unsigned long long)__double_as_longlong(w)
@@ -373,6 +386,12 @@ void wb_launch_halo(double* const q[8], double* const b[3], const WbGeo& geo, co
                     cudaStream_t s) {
   StageArgs a = mini_args(q, b, geo);
   k_halo<<<grid_for(geo.V, (int)m.npatch, 256), 256, 0, s>>>(a, m);
+}
+
+void wb_launch_wrap(const WrapList& L, const WbGeo& geo, int depth, cudaStream_t s) {
+  if (L.n <= 0) return;
+  const long long n = wbu::wrap_shell_count(geo, depth);
+  k_wrap<<<grid_for(n, 1, 256), 256, 0, s>>>(L, geo, depth, n);
 }
 
 void wb_launch_dt_init(double* const q[8], const WbGeo& geo, long long npatch, const WbPhys& ph,

@@ -42,8 +42,7 @@ using wbu::kBlock;
 #define WB_SWEEP_MIN_BLOCKS 4
 #endif
 
-// waves 2, 4, 6 (Alfven, entropy, Alfven) have eps = 0
-constexpr int kEpsZeroLD = (1 << 1) | (1 << 3) | (1 << 5);
+using wbu::kEpsZeroLD;
 
 template <int D, int EZ, bool PROT>
 __global__ void __launch_bounds__(wbu::kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs A) {

@@ -27,6 +27,10 @@ namespace wbu {
 // ---------------------------------------------------------------- sweep ----
 constexpr int kBlock = 64;
 
+// waves 2, 4, 6 (Alfven, entropy, Alfven) have eps = 0 (the default eps_k):
+// the mask of the sweep specialisation that drops their Q-branch arithmetic
+constexpr int kEpsZeroLD = (1 << 1) | (1 << 3) | (1 << 5);
+
 struct Cell {
   double rho, ir, sr, isr;        // rho, 1/rho, sqrt(rho), 1/sqrt(rho)
   double vn, vt1, vt2;
@@ -377,7 +381,7 @@ __device__ __forceinline__ void face_flux(const Rec& f, const double gi[7], cons
 // output arrays.  rec: two shared-memory face records of this thread.
 // Faces without a Roe state or below the protection floor take the HLL flux
 // and give g-tilde = 0 to the limiters of their neighbours.  Returns the
-// number of HLL faces among [fa, fb].
+// number of HLL faces among [fa, fb] that are interior faces of the box.
 template <int D, bool NC, int EZ = 0, bool PROT = true>
 __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const* q,
                                              const double* bn, double* const* F, long long qo,
@@ -400,6 +404,9 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
   load_cell<D, NC>(q, off_in, P, cL);
   double gt_p[7], g_p[7];  // g-tilde of face f-1; g of zone f-2
   int nhll = 0;
+  // HLL faces are counted on interior faces only (distinct faces, whatever
+  // part of the ghost rings the region covers)
+  const bool across = pu >= 0 && pu < g.n[U] && pw >= 0 && pw < g.n[W];
   int cur = 0;
   // faces f = fa-1 .. fb+1; face f lies between zones f-1 and f
   for (int f = fa - 1; f <= fb + 1; ++f) {
@@ -427,7 +434,7 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
         if (wb_neg(fr[R_RHO])) {
 #pragma unroll
           for (int m = 0; m < 7; ++m) out[m] = fr[R_FAVG + m];
-          ++nhll;
+          if (across && f - 1 >= 0 && f - 1 < g.n[D]) ++nhll;
         } else {
           face_flux<EZ>(fr, g_p, gz, dx_2dt, P, out);
         }
@@ -744,6 +751,52 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
     return __longlong_as_double(0x7ff8000000000000LL);
   }
   return signal_rate_core(ir, vv, p, B, P, g);
+}
+
+// Periodic images of intermediates (interior-only stages of a box periodic on
+// every axis): the shell of ghost points within `depth` zones of the
+// interior, enumerated as the two z slabs of the depth-padded box, then the
+// two y slabs and the two x slabs of its interior z (and y) range.
+__host__ __device__ __forceinline__ long long wrap_shell_count(const WbGeo& g, int depth) {
+  const long long w = 2 * depth;
+  return (long long)(g.n[0] + w) * (g.n[1] + w) * w + (long long)(g.n[0] + w) * w * g.n[2] +
+         w * g.n[1] * (long long)g.n[2];
+}
+
+// Shell point t (0 <= t < wrap_shell_count) -> its destination and the
+// interior point it is an image of (offsets in the padded storage).
+__device__ __forceinline__ void wrap_shell_point(const WbGeo& g, int depth, long long t, long long* dst,
+                                                 long long* src) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const int w = 2 * depth;
+  const unsigned e0 = (unsigned)(n0 + w), e1 = (unsigned)(n1 + w);
+  const unsigned long long zs = (unsigned long long)e0 * e1 * w;
+  const unsigned long long ys = (unsigned long long)e0 * w * n2;
+  unsigned long long u = (unsigned long long)t;
+  int i, j, k;
+  if (u < zs) {
+    const unsigned r = (unsigned)(u % ((unsigned long long)e0 * e1));
+    const int dz = (int)(u / ((unsigned long long)e0 * e1));
+    i = (int)(r % e0) - depth;
+    j = (int)(r / e0) - depth;
+    k = dz < depth ? dz - depth : n2 + dz - depth;
+  } else if ((u -= zs) < ys) {
+    const unsigned per = e0 * (unsigned)w;
+    k = (int)(u / per);
+    const unsigned r = (unsigned)(u % per);
+    const int dy = (int)(r / e0);
+    i = (int)(r % e0) - depth;
+    j = dy < depth ? dy - depth : n1 + dy - depth;
+  } else {
+    u -= ys;
+    const unsigned r = (unsigned)(u / (unsigned)w);
+    const int dx = (int)(u % (unsigned)w);
+    j = (int)(r % (unsigned)n1);
+    k = (int)(r / (unsigned)n1);
+    i = dx < depth ? dx - depth : n0 + dx - depth;
+  }
+  *dst = wb_at(g, i, j, k);
+  *src = wb_at(g, ((i % n0) + n0) % n0, ((j % n1) + n1) % n1, ((k % n2) + n2) % n2);
 }
 
 // Ghost fill of a box that is its own periodic/outflow domain (no patches):

@@ -39,11 +39,7 @@ def test_double_rarefaction_protected_parity(wb, oracle_mod):
     W, bx, by, bz = double_rarefaction(n)
     L = (1.0, 1e3, 1e3)
     kw = dict(gamma=1.4, bc=(1, 0, 0))
-    # The HLL counter counts face evaluations, ghost-zone recomputation
-    # included, so it depends on the storage: a periodic one-zone z axis is
-    # stored as one plane, the oracle stores 11.  Outflow z keeps the 3D
-    # storage and gives the same zones for z-uniform data.
-    g = wb.Grid((n, 1, 1), length=L, gamma=1.4, bc=(1, 0, 1), **PROT)
+    g = wb.Grid((n, 1, 1), length=L, **kw, **PROT)
     g.load(W, bx, by, bz, primitive=True)
     o = oracle_mod.Grid((n, 1, 1), L, **kw)
     o.set_protection(PROT["prot_rho"], PROT["prot_p"])
