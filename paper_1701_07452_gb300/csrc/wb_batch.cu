@@ -94,7 +94,6 @@ __host__ __device__ inline WbBox stage_box(int s, int d, const int* n, bool wrap
       if (d == 1) return bxx(0, N0 - 1, 0, N1, 0, N2 - 1);
       return bxx(0, N0 - 1, 0, N1 - 1, 0, N2);
     case BS_FINAL: return bxx(0, N0 - 1, 0, N1 - 1, 0, N2 - 1);
-    case BS_HALO: return bxx(-WB_NG, N0 + WB_NG - 1, -WB_NG, N1 + WB_NG - 1, -WB_NG, N2 + WB_NG - 1);
     default: return bxx(0, 0, 0, 0, 0, 0);
   }
 }
@@ -117,18 +116,23 @@ __host__ __device__ inline long long box_cnt(const WbBox& b) {
   return (long long)(b.hi[0] - b.lo[0] + 1) * (b.hi[1] - b.lo[1] + 1) * (b.hi[2] - b.lo[2] + 1);
 }
 
-// sweep items: pencils x segments
+// sweep items: pencils x segments.  seg_len is the longest segment wanted;
+// a pencil is cut into nseg segments of nearly equal length (*len_out each,
+// the last one shorter by less than nseg faces) so that no item is left far
+// shorter than the others.
 __host__ __device__ inline void sweep_shape(const WbBox& b, int d, int seg_len, long long* npen,
-                                            int* nseg) {
+                                            int* nseg, int* len_out = nullptr) {
   const int U = (d == 0) ? 1 : 0, W = (d == 2) ? 1 : 2;
   *npen = (long long)(b.hi[U] - b.lo[U] + 1) * (b.hi[W] - b.lo[W] + 1);
   const int len = b.hi[d] - b.lo[d] + 1;
   *nseg = (len + seg_len - 1) / seg_len;
+  if (len_out) *len_out = (len + *nseg - 1) / *nseg;
 }
 
 __host__ __device__ inline long long stage_items(int s, int d, const WbGeo& g, bool wrap, int seg_len) {
   if (s == BS_DT) return 1;
-  if (stage_is_wrap(s)) return wrap ? wbu::wrap_shell_count(g, s == BS_W_QH ? 2 : 1) : 0;
+  if (stage_is_wrap(s)) return wrap ? wbu::shell_count(g, s == BS_W_QH ? 2 : 1) : 0;
+  if (s == BS_HALO) return wbu::shell_count(g, WB_NG);
   WbBox b = stage_box(s, d, g.n, wrap);
   if (stage_is_sweep(s)) {
     long long np;
@@ -217,13 +221,13 @@ __device__ __forceinline__ int sweep_item(const BoxInfo& bi, bool corr, const Wb
                                           const wbu::Rec rec[2]) {
   constexpr int U = (D == 0) ? 1 : 0, W = (D == 2) ? 1 : 2;
   long long npen;
-  int nseg;
-  sweep_shape(b, D, seg_len, &npen, &nseg);
+  int nseg, slen;
+  sweep_shape(b, D, seg_len, &npen, &nseg, &slen);
   const int seg = (int)(item / npen);
   const long long pen = item - seg * npen;
   const int nu = b.hi[U] - b.lo[U] + 1;
-  const int fa = b.lo[D] + seg * seg_len;
-  int fb = fa + seg_len - 1;
+  const int fa = b.lo[D] + seg * slen;
+  int fb = fa + slen - 1;
   if (fb > b.hi[D]) fb = b.hi[D];
   const WbView& v = bi.v;
   const double* const* q = corr ? v.qh[D] : v.q;
@@ -334,6 +338,130 @@ __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, in
   (void)box;
 }
 
+// Stages whose items are cheap and mostly waiting on memory: a thread takes
+// two items per pass and loads both before storing either (the grid path's
+// per-stage kernels hide that latency with many resident warps instead).
+__host__ __device__ inline bool stage_pairs(int s) {
+  return s == BS_EREF || s == BS_EDGE_P || s == BS_EDGE_C || s == BS_CT_H || s == BS_CT_F ||
+         s == BS_HALO || stage_is_wrap(s);
+}
+
+__device__ __forceinline__ void item_ijk(const WbBox& b, long long item, int* i, int* j, int* k) {
+  const int nx = b.hi[0] - b.lo[0] + 1, ny = b.hi[1] - b.lo[1] + 1;
+  *i = b.lo[0] + (int)(item % nx);
+  const long long r = item / nx;
+  *j = b.lo[1] + (int)(r % ny);
+  *k = b.lo[2] + (int)(r / ny);
+}
+
+// Copy of one array for two shell points: both loads issue before either
+// store.
+__device__ __forceinline__ void copy2(double* a, long long d0, long long s0, long long d1, long long s1,
+                                      bool two) {
+  const double x0 = a[s0];
+  const double x1 = two ? a[s1] : 0.0;
+  a[d0] = x0;
+  if (two) a[d1] = x1;
+}
+
+// The arrays of a copy stage (state for the ghost fill, intermediates for
+// the periodic-image stages), moved for two shell points at a time.
+__device__ __forceinline__ void copy_stage(const WbView& v, int s, long long d0, long long s0, long long d1,
+                                           long long s1, bool two) {
+  switch (s) {
+    case BS_HALO:
+#pragma unroll
+      for (int c = 0; c < 8; ++c) copy2(v.q[c], d0, s0, d1, s1, two);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) copy2(v.b[c], d0, s0, d1, s1, two);
+      return;
+    case BS_W_FP:
+    case BS_W_FC: {
+      double* const(*F)[8] = s == BS_W_FP ? v.Fp : v.Fc;
+#pragma unroll
+      for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c != F_BX + e) copy2(F[e][c], d0, s0, d1, s1, two);
+      if (s == BS_W_FP) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) copy2(v.Eref[e], d0, s0, d1, s1, two);
+      }
+      return;
+    }
+    case BS_W_QH:
+#pragma unroll
+      for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) copy2(v.qh[e][c], d0, s0, d1, s1, two);
+      return;
+    default: {
+      double* const* a3 = s == BS_W_EE ? v.Eedge : (s == BS_W_BH ? v.bh : (s == BS_W_ERH ? v.Erefh : v.Eedgeh));
+#pragma unroll
+      for (int e = 0; e < 3; ++e) copy2(a3[e], d0, s0, d1, s1, two);
+    }
+  }
+}
+
+// Items it0 and it1 (it1 < 0: none) of a pairing stage for one box.
+__device__ __forceinline__ void unit_pair(int s, int d, const BoxInfo& bi, long long it0, long long it1,
+                                          double dt) {
+  const WbView& v = bi.v;
+  const bool two = it1 >= 0;
+  if (s == BS_HALO || stage_is_wrap(s)) {
+    long long d0, s0, d1 = 0, s1 = 0;
+    if (s == BS_HALO) {
+      wbu::halo_self_offsets(v.geo, bi.bc, it0, &d0, &s0);
+      if (two) wbu::halo_self_offsets(v.geo, bi.bc, it1, &d1, &s1);
+    } else {
+      const int depth = s == BS_W_QH ? 2 : 1;
+      wbu::wrap_shell_point(v.geo, depth, it0, &d0, &s0);
+      if (two) wbu::wrap_shell_point(v.geo, depth, it1, &d1, &s1);
+    }
+    copy_stage(v, s, d0, s0, d1, s1, two);
+    return;
+  }
+  const WbBox b = stage_box(s, d, v.geo.n, bi.wrap != 0);
+  int i0, j0, k0, i1 = 0, j1 = 0, k1 = 0;
+  item_ijk(b, it0, &i0, &j0, &k0);
+  if (two) item_ijk(b, it1, &i1, &j1, &k1);
+  switch (s) {
+    case BS_EREF: {
+      wbu::ErefIn a0, a1;
+      wbu::eref_load(v, 0, 0, i0, j0, k0, a0);
+      if (two) wbu::eref_load(v, 0, 0, i1, j1, k1, a1);
+      wbu::eref_finish(v, a0);
+      if (two) wbu::eref_finish(v, a1);
+      return;
+    }
+    case BS_EDGE_P:
+    case BS_EDGE_C: {
+      const bool corr = s == BS_EDGE_C;
+      wbu::EdgeIn a0, a1;
+#define WB_EDGE_PAIR(C)                                             \
+  wbu::edge_load<C>(v, 0, corr, i0, j0, k0, a0);                    \
+  if (two) wbu::edge_load<C>(v, 0, corr, i1, j1, k1, a1);           \
+  wbu::edge_finish<C>(v, corr, a0);                                 \
+  if (two) wbu::edge_finish<C>(v, corr, a1);
+      if (d == 0) { WB_EDGE_PAIR(0) } else if (d == 1) { WB_EDGE_PAIR(1) } else { WB_EDGE_PAIR(2) }
+#undef WB_EDGE_PAIR
+      return;
+    }
+    default: {  // BS_CT_H, BS_CT_F
+      const bool fin = s == BS_CT_F;
+      wbu::CtIn a0, a1;
+#define WB_CT_PAIR(D)                                               \
+  wbu::ct_load<D>(v, 0, 0, fin, i0, j0, k0, a0);                    \
+  if (two) wbu::ct_load<D>(v, 0, 0, fin, i1, j1, k1, a1);           \
+  wbu::ct_finish<D>(v, fin, dt, a0);                                \
+  if (two) wbu::ct_finish<D>(v, fin, dt, a1);
+      if (d == 0) { WB_CT_PAIR(0) } else if (d == 1) { WB_CT_PAIR(1) } else { WB_CT_PAIR(2) }
+#undef WB_CT_PAIR
+      return;
+    }
+  }
+}
+
 // dt of one box for the coming step (reading R3 of the design notes)
 __device__ void box_dt(const BatchParams& B, int box) {
   WbScalars* s = B.scal + box;
@@ -418,8 +546,13 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
           if (i1 > nitems) i1 = nitems;
           double wmax = 0.0;
           int hits = 0, bad = 0, hll = 0;
-          for (long long it = i0 + threadIdx.x; it < i1; it += kB)
-            unit_item<EZ, PROT>(B, s, sub, box, bi, it, dt, rec, &wmax, &hits, &bad, &hll);
+          if (stage_pairs(s)) {
+            for (long long it = i0 + threadIdx.x; it < i1; it += 2 * kB)
+              unit_pair(s, sub, bi, it, it + kB < i1 ? it + kB : -1, dt);
+          } else {
+            for (long long it = i0 + threadIdx.x; it < i1; it += kB)
+              unit_item<EZ, PROT>(B, s, sub, box, bi, it, dt, rec, &wmax, &hits, &bad, &hll);
+          }
           if (s == BS_FINAL) warp_max_atomic(wmax, &B.scal[box].wmax_next);
           if (hits) atomicAdd((unsigned long long*)&B.scal[box].floor_hits, (unsigned long long)hits);
           if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
@@ -1198,7 +1331,7 @@ int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms) {
   if (!b || trial_steps < 1) return bfail(b, WB_ERR_INVALID, "bad argument");
   int brc = ensure_built(b);
   if (brc) return brc;
-  const int segs[] = {16, 24, 32, 48, 64, 96};
+  const int segs[] = {16, 24, 32, 48, 64, 96, 136};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

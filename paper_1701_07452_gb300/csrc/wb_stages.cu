@@ -390,7 +390,7 @@ void wb_launch_halo(double* const q[8], double* const b[3], const WbGeo& geo, co
 
 void wb_launch_wrap(const WrapList& L, const WbGeo& geo, int depth, cudaStream_t s) {
   if (L.n <= 0) return;
-  const long long n = wbu::wrap_shell_count(geo, depth);
+  const long long n = wbu::shell_count(geo, depth);
   k_wrap<<<grid_for(n, 1, 256), 256, 0, s>>>(L, geo, depth, n);
 }
 

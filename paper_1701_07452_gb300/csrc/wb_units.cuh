@@ -464,16 +464,43 @@ __device__ __forceinline__ bool in_box(const WbBox& b, int i, int j, int k) {
   return i >= b.lo[0] && i <= b.hi[0] && j >= b.lo[1] && j <= b.hi[1] && k >= b.lo[2] && k <= b.hi[2];
 }
 
+// The cheap stages are split into a load of their inputs and a finish that
+// computes and stores, so that the batch kernel can load a second item before
+// storing the first (two memory requests in flight per thread).  Their
+// arithmetic is written with explicit rounding: an item gives the same bits
+// whichever inlined copy (first or second of a pair, or alone) handles it.
+
 // Step 2: zone-centred reference EMF E = -v x B from q^n.
-__device__ __forceinline__ void eref(const WbView& v, long long qo, long long wo, int i, int j, int k) {
+struct ErefIn {
+  long long w;
+  double rho, m[3], B[3];
+};
+
+__device__ __forceinline__ void eref_load(const WbView& v, long long qo, long long wo, int i, int j, int k,
+                                          ErefIn& in) {
   const long long o = qo + wb_at(v.geo, i, j, k);
-  const long long w = wo + wb_at(v.geo, i, j, k);
-  const double ir = wb_rcp(v.q[F_RHO][o]);
-  const double vx = v.q[F_MX][o] * ir, vy = v.q[F_MY][o] * ir, vz = v.q[F_MZ][o] * ir;
-  const double bx = v.q[F_BX][o], by = v.q[F_BY][o], bz = v.q[F_BZ][o];
-  v.Eref[0][w] = vz * by - vy * bz;
-  v.Eref[1][w] = vx * bz - vz * bx;
-  v.Eref[2][w] = vy * bx - vx * by;
+  in.w = wo + wb_at(v.geo, i, j, k);
+  in.rho = v.q[F_RHO][o];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    in.m[e] = v.q[F_MX + e][o];
+    in.B[e] = v.q[F_BX + e][o];
+  }
+}
+
+__device__ __forceinline__ void eref_finish(const WbView& v, const ErefIn& in) {
+  const double ir = wb_rcp(in.rho);
+  const double vx = __dmul_rn(in.m[0], ir), vy = __dmul_rn(in.m[1], ir), vz = __dmul_rn(in.m[2], ir);
+  const double bx = in.B[0], by = in.B[1], bz = in.B[2];
+  v.Eref[0][in.w] = __fma_rn(vz, by, __dmul_rn(-vy, bz));
+  v.Eref[1][in.w] = __fma_rn(vx, bz, __dmul_rn(-vz, bx));
+  v.Eref[2][in.w] = __fma_rn(vy, bx, __dmul_rn(-vx, by));
+}
+
+__device__ __forceinline__ void eref(const WbView& v, long long qo, long long wo, int i, int j, int k) {
+  ErefIn in;
+  eref_load(v, qo, wo, i, j, k, in);
+  eref_finish(v, in);
 }
 
 // Difference x - y upwind of the mass flux m: (xm - ym) from the minus-side
@@ -497,8 +524,14 @@ __device__ __forceinline__ double upwind_diff(double m, double xm, double ym, do
 // one quarter of [(dE/db) at -3/4 minus (dE/db) at -1/4] and the same along
 // a, each derivative taken from the zone upwind of the mass flux through the
 // face it sits on (the mean of both zones when that flux is zero).
+struct EdgeIn {
+  long long o;
+  double Ea_0, Ea_m, Eb_0, Eb_m, ma_0, ma_m, mb_0, mb_m, R00, Rm0, R0m, Rmm;
+};
+
 template <int C>
-__device__ __forceinline__ void edge(const WbView& v, long long wo, bool corr, int i, int j, int k) {
+__device__ __forceinline__ void edge_load(const WbView& v, long long wo, bool corr, int i, int j, int k,
+                                          EdgeIn& in) {
   constexpr int a = (C + 1) % 3, b = (C + 2) % 3;
   const WbGeo& g = v.geo;
   const long long o = wo + wb_at(g, i, j, k);
@@ -507,39 +540,79 @@ __device__ __forceinline__ void edge(const WbView& v, long long wo, bool corr, i
   double* const* Fa = corr ? v.Fc[a] : v.Fp[a];
   double* const* Fb = corr ? v.Fc[b] : v.Fp[b];
   const double* Er = corr ? v.Erefh[C] : v.Eref[C];
-  const double Ea_0 = -Fa[F_BX + b][o];
-  const double Ea_m = -Fa[F_BX + b][o - sb];
-  const double Eb_0 = Fb[F_BX + a][o];
-  const double Eb_m = Fb[F_BX + a][o - sa];
-  const double ma_0 = Fa[F_RHO][o], ma_m = Fa[F_RHO][o - sb];
-  const double mb_0 = Fb[F_RHO][o], mb_m = Fb[F_RHO][o - sa];
-  const double R00 = Er[o], Rm0 = Er[o - sa], R0m = Er[o - sb], Rmm = Er[o - sa - sb];
-  const double db_hi = upwind_diff(ma_0, Rm0, Eb_m, R00, Eb_0);
-  const double db_lo = upwind_diff(ma_m, Eb_m, Rmm, Eb_0, R0m);
-  const double da_hi = upwind_diff(mb_0, R0m, Ea_m, R00, Ea_0);
-  const double da_lo = upwind_diff(mb_m, Ea_m, Rmm, Ea_0, Rm0);
+  in.o = o;
+  in.Ea_0 = -Fa[F_BX + b][o];
+  in.Ea_m = -Fa[F_BX + b][o - sb];
+  in.Eb_0 = Fb[F_BX + a][o];
+  in.Eb_m = Fb[F_BX + a][o - sa];
+  in.ma_0 = Fa[F_RHO][o];
+  in.ma_m = Fa[F_RHO][o - sb];
+  in.mb_0 = Fb[F_RHO][o];
+  in.mb_m = Fb[F_RHO][o - sa];
+  in.R00 = Er[o];
+  in.Rm0 = Er[o - sa];
+  in.R0m = Er[o - sb];
+  in.Rmm = Er[o - sa - sb];
+}
+
+template <int C>
+__device__ __forceinline__ void edge_finish(const WbView& v, bool corr, const EdgeIn& in) {
+  const double db_hi = upwind_diff(in.ma_0, in.Rm0, in.Eb_m, in.R00, in.Eb_0);
+  const double db_lo = upwind_diff(in.ma_m, in.Eb_m, in.Rmm, in.Eb_0, in.R0m);
+  const double da_hi = upwind_diff(in.mb_0, in.R0m, in.Ea_m, in.R00, in.Ea_0);
+  const double da_lo = upwind_diff(in.mb_m, in.Ea_m, in.Rmm, in.Ea_0, in.Rm0);
   double* out = corr ? v.Eedgeh[C] : v.Eedge[C];
-  out[o] = wb_quarter((Ea_0 + Ea_m) + (Eb_0 + Eb_m) + (db_lo - db_hi) + (da_lo - da_hi));
+  out[in.o] = wb_quarter((in.Ea_0 + in.Ea_m) + (in.Eb_0 + in.Eb_m) + (db_lo - db_hi) + (da_lo - da_hi));
+}
+
+template <int C>
+__device__ __forceinline__ void edge(const WbView& v, long long wo, bool corr, int i, int j, int k) {
+  EdgeIn in;
+  edge_load<C>(v, wo, corr, i, j, k, in);
+  edge_finish<C>(v, corr, in);
 }
 
 // Steps 4 and 11: b_out = b_in - tau curl E on the faces normal to D.
 // Step 4 writes b^{n+1/2} to the workspace, Step 11 updates b in place.
+struct CtIn {
+  long long w, q;
+  double Eb0, Eb1, Ea0, Ea1, b;
+};
+
 template <int D>
-__device__ __forceinline__ void ct(const WbView& v, long long qo, long long wo, bool fin, double dt,
-                                   int i, int j, int k) {
+__device__ __forceinline__ void ct_load(const WbView& v, long long qo, long long wo, bool fin, int i, int j,
+                                        int k, CtIn& in) {
   constexpr int a = (D + 1) % 3, b = (D + 2) % 3;
   const WbGeo& g = v.geo;
-  const long long w = wo + wb_at(g, i, j, k);
-  const long long q = qo + wb_at(g, i, j, k);
+  in.w = wo + wb_at(g, i, j, k);
+  in.q = qo + wb_at(g, i, j, k);
   const long long sa = a == 0 ? 1 : (a == 1 ? g.sy : g.sz);
   const long long sb = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
   const double* Eb = fin ? v.Eedgeh[b] : v.Eedge[b];
   const double* Ea = fin ? v.Eedgeh[a] : v.Eedge[a];
+  in.Eb0 = Eb[in.w];
+  in.Eb1 = Eb[in.w + sa];
+  in.Ea0 = Ea[in.w];
+  in.Ea1 = Ea[in.w + sb];
+  in.b = v.b[D][in.q];
+}
+
+template <int D>
+__device__ __forceinline__ void ct_finish(const WbView& v, bool fin, double dt, const CtIn& in) {
+  constexpr int a = (D + 1) % 3, b = (D + 2) % 3;
   const double tau = fin ? dt : wb_half(dt);
-  const double curl = (Eb[w + sa] - Eb[w]) * g.idx[a] - (Ea[w + sb] - Ea[w]) * g.idx[b];
-  const double bn = v.b[D][q] - tau * curl;
-  if (fin) v.b[D][q] = bn;
-  else v.bh[D][w] = bn;
+  const double curl = __fma_rn(in.Eb1 - in.Eb0, v.geo.idx[a], __dmul_rn(in.Ea0 - in.Ea1, v.geo.idx[b]));
+  const double bn = __fma_rn(-tau, curl, in.b);
+  if (fin) v.b[D][in.q] = bn;
+  else v.bh[D][in.w] = bn;
+}
+
+template <int D>
+__device__ __forceinline__ void ct(const WbView& v, long long qo, long long wo, bool fin, double dt,
+                                   int i, int j, int k) {
+  CtIn in;
+  ct_load<D>(v, qo, wo, fin, i, j, k, in);
+  ct_finish<D>(v, fin, dt, in);
 }
 
 // Steps 5 and 7: q^{n+1/2}_D = q^n - dt/2 (transverse flux divergence)
@@ -624,31 +697,59 @@ __device__ __forceinline__ void transverse_set(const WbView& v, long long qo, lo
 
 // Step 8: reference EMF at n+1/2 from v of q^n - dt/2 div F* and B = mean of
 // b^{n+1/2}.
-__device__ __forceinline__ void eref_half(const WbView& v, long long qo, long long wo, double dt,
-                                          int i, int j, int k) {
+struct ErefHalfIn {
+  long long w;
+  double q[4];        // rho, M of q^n
+  double dF[4][3];    // F*_e+ - F*_e for rho, M
+  double bh[3][2];    // b^{n+1/2} on the low and high faces
+};
+
+__device__ __forceinline__ void eref_half_load(const WbView& v, long long qo, long long wo, int i, int j,
+                                               int k, ErefHalfIn& in) {
   const WbGeo& g = v.geo;
   const long long q = qo + wb_at(g, i, j, k);
   const long long w = wo + wb_at(g, i, j, k);
   const long long s[3] = {1, g.sy, g.sz};
-  const double hdt = wb_half(dt);
-  double u[4];
-  const int comps[4] = {F_RHO, F_MX, F_MY, F_MZ};
+  in.w = w;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    double div = 0.0;
+    in.q[c] = v.q[c][q];
 #pragma unroll
-    for (int e = 0; e < 3; ++e)
-      div += (v.Fc[e][comps[c]][w + s[e]] - v.Fc[e][comps[c]][w]) * g.idx[e];
-    u[c] = v.q[comps[c]][q] - hdt * div;
+    for (int e = 0; e < 3; ++e) in.dF[c][e] = v.Fc[e][c][w + s[e]] - v.Fc[e][c][w];
+  }
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    in.bh[e][0] = v.bh[e][w];
+    in.bh[e][1] = v.bh[e][w + s[e]];
+  }
+}
+
+__device__ __forceinline__ void eref_half_finish(const WbView& v, double dt, const ErefHalfIn& in) {
+  const WbGeo& g = v.geo;
+  const double hdt = wb_half(dt);
+  double u[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double div = __dmul_rn(in.dF[c][0], g.idx[0]);
+    div = __fma_rn(in.dF[c][1], g.idx[1], div);
+    div = __fma_rn(in.dF[c][2], g.idx[2], div);
+    u[c] = __fma_rn(-hdt, div, in.q[c]);
   }
   const double ir = wb_rcp(u[0]);
-  const double vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
+  const double vx = __dmul_rn(u[1], ir), vy = __dmul_rn(u[2], ir), vz = __dmul_rn(u[3], ir);
   double B[3];
 #pragma unroll
-  for (int e = 0; e < 3; ++e) B[e] = wb_half(v.bh[e][w] + v.bh[e][w + s[e]]);
-  v.Erefh[0][w] = vz * B[1] - vy * B[2];
-  v.Erefh[1][w] = vx * B[2] - vz * B[0];
-  v.Erefh[2][w] = vy * B[0] - vx * B[1];
+  for (int e = 0; e < 3; ++e) B[e] = wb_half(in.bh[e][0] + in.bh[e][1]);
+  v.Erefh[0][in.w] = __fma_rn(vz, B[1], __dmul_rn(-vy, B[2]));
+  v.Erefh[1][in.w] = __fma_rn(vx, B[2], __dmul_rn(-vz, B[0]));
+  v.Erefh[2][in.w] = __fma_rn(vy, B[0], __dmul_rn(-vx, B[1]));
+}
+
+__device__ __forceinline__ void eref_half(const WbView& v, long long qo, long long wo, double dt,
+                                          int i, int j, int k) {
+  ErefHalfIn in;
+  eref_half_load(v, qo, wo, i, j, k, in);
+  eref_half_finish(v, dt, in);
 }
 
 // sqrt for the CFL rate; inputs below the normal range (or not > 0) give 0
@@ -753,20 +854,20 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
   return signal_rate_core(ir, vv, p, B, P, g);
 }
 
-// Periodic images of intermediates (interior-only stages of a box periodic on
-// every axis): the shell of ghost points within `depth` zones of the
-// interior, enumerated as the two z slabs of the depth-padded box, then the
-// two y slabs and the two x slabs of its interior z (and y) range.
-__host__ __device__ __forceinline__ long long wrap_shell_count(const WbGeo& g, int depth) {
+// The shell of ghost points within `depth` zones of a box's interior,
+// enumerated as the two z slabs of the depth-padded box, then the two y slabs
+// and the two x slabs of its interior z (and y) range.  Used for the periodic
+// images of intermediates (interior-only stages of a box periodic on every
+// axis) and for the ghost fill of a box that is its own domain.
+__host__ __device__ __forceinline__ long long shell_count(const WbGeo& g, int depth) {
   const long long w = 2 * depth;
   return (long long)(g.n[0] + w) * (g.n[1] + w) * w + (long long)(g.n[0] + w) * w * g.n[2] +
          w * g.n[1] * (long long)g.n[2];
 }
 
-// Shell point t (0 <= t < wrap_shell_count) -> its destination and the
-// interior point it is an image of (offsets in the padded storage).
-__device__ __forceinline__ void wrap_shell_point(const WbGeo& g, int depth, long long t, long long* dst,
-                                                 long long* src) {
+// Shell point t (0 <= t < shell_count) -> its zone index (i, j, k).
+__device__ __forceinline__ void shell_point(const WbGeo& g, int depth, long long t, int* pi, int* pj,
+                                            int* pk) {
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const int w = 2 * depth;
   const unsigned e0 = (unsigned)(n0 + w), e1 = (unsigned)(n1 + w);
@@ -795,21 +896,30 @@ __device__ __forceinline__ void wrap_shell_point(const WbGeo& g, int depth, long
     k = (int)(r / (unsigned)n1);
     i = dx < depth ? dx - depth : n0 + dx - depth;
   }
+  *pi = i;
+  *pj = j;
+  *pk = k;
+}
+
+// Shell point t -> its offset and the offset of the interior point it is a
+// periodic image of.
+__device__ __forceinline__ void wrap_shell_point(const WbGeo& g, int depth, long long t, long long* dst,
+                                                 long long* src) {
+  int i, j, k;
+  shell_point(g, depth, t, &i, &j, &k);
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   *dst = wb_at(g, i, j, k);
   *src = wb_at(g, ((i % n0) + n0) % n0, ((j % n1) + n1) % n1, ((k % n2) + n2) % n2);
 }
 
 // Ghost fill of a box that is its own periodic/outflow domain (no patches):
-// padded index t outside the interior copies the wrapped/clamped interior
-// zone of the same box (all 11 fields).
-__device__ __forceinline__ void halo_self(const WbView& v, long long qo, const int bc[3], long long t) {
-  const WbGeo& g = v.geo;
-  const int i = (int)(t % g.pd[0]) - WB_NG;
-  const long long r = t / g.pd[0];
-  const int j = (int)(r % g.pd[1]) - WB_NG;
-  const int k = (int)(r / g.pd[1]) - WB_NG;
-  if (i >= 0 && i < g.n[0] && j >= 0 && j < g.n[1] && k >= 0 && k < g.n[2]) return;
-  int loc[3] = {i, j, k};
+// ghost point t of the 5-zone shell (shell_point order) copies the wrapped
+// (periodic) or clamped (outflow) interior zone of the same box, all 11
+// fields; face arrays use the same rule on their face index.
+__device__ __forceinline__ void halo_self_offsets(const WbGeo& g, const int bc[3], long long t, long long* dst,
+                                                  long long* src_off) {
+  int loc[3];
+  shell_point(g, WB_NG, t, &loc[0], &loc[1], &loc[2]);
   int src[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -821,8 +931,15 @@ __device__ __forceinline__ void halo_self(const WbView& v, long long qo, const i
     }
     src[d] = x;
   }
-  const long long dst = qo + t;
-  const long long so = qo + wb_at(g, src[0], src[1], src[2]);
+  *dst = wb_at(g, loc[0], loc[1], loc[2]);
+  *src_off = wb_at(g, src[0], src[1], src[2]);
+}
+
+__device__ __forceinline__ void halo_self(const WbView& v, long long qo, const int bc[3], long long t) {
+  long long dst, so;
+  halo_self_offsets(v.geo, bc, t, &dst, &so);
+  dst += qo;
+  so += qo;
 #pragma unroll
   for (int c = 0; c < 8; ++c) v.q[c][dst] = v.q[c][so];
 #pragma unroll
