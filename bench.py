@@ -44,9 +44,14 @@ N_BOX = 256
 SEED = 2
 # FP64 flops (DFMA = 2, DMUL = DADD = 1) the MHDTVD sweep executes per interface
 # system it computes, from the ncu FP64 instruction counters of k_sweep on the
-# 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full_v4.md): 552 M flops
-# over 9604 pencils x 107 interface systems.
-FLOPS_PER_FACE = 537.0
+# 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full.md): 492 M flops over
+# 9216 pencils x 4 segments x 26 interface systems.
+FLOPS_PER_FACE = 513.0
+# DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the mean
+# of the six sweeps of a step from one ncu capture of this kernel
+# (profiles/k_sweep_256cube_dram.md); the algorithmic figure is 128 B per face.
+SWEEP_DRAM_BYTES_256 = 3.197e9
+SWEEP_BYTES_PER_FACE = 128.0
 # FP64 issue rate of one GB300 SM: 2 DFMA per clock (measured with the DFMA
 # probe: 1196 GFLOP/s at 1995 MHz on 152 SMs), i.e. 4 flops per clock per SM.
 FP64_FLOPS_PER_CLK_PER_SM = 4.0
@@ -432,7 +437,10 @@ def main():
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": args.e2e_steps},
             "roofline": {"bound": "alu", "kernel": "k_sweep (MHDTVD flux)", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": SWEEP_DRAM_BYTES_256 if n == 256 else None,
+                         "algorithmic_bytes": SWEEP_BYTES_PER_FACE * faces_per_launch,
+                         "flops_per_face": FLOPS_PER_FACE,
                          "peak_source": "SMs x 2 DFMA/clk x 2 flops x median SM clock under load; "
                                         "DFMA probe in this process: %.3f TFLOP/s" % (fp64_peak / 1e12),
                          "sweep_ms_per_launch": per_launch_ms,
