@@ -122,7 +122,10 @@ int wb_grid_create(const wb_desc* d, void* dev_mem, size_t bytes, void* stream,
 int wb_grid_destroy(wb_grid* g);
 
 /* Load conserved U and faces bx, by, bz (layouts above).  on_device != 0:
- * the pointers are device memory, else host memory (pinned for overlap).
+ * the pointers are device memory, else host memory.  A host array in
+ * page-locked memory the GPU can address (cudaHostAlloc, cudaHostRegister)
+ * is read in place by the scatter kernel over the CPU-GPU link; any other
+ * host array goes through a staging copy.  The call synchronises the stream.
  * The zone field is set to the face averages; the high boundary face of
  * each axis is taken from the ghost fill (periodic: face 0). */
 int wb_load_state(wb_grid* g, const double* U, const double* bx, const double* by,
@@ -146,12 +149,16 @@ int wb_compute_dt(wb_grid* g, double* dt);
  * returns WB_ERR_UNPHYSICAL. */
 int wb_advance(wb_grid* g, int nsteps, double t_end, double* t_out);
 
-/* Read back the state (any pointer may be NULL); on_device as for load. */
+/* Read back the state (any pointer may be NULL); on_device as for load
+ * (page-locked host arrays are written in place by the gather kernel).
+ * With host arrays the call synchronises the stream. */
 int wb_read_state(wb_grid* g, double* U, double* bx, double* by, double* bz, double* B,
                   int on_device);
 
 /* Conserved totals times zone volume: rho, Mx, My, Mz, E over zones and
- * bx, by, bz over owned faces (compensated summation on the host). */
+ * bx, by, bz over owned faces (the low face of each zone).  Compensated
+ * (Neumaier) sums in a fixed-order reduction on the device: the same state
+ * gives the same totals bit for bit.  Synchronises the stream. */
 int wb_conserved_totals(wb_grid* g, double tot[8]);
 /* max over zones of |div b| with the face differences of Step 11. */
 int wb_divb_max(wb_grid* g, double* divb);

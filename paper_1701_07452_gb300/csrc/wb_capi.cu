@@ -43,8 +43,8 @@ struct wb_grid {
   unsigned long long* red;
   std::string err;
   bool loaded;
-  // interior-only stages with periodic images of the intermediates (a single
-  // patch periodic on every axis, 3D storage)
+  // interior-only stages with periodic images of the intermediates: periodic
+  // on every axis, 3D storage, every patch in one pass
   bool wrap = false;
   // sweep timing (wb_profile_sweeps)
   bool prof;
@@ -116,6 +116,10 @@ WbGeo make_geo(const wb_desc* d) {
 
 const int kWorkArrays = 3 * 7 + 3 * 7 + 3 + 3 + 3 + 3 * 8 + 3 + 3;  // 81
 
+// blocks of the conserved-totals reduction (a fixed count: the summation
+// order, and so the result, do not depend on the device)
+constexpr int kTotalsBlocks = 256;
+
 Layout layout(const wb_desc* d) {
   Layout L;
   WbGeo g = make_geo(d);
@@ -128,7 +132,9 @@ Layout layout(const wb_desc* d) {
   L.work = align_up(sizeof(double) * (size_t)L.V * S * kWorkArrays);
   size_t gmax = (size_t)(d->n[0] + 1) * (d->n[1] + 1) * (d->n[2] + 1);
   L.staging = align_up(sizeof(double) * gmax);
-  L.scalars = align_up(sizeof(WbScalars) + 64 * sizeof(unsigned long long));
+  // device scalars, 64 reduction words, the 8 totals and the totals' partials
+  L.scalars = align_up(sizeof(WbScalars) + 64 * sizeof(unsigned long long) +
+                       sizeof(double) * (8 + 16 * kTotalsBlocks));
   L.total = L.state + L.work + L.staging + L.scalars;
   return L;
 }
@@ -243,33 +249,36 @@ WrapList wrap_list(std::initializer_list<double*> arrays) {
   return L;
 }
 
-// One step of a single-patch box periodic on every axis.  Every stage runs on
-// the interior index range only; between stages the ghost points a later
-// stage reads (1 deep, 2 for the preconditioned states the corrector sweeps
-// read) are filled with periodic images.  On one GPU the copies cost a small
+// One step of a grid periodic on every axis whose patches all sit in one
+// pass (a single patch, or every patch resident: slot = patch).  Every stage
+// runs on the interior index range of each patch only; between stages the
+// ghost points a later stage reads (1 deep, 2 for the preconditioned states
+// the corrector sweeps read) are filled with periodic images, from the
+// neighbouring patch where there is one.  On one GPU the copies cost a small
 // fraction of recomputing the ghost rings, which the 5-zone scheme (one
 // exchange per step) otherwise does at every stage.
 void enqueue_pass_wrap(wb_grid* g) {
   cudaStream_t s = g->stream;
-  StageArgs A = stage_args(g, 0, 1);
+  const int ns = (int)g->npatch;
+  StageArgs A = stage_args(g, 0, ns);
   const WbGeo& G = g->geo;
   const int N0 = G.n[0], N1 = G.n[1], N2 = G.n[2];
   const WbBox in = box(0, N0 - 1, 0, N1 - 1, 0, N2 - 1);
   const WbBox in3[3] = {in, in, in};
   // Step 1: predictor fluxes on the interior faces (face N_d is face 0)
-  for (int d = 0; d < 3; ++d) sweep(g, d, sweep_args(g, A, d, false, in), 1);
+  for (int d = 0; d < 3; ++d) sweep(g, d, sweep_args(g, A, d, false, in), ns);
   // Step 2: reference EMF; then the images of both
   wb_launch_eref(A, in, s);
   wb_launch_wrap(wrap_list({g->Fp[0][0], g->Fp[0][1], g->Fp[0][2], g->Fp[0][3], g->Fp[0][4], g->Fp[0][6],
                             g->Fp[0][7], g->Fp[1][0], g->Fp[1][1], g->Fp[1][2], g->Fp[1][3], g->Fp[1][4],
                             g->Fp[1][5], g->Fp[1][7], g->Fp[2][0], g->Fp[2][1], g->Fp[2][2], g->Fp[2][3],
                             g->Fp[2][4], g->Fp[2][5], g->Fp[2][6], g->Eref[0], g->Eref[1], g->Eref[2]}),
-                 G, 1, s);
+                 G, g->map, 1, s);
   // Step 3: corner EMFs; Step 4: b^{n+1/2}
   wb_launch_edges(A, false, in3, s);
-  wb_launch_wrap(wrap_list({g->Eedge[0], g->Eedge[1], g->Eedge[2]}), G, 1, s);
+  wb_launch_wrap(wrap_list({g->Eedge[0], g->Eedge[1], g->Eedge[2]}), G, g->map, 1, s);
   wb_launch_ct(A, false, in3, s);
-  wb_launch_wrap(wrap_list({g->bh[0], g->bh[1], g->bh[2]}), G, 1, s);
+  wb_launch_wrap(wrap_list({g->bh[0], g->bh[1], g->bh[2]}), G, g->map, 1, s);
   // Steps 5, 7: preconditioned states (the corrector sweeps read 2 zones out)
   wb_launch_transverse(A, in3, s);
   {
@@ -277,20 +286,20 @@ void enqueue_pass_wrap(wb_grid* g) {
     for (int d = 0; d < 3; ++d)
       for (int c = 0; c < 8; ++c)
         if (g->qh[d][c]) L.a[L.n++] = g->qh[d][c];
-    wb_launch_wrap(L, G, 2, s);
+    wb_launch_wrap(L, G, g->map, 2, s);
   }
   // Steps 6, 7: corrector fluxes
-  for (int d = 0; d < 3; ++d) sweep(g, d, sweep_args(g, A, d, true, in), 1);
+  for (int d = 0; d < 3; ++d) sweep(g, d, sweep_args(g, A, d, true, in), ns);
   wb_launch_wrap(wrap_list({g->Fc[0][0], g->Fc[0][1], g->Fc[0][2], g->Fc[0][3], g->Fc[0][4], g->Fc[0][6],
                             g->Fc[0][7], g->Fc[1][0], g->Fc[1][1], g->Fc[1][2], g->Fc[1][3], g->Fc[1][4],
                             g->Fc[1][5], g->Fc[1][7], g->Fc[2][0], g->Fc[2][1], g->Fc[2][2], g->Fc[2][3],
                             g->Fc[2][4], g->Fc[2][5], g->Fc[2][6]}),
-                 G, 1, s);
+                 G, g->map, 1, s);
   // Step 8: half-step reference EMF; Step 9: corner EMFs
   wb_launch_eref_half(A, in, s);
-  wb_launch_wrap(wrap_list({g->Erefh[0], g->Erefh[1], g->Erefh[2]}), G, 1, s);
+  wb_launch_wrap(wrap_list({g->Erefh[0], g->Erefh[1], g->Erefh[2]}), G, g->map, 1, s);
   wb_launch_edges(A, true, in3, s);
-  wb_launch_wrap(wrap_list({g->Eedgeh[0], g->Eedgeh[1], g->Eedgeh[2]}), G, 1, s);
+  wb_launch_wrap(wrap_list({g->Eedgeh[0], g->Eedgeh[1], g->Eedgeh[2]}), G, g->map, 1, s);
   // Step 11 (faces, the high boundary face included), then Step 10
   {
     WbBox bb[3] = {box(0, N0, 0, N1 - 1, 0, N2 - 1), box(0, N0 - 1, 0, N1, 0, N2 - 1),
@@ -361,6 +370,24 @@ int sync(wb_grid* g, const char* where) {
   return check_cuda(g, cudaStreamSynchronize(g->stream), where);
 }
 
+// Device address of a host array of n doubles that lives in page-locked host
+// memory the GPU can address (cudaHostAlloc / cudaHostRegister), or null.
+// Kernels then read or write it in place over the CPU-GPU link instead of
+// going through a staging copy; both ends of the array are checked.
+const void* host_mapped(const void* p, long long n) {
+  if (!p || n <= 0) return nullptr;
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  const char* last = static_cast<const char*>(p) + sizeof(double) * (size_t)(n - 1);
+  if (cudaPointerGetAttributes(&a1, last) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost) return nullptr;
+  if (!a0.devicePointer || !a1.devicePointer) return nullptr;
+  const char* d0 = static_cast<const char*>(a0.devicePointer);
+  const char* d1 = static_cast<const char*>(a1.devicePointer);
+  if (d1 - d0 != last - static_cast<const char*>(p)) return nullptr;
+  return a0.devicePointer;
+}
+
 int load_common(wb_grid* g, const double* U, const double* bx, const double* by,
                 const double* bz, int on_device, bool primitive) {
   if (!g || !U || !bx || !by || !bz) return fail(g, WB_ERR_INVALID, "null argument");
@@ -374,14 +401,17 @@ int load_common(wb_grid* g, const double* U, const double* bx, const double* by,
     else { ext[comp - 5] += 1; src = faces[comp - 5]; }
     long long n = ext[0] * ext[1] * ext[2];
     const double* dsrc = src;
-    if (!on_device) {
+    const void* mapped = on_device ? nullptr : host_mapped(src, n);
+    const bool staged = !on_device && !mapped;
+    if (mapped) dsrc = static_cast<const double*>(mapped);
+    if (staged) {
       cudaError_t e = cudaMemcpyAsync(g->staging, src, sizeof(double) * n, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) return check_cuda(g, e, "load copy");
       dsrc = g->staging;
     }
     double* dst = comp < 5 ? g->q[comp] : g->b[comp - 5];
     wb_launch_scatter(dsrc, dst, comp, g->geo, g->map, s);
-    if (!on_device) {
+    if (staged) {
       // staging is reused by the next component
       int rc = sync(g, "load");
       if (rc) return rc;
@@ -448,7 +478,7 @@ int wb_grid_create(const wb_desc* d, void* dev_mem, size_t bytes, void* stream, 
   }
   g->map.npatch = L.npatch;
   g->npatch = L.npatch;
-  g->wrap = L.npatch == 1 && !flat_z(d) && d->bc[0] == WB_BC_PERIODIC && d->bc[1] == WB_BC_PERIODIC &&
+  g->wrap = L.S == L.npatch && !flat_z(d) && d->bc[0] == WB_BC_PERIODIC && d->bc[1] == WB_BC_PERIODIC &&
             d->bc[2] == WB_BC_PERIODIC;
   g->S = L.S;
   g->phys = wb_phys_of(d);
@@ -616,61 +646,37 @@ int wb_read_state(wb_grid* g, double* U, double* bx, double* by, double* bz, dou
       dst = B + (comp - 8) * nc; src = g->q[F_BX + comp - 8]; mcomp = 0;
     }
     long long n = ext[0] * ext[1] * ext[2];
-    double* ddst = on_device ? dst : g->staging;
+    const void* mapped = on_device ? nullptr : host_mapped(dst, n);
+    const bool staged = !on_device && !mapped;
+    double* ddst = on_device ? dst : (mapped ? static_cast<double*>(const_cast<void*>(mapped)) : g->staging);
     wb_launch_gather(src, ddst, mcomp, g->geo, g->map, s);
-    if (!on_device) {
+    if (staged) {
       cudaError_t e = cudaMemcpyAsync(dst, g->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return check_cuda(g, e, "read");
     }
+  }
+  // host arrays written in place by the kernels are complete once the stream is
+  if (!on_device) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return check_cuda(g, e, "read");
   }
   return check_cuda(g, cudaGetLastError(), "read");
 }
 
 int wb_conserved_totals(wb_grid* g, double tot[8]) {
   if (!g || !tot) return fail(g, WB_ERR_INVALID, "null argument");
+  if (!g->loaded) return fail(g, WB_ERR_INVALID, "no state loaded");
   const int nx = g->d.n[0], ny = g->d.n[1], nz = g->d.n[2];
-  const long long nc = (long long)nx * ny * nz;
-  std::vector<double> U(5 * nc), bx((size_t)(nx + 1) * ny * nz), by((size_t)nx * (ny + 1) * nz),
-      bz((size_t)nx * ny * (nz + 1));
-  int rc = wb_read_state(g, U.data(), bx.data(), by.data(), bz.data(), nullptr, 0);
-  if (rc) return rc;
-  double vol = (g->d.length[0] / nx) * (g->d.length[1] / ny) * (g->d.length[2] / nz);
-  auto neumaier = [](const double* x, long long n, long long stride_skip, long long period) {
-    double s = 0.0, c = 0.0;
-    for (long long i = 0; i < n; ++i) {
-      if (period > 0 && (i % period) == stride_skip) continue;
-      double t = s + x[i];
-      if (std::fabs(s) >= std::fabs(x[i])) c += (s - t) + x[i];
-      else c += (x[i] - t) + s;
-      s = t;
-    }
-    return s + c;
-  };
-  for (int c = 0; c < 5; ++c) tot[c] = neumaier(U.data() + c * nc, nc, -1, 0) * vol;
-  // owned faces only: skip the high boundary face of the face axis
-  {
-    double s = 0.0, cc = 0.0;
-    for (long long i = 0; i < (long long)bx.size(); ++i) {
-      if (i % (nx + 1) == nx) continue;
-      double t = s + bx[i];
-      if (std::fabs(s) >= std::fabs(bx[i])) cc += (s - t) + bx[i]; else cc += (bx[i] - t) + s;
-      s = t;
-    }
-    tot[5] = (s + cc) * vol;
-  }
-  {
-    double s = 0.0, cc = 0.0;
-    for (long long i = 0; i < (long long)by.size(); ++i) {
-      if ((i / nx) % (ny + 1) == ny) continue;
-      double t = s + by[i];
-      if (std::fabs(s) >= std::fabs(by[i])) cc += (s - t) + by[i]; else cc += (by[i] - t) + s;
-      s = t;
-    }
-    tot[6] = (s + cc) * vol;
-  }
-  tot[7] = neumaier(bz.data(), (long long)nx * ny * nz, -1, 0) * vol;
-  return WB_OK;
+  const double vol = (g->d.length[0] / nx) * (g->d.length[1] / ny) * (g->d.length[2] / nz);
+  double* out = reinterpret_cast<double*>(g->red + 64);
+  double* part = out + 8;
+  cudaStream_t s = g->stream;
+  wb_launch_totals(g->q, g->b, g->geo, g->npatch, vol, part, kTotalsBlocks, out, s);
+  cudaError_t e = cudaMemcpyAsync(tot, out, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return check_cuda(g, e, "totals");
+  return check_cuda(g, cudaGetLastError(), "totals");
 }
 
 int wb_divb_max(wb_grid* g, double* divb) {

@@ -59,7 +59,9 @@ struct WrapList {
   double* a[24];
   int n;
 };
-void wb_launch_wrap(const WrapList& L, const WbGeo& geo, int depth, cudaStream_t s);
+// Periodic images on every axis: one patch (the box's own interior) or all
+// patches of a grid resident in one pass (slot = patch, neighbour patches).
+void wb_launch_wrap(const WrapList& L, const WbGeo& geo, const GridMap& m, int depth, cudaStream_t s);
 void wb_launch_dt_init(double* const q[8], const WbGeo& geo, long long npatch, const WbPhys& ph,
                        WbScalars* scal, cudaStream_t s);
 void wb_launch_dt_step(WbScalars* scal, double cfl, double t_end, int lag, cudaStream_t s);
@@ -72,6 +74,10 @@ void wb_launch_scatter(const double* src, double* dst_field, int comp, const WbG
                        const GridMap& m, cudaStream_t s);
 void wb_launch_gather(const double* src_field, double* dst, int comp, const WbGeo& geo,
                       const GridMap& m, cudaStream_t s);
+// Conserved totals: nblocks partial pairs in part (16 doubles each), the 8
+// totals x vol in out (device memory).
+void wb_launch_totals(double* const q[8], double* const b[3], const WbGeo& geo, long long npatch, double vol,
+                      double* part, int nblocks, double* out, cudaStream_t s);
 void wb_launch_divb(double* const b[3], const WbGeo& geo, long long npatch,
                     unsigned long long* out_bits, cudaStream_t s);
 void wb_launch_copy_box(const double* src, long long slot, const WbGeo& geo, const WbBox& box,

@@ -107,6 +107,36 @@ __global__ void k_wrap(WrapList L, WbGeo g, int depth, long long n) {
   for (int a = 0; a < L.n; ++a) L.a[a][dst] = L.a[a][src];
 }
 
+// The same for a grid of patches periodic on every axis, all patches resident
+// (slot = patch): a ghost point of patch blockIdx.y takes the value the
+// neighbouring patch (periodic across the domain) holds at that global
+// position.
+__global__ void k_wrap_patches(WrapList L, WbGeo g, GridMap m, int depth, long long n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const long long p = blockIdx.y;
+  int loc[3];
+  wbu::shell_point(g, depth, t, &loc[0], &loc[1], &loc[2]);
+  long long pc[3];
+  pc[0] = p % m.np[0];
+  pc[1] = (p / m.np[0]) % m.np[1];
+  pc[2] = p / ((long long)m.np[0] * m.np[1]);
+  long long sp = 0, mul = 1;
+  int sl[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    long long G = pc[d] * g.n[d] + loc[d];
+    G = ((G % m.N[d]) + m.N[d]) % m.N[d];
+    const long long q = G / g.n[d];
+    sl[d] = (int)(G - q * g.n[d]);
+    sp += q * mul;
+    mul *= m.np[d];
+  }
+  const long long dst = p * g.V + wb_at(g, loc[0], loc[1], loc[2]);
+  const long long src = sp * g.V + wb_at(g, sl[0], sl[1], sl[2]);
+  for (int a = 0; a < L.n; ++a) L.a[a][dst] = L.a[a][src];
+}
+
 __device__ __forceinline__ void block_max_atomic(double w, unsigned long long* dst) {
   // warp-shuffle max, then one atomic per warp (exact, order independent)
   unsigned long long bits = (w >= 0.0) ? (unsigned long long)__double_as_longlong(w)
@@ -314,6 +344,77 @@ __global__ void k_divb(StageArgs A, long long npatch, unsigned long long* out) {
   block_max_atomic(w, out);
 }
 
+// Conserved totals (diagnostic): compensated sums over the interior zones of
+// every patch of rho, M, E and of the owned faces of b (the low face of each
+// zone).  Each thread keeps a Neumaier pair (sum, compensation) per quantity
+// over a strided range of zones; a block combines its pairs in a fixed tree
+// and writes one partial per quantity; k_totals_final combines the partials
+// in block order.  The grid size is fixed, so the result does not depend on
+// timing.
+constexpr int kTotBlock = 256;
+
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
+  const double t = s + x;
+  const bool big = !wb_abs_less(s, x);  // |s| >= |x|
+  const double a = big ? s : x, b = big ? x : s;
+  c += (a - t) + b;
+  s = t;
+}
+
+__global__ void __launch_bounds__(kTotBlock) k_totals(StageArgs A, long long npatch, double* part) {
+  __shared__ double ss[8][kTotBlock], sc[8][kTotBlock];
+  const WbGeo& g = A.v.geo;
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  double s[8], c[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s[q] = c[q] = 0.0;
+  const long long stride = (long long)gridDim.x * kTotBlock;
+  for (long long t = blockIdx.x * (long long)kTotBlock + threadIdx.x; t < nint * npatch; t += stride) {
+    const long long p = t / nint, r = t % nint;
+    const int i = (int)(r % g.n[0]);
+    const int j = (int)((r / g.n[0]) % g.n[1]);
+    const int k = (int)(r / ((long long)g.n[0] * g.n[1]));
+    const long long o = p * g.V + wb_at(g, i, j, k);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) neumaier_add(s[q], c[q], A.v.q[q][o]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) neumaier_add(s[5 + q], c[5 + q], A.v.b[q][o]);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    ss[q][threadIdx.x] = s[q];
+    sc[q][threadIdx.x] = c[q];
+  }
+  __syncthreads();
+  for (int h = kTotBlock / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        double a = ss[q][threadIdx.x], ca = sc[q][threadIdx.x] + sc[q][threadIdx.x + h];
+        neumaier_add(a, ca, ss[q][threadIdx.x + h]);
+        ss[q][threadIdx.x] = a;
+        sc[q][threadIdx.x] = ca;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) {
+    part[(size_t)blockIdx.x * 16 + threadIdx.x] = ss[threadIdx.x][0];
+    part[(size_t)blockIdx.x * 16 + 8 + threadIdx.x] = sc[threadIdx.x][0];
+  }
+}
+
+__global__ void k_totals_final(const double* part, int nblocks, double vol, double* out) {
+  const int q = threadIdx.x;
+  if (q >= 8) return;
+  double s = 0.0, c = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    c += part[(size_t)b * 16 + 8 + q];
+    neumaier_add(s, c, part[(size_t)b * 16 + q]);
+  }
+  out[q] = (s + c) * vol;
+}
+
 __global__ void k_copy_box(const double* src, long long slot, WbGeo g, WbBox box, double* dst) {
   int i, j, k;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -388,10 +489,11 @@ void wb_launch_halo(double* const q[8], double* const b[3], const WbGeo& geo, co
   k_halo<<<grid_for(geo.V, (int)m.npatch, 256), 256, 0, s>>>(a, m);
 }
 
-void wb_launch_wrap(const WrapList& L, const WbGeo& geo, int depth, cudaStream_t s) {
+void wb_launch_wrap(const WrapList& L, const WbGeo& geo, const GridMap& m, int depth, cudaStream_t s) {
   if (L.n <= 0) return;
   const long long n = wbu::shell_count(geo, depth);
-  k_wrap<<<grid_for(n, 1, 256), 256, 0, s>>>(L, geo, depth, n);
+  if (m.npatch == 1) k_wrap<<<grid_for(n, 1, 256), 256, 0, s>>>(L, geo, depth, n);
+  else k_wrap_patches<<<grid_for(n, (int)m.npatch, 256), 256, 0, s>>>(L, geo, m, depth, n);
 }
 
 void wb_launch_dt_init(double* const q[8], const WbGeo& geo, long long npatch, const WbPhys& ph,
@@ -444,6 +546,13 @@ void wb_launch_divb(double* const b[3], const WbGeo& geo, long long npatch,
   StageArgs a = mini_args(q, b, geo);
   long long n = (long long)geo.n[0] * geo.n[1] * geo.n[2] * npatch;
   k_divb<<<grid_for(n, 1, 256), 256, 0, s>>>(a, npatch, out_bits);
+}
+
+void wb_launch_totals(double* const q[8], double* const b[3], const WbGeo& geo, long long npatch, double vol,
+                      double* part, int nblocks, double* out, cudaStream_t s) {
+  StageArgs a = mini_args(q, b, geo);
+  k_totals<<<nblocks, kTotBlock, 0, s>>>(a, npatch, part);
+  k_totals_final<<<1, 32, 0, s>>>(part, nblocks, vol, out);
 }
 
 void wb_launch_copy_box(const double* src, long long slot, const WbGeo& geo, const WbBox& box,
