@@ -67,6 +67,10 @@ def step_launches(desc):
     return 2 + 14 * (-(-npatch // per_pass))
 
 
+def workload_name(n):
+    return f"{n}^3 periodic FP64 MHD turbulence box, CTU+CT MHDTVD step"
+
+
 def sweep_faces_per_step(n):
     """Interfaces the six sweeps of one step must compute (one per zone and
     direction, predictor and corrector) -- the algorithmic count; the kernel
@@ -183,7 +187,7 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{N_BOX}^3 periodic FP64 MHD turbulence box (CTU+CT MHDTVD)",
+        "config": {"workload": workload_name(N_BOX), "patches": "1 (single grid)",
                    "sample": f"{n_sample}^3 box of the same turbulence data, {steps_per} step per bench step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                          "sample": f"{n_sample}^3 x {steps_per} step per bench step"},
@@ -440,7 +444,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded turbulence IC, no dataset)",
-            "config": {"workload": f"{n}^3 periodic FP64 MHD turbulence box, CTU+CT MHDTVD step",
+            "config": {"workload": workload_name(n),
                        "patches": "1 (single grid)", "l2": "state 1.6 GB > L2, no flush",
                        "parallelism": "replicas only" if world > 1 else "1 GPU"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -484,6 +484,7 @@ __device__ void box_dt(const BatchParams& B, int box) {
   s->steps += 1;
   if (B.dt_lag) s->wmax_lag = s->wmax_next;
   s->wmax_next = 0ULL;
+  s->rate_screen = 0u;
   B.steps_left[box] -= 1;
 }
 
@@ -582,7 +583,7 @@ __global__ void k_box_rate(WbView v, WbScalars* scal, WbPhys P) {
     const int k = (int)(t / ((long long)g.n[0] * g.n[1]));
     const long long o = wb_at(g, i, j, k);
     w = wbu::signal_rate(v.q[0][o], v.q[1][o], v.q[2][o], v.q[3][o], v.q[4][o], v.q[5][o], v.q[6][o],
-                         v.q[7][o], P, g);
+                         v.q[7][o], P, g, scal);
   }
   warp_max_atomic(w, &scal->wmax_next);
 }

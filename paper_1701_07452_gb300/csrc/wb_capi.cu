@@ -144,6 +144,7 @@ Layout layout(const wb_desc* d) {
 WbPhys wb_phys_of(const wb_desc* d) {
   WbPhys p;
   p.gamma = d->gamma;
+  p.gamma_f = (float)d->gamma;
   p.gm1 = d->gamma - 1.0;
   p.gm2 = d->gamma - 2.0;
   p.hgm2 = 0.5 * (d->gamma - 2.0);

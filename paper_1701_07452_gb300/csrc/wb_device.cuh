@@ -11,6 +11,7 @@ enum { F_RHO = 0, F_MX = 1, F_MY = 2, F_MZ = 3, F_EN = 4, F_BX = 5, F_BY = 6, F_
 
 struct WbPhys {
   double gamma, gm1, gm2, g_over_gm1, inv_gm1, gm2_over_gm1, cfl;
+  float gamma_f;  // gamma for the FP32 screen of the signal rate
   double hgm2;  // (gamma - 2) / 2
   double eps[7], two_eps[7], inv4eps[7];
   int eps_zero;  // bit k set when eps_k == 0
@@ -50,6 +51,8 @@ struct WbScalars {
   double t;               // time since load
   unsigned long long wmax_lag;   // lagged dt: signal rate of the previous step's start state (0: none)
   unsigned long long wmax_next;  // accumulated by the final update for the next step
+  unsigned int rate_screen;      // running max of the FP32 screen of the signal rate (float bits)
+  unsigned int pad_;
   long long steps;
   long long floor_hits;
   long long unphysical;

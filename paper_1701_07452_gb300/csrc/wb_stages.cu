@@ -219,7 +219,7 @@ __global__ void k_dt_init(StageArgs A, long long npatch) {
     int k = (int)(r / ((long long)g.n[0] * g.n[1]));
     long long o = p * g.V + wb_at(g, i, j, k);
     w = wbu::signal_rate(A.v.q[0][o], A.v.q[1][o], A.v.q[2][o], A.v.q[3][o], A.v.q[4][o], A.v.q[5][o], A.v.q[6][o],
-                    A.v.q[7][o], A.phys, g);
+                    A.v.q[7][o], A.phys, g, A.v.scal);
     if (!(w >= 0.0)) w = __longlong_as_double(0x7ff8000000000000LL);
   }
   block_max_atomic(w, &A.v.scal->wmax_next);
@@ -257,6 +257,7 @@ __global__ void k_dt_step(WbScalars* s, double cfl, double t_end, int lag) {
   if (lag) s->wmax_lag = s->wmax_next;
   s->steps += 1;
   s->wmax_next = 0ULL;
+  s->rate_screen = 0u;
 }
 
 __global__ void k_ccb(StageArgs A, long long npatch) {

@@ -783,24 +783,89 @@ __device__ __forceinline__ double signal_rate_core(double ir, const double vv[3]
   return w;
 }
 
+// FP32 copy of a double by exponent re-biasing and mantissa truncation on the
+// integer pipe (relative error below 2^-23).  Zero maps to zero; magnitudes
+// outside [2^-60, 2^61), subnormals, inf and NaN clear *ok.
+__device__ __forceinline__ float wb_f32_of(double x, bool* ok) {
+  const long long b = __double_as_longlong(x);
+  if ((b << 1) == 0) return 0.0f;
+  const int hi = (int)(b >> 32);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (ex < 1023 - 60 || ex > 1023 + 60) {
+    *ok = false;
+    return 0.0f;
+  }
+  const unsigned sign = (unsigned)hi & 0x80000000u;
+  const unsigned mant = (unsigned)((b >> 29) & 0x7fffff);
+  return __uint_as_float(sign | ((unsigned)(ex - 1023 + 127) << 23) | mant);
+}
+
+// The CFL signal rate in FP32 (same formula as signal_rate_core, relative
+// error well below 1e-5 for inputs the conversion accepts; *ok cleared when it
+// cannot vouch for one).  p enters already computed in FP64, so the rate has
+// no cancellation left: every term of the sum and of the discriminant is
+// non-negative except a^2 - c_n^2, which only enters squared.
+__device__ __forceinline__ float signal_rate_f32(double ir, const double vv[3], double p, const double B[3],
+                                                 const WbPhys& P, const WbGeo& g, bool* ok) {
+  const float fir = wb_f32_of(ir, ok), fp = wb_f32_of(p, ok);
+  float fv[3], sq[3], fidx[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    fv[d] = fabsf(wb_f32_of(vv[d], ok));
+    const float b = wb_f32_of(B[d], ok);
+    sq[d] = b * b;
+    fidx[d] = wb_f32_of(g.idx[d], ok);
+  }
+  const float a2 = P.gamma_f * fp * fir;
+  float w = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float cn2 = sq[d] * fir;
+    const float ct2 = (sq[(d + 1) % 3] + sq[(d + 2) % 3]) * fir;
+    const float dd = a2 - cn2;
+    const float disc = dd * dd + ct2 * (ct2 + 2.0f * (a2 + cn2));
+    const float cf = sqrtf(0.5f * (a2 + cn2 + ct2 + sqrtf(disc)));
+    w += (fv[d] + cf) * fidx[d];
+  }
+  return w;
+}
+
+// The zone's exact (FP64) signal rate when it could be the largest of the
+// box, else 0.  The max over zones is all the time step needs: a zone whose
+// FP32 screen r32 lies below 0.9999 of the running maximum of the screens
+// already seen cannot hold the largest exact rate (with screen errors e < 1e-5,
+// the largest exact rate R* has r32 >= R*(1 - e) while the running maximum
+// is <= R*(1 + e)), so it skips the FP64 evaluation.  The maximum of the
+// returned values is bit-identical to the maximum of signal_rate_core over
+// all zones.
+__device__ __forceinline__ double screened_rate(double ir, const double vv[3], double p, const double B[3],
+                                                const WbPhys& P, const WbGeo& g, WbScalars* scal) {
+  bool ok = true;
+  const float r32 = signal_rate_f32(ir, vv, p, B, P, g, &ok);
+  const float G = __uint_as_float(*(volatile unsigned*)&scal->rate_screen);
+  if (ok && r32 < 0.9999f * G) return 0.0;
+  if (ok && r32 > G) atomicMax(&scal->rate_screen, __float_as_uint(r32));
+  return signal_rate_core(ir, vv, p, B, P, g);
+}
+
 // kinetic energy density rho v^2 / 2 from the momentum and the velocity
 __device__ __forceinline__ double kinetic(const double m[3], const double vv[3]) {
   return wb_half(fma(m[2], vv[2], fma(m[1], vv[1], m[0] * vv[0])));
 }
 
-// The signal rate of one stored zone (conserved state and zone field).
+// The signal rate of one stored zone (conserved state and zone field), or 0
+// when the screen shows it cannot be the box's largest (screened_rate).
 __device__ __forceinline__ double signal_rate(double rho, double mx, double my, double mz, double e,
                                               double bx, double by, double bz, const WbPhys& P,
-                                              const WbGeo& g) {
+                                              const WbGeo& g, WbScalars* scal) {
   const double ir = wb_rcp(rho);
   const double m[3] = {mx, my, mz};
   const double vv[3] = {mx * ir, my * ir, mz * ir};
   const double B[3] = {bx, by, bz};
   const double me = wb_half(fma(bz, bz, fma(by, by, bx * bx)));
   const double p = P.gm1 * (e - kinetic(m, vv) - me);
-  double w = signal_rate_core(ir, vv, p, B, P, g);
-  if (!(rho > 0.0)) w = __longlong_as_double(0x7ff8000000000000LL);
-  return w;
+  if (!(rho > 0.0)) return __longlong_as_double(0x7ff8000000000000LL);
+  return screened_rate(ir, vv, p, B, P, g, scal);
 }
 
 // Step 10 (+ the zone field of Step 11, floors and the next step's signal
@@ -851,7 +916,7 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
     ++*bad;
     return __longlong_as_double(0x7ff8000000000000LL);
   }
-  return signal_rate_core(ir, vv, p, B, P, g);
+  return screened_rate(ir, vv, p, B, P, g, v.scal);
 }
 
 // The shell of ghost points within `depth` zones of a box's interior,

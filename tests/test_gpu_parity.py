@@ -221,3 +221,34 @@ def test_pinned_host_buffers_round_trip(wb):
     k.advance(2)
     for a, b in zip(h.read(), k.read()):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["late_max", "near_ties", "out_of_range"])
+def test_screened_cfl_rate_finds_the_exact_max(wb, oracle_mod, case):
+    """The CFL reduction screens zones with an FP32 estimate and evaluates the
+    FP64 rate only where a zone could hold the maximum; dt must equal the
+    oracle's (the max over every zone) whatever the data: the largest zone
+    last in memory, near-ties below the FP32 resolution, and values outside
+    the FP32 screen's range."""
+    n = (24, 20, 16)
+    W = np.zeros((5, n[2], n[1], n[0]))
+    W[0], W[1], W[2], W[3], W[4] = 1.0, 0.3, -0.2, 0.1, 0.6
+    bx = np.full((n[2], n[1], n[0] + 1), 0.4)
+    by = np.full((n[2], n[1] + 1, n[0]), -0.3)
+    bz = np.full((n[2] + 1, n[1], n[0]), 0.25)
+    rng = np.random.default_rng(11)
+    if case == "late_max":
+        W[1] += 0.01 * rng.uniform(-1, 1, W[1].shape)
+        W[1][-1, -1, -1] = 0.5              # fastest zone: the last one stored
+    elif case == "near_ties":
+        W[1] *= 1.0 + 1e-9 * rng.uniform(-1, 1, W[1].shape)   # below FP32 resolution
+    else:
+        W[0][n[2] // 2, 3, 5] = 1e-25       # density far below the screen's range
+        W[4][0, 0, 0] = 1e-30
+    L = (1.0, 1.0, 1.0)
+    g = wb.Grid(n, length=L)
+    g.load(W, bx, by, bz, primitive=True)
+    o = oracle_mod.Grid(n, L)
+    o.load_primitive(W, bx, by, bz)
+    dg, do = g.dt(), o.dt()
+    assert abs(dg - do) <= 1e-14 * do, (dg, do)
