@@ -80,6 +80,13 @@ bool valid_desc(const wb_desc* d, std::string* why) {
     if (!(d->eps[k] >= 0.0) || !(d->eps[k] < 0.5)) { *why = "eps_k must be in [0, 0.5)"; return false; }
   if (!(d->sweby_beta >= 1.0) || d->sweby_beta > 2.0) { *why = "sweby_beta must be in [1, 2]"; return false; }
   if (d->batch_patches < 0) { *why = "batch_patches must be >= 0"; return false; }
+  {
+    // padded zones of all patches (sizes beyond any device are refused before
+    // a byte count could overflow)
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) vol *= (double)(d->n[a] / d->patches[a] + 2 * WB_NG) * d->patches[a];
+    if (vol > 1.0e12) { *why = "grid too large (more than 1e12 padded zones)"; return false; }
+  }
   if (!(d->prot_rho >= 0.0) || !(d->prot_p >= 0.0)) {
     *why = "protection floors must be >= 0";
     return false;

@@ -44,3 +44,38 @@ def test_descriptor_validation_without_gpu():
         assert e.code == binding.WB_ERR_INVALID
     else:
         raise AssertionError("uneven patches accepted")
+
+
+def test_descriptor_edge_cases_rejected_without_gpu():
+    """Empty, ragged and out-of-range descriptors fail with WB_ERR_INVALID
+    before any device work (no GPU needed)."""
+    from paper_1701_07452_gb300 import binding
+    bad = [
+        dict(n=(0, 8, 8)),                        # empty axis
+        dict(n=(8, -4, 8)),
+        dict(n=(30, 32, 32), patches=(4, 1, 1)),  # patches must divide n
+        dict(n=(8, 8, 8), patches=(0, 1, 1)),
+        dict(n=(8, 8, 8), length=(1.0, 0.0, 1.0)),
+        dict(n=(8, 8, 8), gamma=1.0),
+        dict(n=(8, 8, 8), gamma=2.5),
+        dict(n=(8, 8, 8), cfl=0.0),
+        dict(n=(8, 8, 8), eps=(0.1, 0.0, 0.5, 0.0, 0.1, 0.0, 0.1)),
+        dict(n=(8, 8, 8), sweby=0.5),
+        dict(n=(8, 8, 8), bc=(0, 2, 0)),
+        dict(n=(8, 8, 8), batch_patches=-1),
+        dict(n=(8, 8, 8), prot_rho=-1.0),
+        dict(n=(20000, 20000, 20000)),            # beyond any device: refused, no overflow
+    ]
+    for kw in bad:
+        kw = dict(kw)
+        n = kw.pop("n")
+        d = binding.make_desc(n, **kw)
+        try:
+            binding.grid_bytes(d)
+        except binding.WombatError as e:
+            assert e.code == binding.WB_ERR_INVALID, kw
+        else:
+            raise AssertionError(f"accepted: n={n} {kw}")
+    # ragged (non-cubic, odd) sizes and one-zone axes are valid
+    for n in ((7, 5, 3), (1, 1, 9), (33, 1, 1)):
+        assert binding.grid_bytes(binding.make_desc(n)) > 0
