@@ -298,6 +298,7 @@ def run_mode(args):
         line = {"metric": "serving p50/p99 completion latency and cell-updates/s", "mode": "serve",
                 "value": summ["cell_updates_per_s"], "unit": "cell-updates/s", "higher_is_better": True,
                 "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "solves_per_s": summ["solves_per_s"],
+                "completed": summ["completed"], "failed": summ["failed"],
                 "wall_s": summ["wall_s"], "ticks": srv.ticks, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"{args.requests} requests, Poisson 50/s (seed 5), edge "
                                        f"log-uniform 32..192, steps U{{50..500}} x {args.steps_scale}, "

@@ -34,21 +34,25 @@
 
 namespace {
 
-using wbu::kBlock;
-
-// resident blocks per SM the sweep is compiled for (registers per thread
-// follow from it)
+// threads per block and resident blocks per SM the sweep is compiled for
+// (registers per thread follow from their product; the face records take
+// 2 x 39 doubles per thread of shared memory)
+#ifndef WB_SWEEP_BLOCK
+#define WB_SWEEP_BLOCK 64
+#endif
 #ifndef WB_SWEEP_MIN_BLOCKS
 #define WB_SWEEP_MIN_BLOCKS 4
 #endif
+constexpr int kBlock = WB_SWEEP_BLOCK;
+using SRec = wbu::RecT<kBlock>;
 
 using wbu::kEpsZeroLD;
 
 template <int D, int EZ, bool PROT>
-__global__ void __launch_bounds__(wbu::kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs A) {
+__global__ void __launch_bounds__(kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs A) {
   constexpr int U = (D == 0) ? 1 : 0;  // fastest transverse axis of the thread map
   constexpr int W = (D == 2) ? 1 : 2;
-  __shared__ double srec[2][wbu::R_WORDS][wbu::kBlock];
+  __shared__ double srec[2][wbu::R_WORDS][kBlock];
   const double dt = *A.dt;
   if (!(dt > 0.0)) return;
   const int nu_ = A.box.hi[U] - A.box.lo[U] + 1;
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(wbu::kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(Swee
   int fb = fa + A.seg_len - 1;
   if (fb > A.box.hi[D]) fb = A.box.hi[D];
   if (fa > fb) return;
-  const wbu::Rec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
+  const SRec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
   const int nhll = wbu::sweep_segment<D, true, EZ, PROT>(A.geo, A.q, A.bn, A.F, slot * A.slot_in, slot * A.slot_out,
                                         A.box.lo[U] + (int)(pen % nu_), A.box.lo[W] + (int)(pen / nu_),
                                         fa, fb, dt, A.phys, rec);

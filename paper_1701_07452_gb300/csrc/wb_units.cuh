@@ -100,10 +100,14 @@ enum {
   R_VN, R_VT1, R_VT2, R_BT1, R_BT2, R_KX, R_FAVG, R_WORDS = R_FAVG + 7
 };
 
-struct Rec {
+// One thread's face record in shared memory, word w at p[w * BS] (the block's
+// records interleaved, BS = threads per block).
+template <int BS>
+struct RecT {
   double* p;
-  __device__ __forceinline__ double& operator[](int w) const { return p[w * kBlock]; }
+  __device__ __forceinline__ double& operator[](int w) const { return p[w * BS]; }
 };
+using Rec = RecT<kBlock>;
 
 // Q_k(nu) - nu^2 for the g-tilde of App. A.  Waves in the compile-time mask
 // EZ have eps_k = 0, where Q is |nu|; the branch test runs on the integer pipe.
@@ -159,8 +163,9 @@ constexpr double kHllFace = -1.0;
 // with a_max, a_min = vn_ +- cf_ of the Roe state when it exists (roe), the
 // Einfeldt sign of the F_R term (the printed +b- F_R is not consistent), and
 // bounds +-max(|v| + c_f) if both speeds vanish.  Rare path.
+template <class Rc>
 __device__ __forceinline__ void hll_face(const Cell& L, const Cell& R, double bnL, double bnR, bool roe,
-                                      const WbPhys& P, const Rec& f) {
+                                      const WbPhys& P, const Rc& f) {
   const double cfL = zone_fast_speed(L, bnL, P), cfR = zone_fast_speed(R, bnR, P);
   double bp = fmax(R.vn + cfR, 0.0);
   double bm = fmin(L.vn - cfL, 0.0);
@@ -190,9 +195,9 @@ __device__ __forceinline__ void hll_face(const Cell& L, const Cell& R, double bn
 // flux (the record holds the Roe state), 2 when the Roe state has no real
 // sound speed (HLL without Roe speeds).  The protection test is compiled in
 // only when PROT is set.
-template <int EZ, bool PROT>
+template <int EZ, bool PROT, class Rc>
 __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double b, double dtdx,
-                                           const WbPhys& P, const Rec& f, double gt[7]) {
+                                           const WbPhys& P, const Rc& f, double gt[7]) {
   const double iD = wb_rcp(L.sr + R.sr);
   const double wL = L.sr * iD, wR = R.sr * iD;
   const double rho = L.sr * R.sr;
@@ -337,8 +342,8 @@ __device__ __forceinline__ double beta_k(double al, double nu, double gi, double
 }
 
 // u-bar = (F_L + F_R)/2 - (dx/(2 dt)) sum_k beta_k R_k  (App. A)
-template <int EZ>
-__device__ __forceinline__ void face_flux(const Rec& f, const double gi[7], const double gi1[7],
+template <int EZ, class Rc>
+__device__ __forceinline__ void face_flux(const Rc& f, const double gi[7], const double gi1[7],
                                           double dx_2dt, const WbPhys& P, double out[7]) {
   double be[7];
 #pragma unroll
@@ -382,11 +387,11 @@ __device__ __forceinline__ void face_flux(const Rec& f, const double gi[7], cons
 // Faces without a Roe state or below the protection floor take the HLL flux
 // and give g-tilde = 0 to the limiters of their neighbours.  Returns the
 // number of HLL faces among [fa, fb] that are interior faces of the box.
-template <int D, bool NC, int EZ = 0, bool PROT = true>
+template <int D, bool NC, int EZ = 0, bool PROT = true, class Rc = Rec>
 __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const* q,
                                              const double* bn, double* const* F, long long qo,
                                              long long wo, int pu, int pw, int fa, int fb,
-                                             double dt, const WbPhys& P, const Rec rec[2]) {
+                                             double dt, const WbPhys& P, const Rc rec[2]) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   constexpr int U = (D == 0) ? 1 : 0;
   constexpr int W = (D == 2) ? 1 : 2;
@@ -430,7 +435,7 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
       if (f >= fa + 1) {
         // flux of face f-1 (zones f-2, f-1): g_{i} = g_p (zone f-2), g_{i+1} = gz
         double out[7];
-        const Rec& fr = rec[cur ^ 1];
+        const Rc& fr = rec[cur ^ 1];
         if (wb_neg(fr[R_RHO])) {
 #pragma unroll
           for (int m = 0; m < 7; ++m) out[m] = fr[R_FAVG + m];

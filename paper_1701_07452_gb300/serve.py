@@ -7,6 +7,12 @@ one does not fit), loads their initial data, advances every resident run by
 up to ``tick_steps`` steps in one shared persistent launch, and reads back and
 releases the runs that finished.  Completion latency is measured from a run's
 arrival to the end of the tick in which its last step ran.
+
+Failures stay with their run: a run whose state becomes unphysical stops on
+the device (its own time step fails, the other boxes of the launch go on), is
+released and recorded as failed, and the loop keeps serving the others.  A
+run can be cancelled at a given time: dropped from the queue if it has not
+been admitted, released at the next tick boundary if it is resident.
 """
 from __future__ import annotations
 
@@ -38,6 +44,8 @@ class Record:
     admitted: float = float("nan")
     finished: float = float("nan")
     result: tuple = None
+    status: str = "pending"   # done, failed or cancelled once the loop is through
+    error: str = ""
 
 
 class Server:
@@ -49,8 +57,11 @@ class Server:
         self.keep_results = keep_results
         self.ticks = 0
 
-    def run(self, requests, clock=time.perf_counter, sleep=time.sleep):
+    def run(self, requests, clock=time.perf_counter, sleep=time.sleep, cancellations=()):
+        """Serve requests until every one is done, failed or cancelled.
+        cancellations: (time, rid) pairs, times after the start of the stream."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        cancels = sorted(cancellations)
         queue = []
         resident = {}   # slot -> (request, record)
         records = {}
@@ -61,6 +72,27 @@ class Server:
                 r = pending.popleft()
                 queue.append(r)
                 records[r.rid] = Record(r.rid, tuple(r.n), r.steps, r.arrival)
+            # cancellations that are due: queued runs leave the queue, resident
+            # runs give their slot back between launches
+            while cancels and cancels[0][0] <= now:
+                _, rid = cancels.pop(0)
+                rec = records.get(rid)
+                if rec is None:   # not arrived yet: drop it from the stream
+                    for r in list(pending):
+                        if r.rid == rid:
+                            pending.remove(r)
+                            records[rid] = rec = Record(r.rid, tuple(r.n), r.steps, r.arrival)
+                    if rec is None:
+                        continue
+                if rec.status != "pending":
+                    continue
+                queue = [r for r in queue if r.rid != rid]
+                for slot, r in list(resident.items()):
+                    if r.rid == rid:
+                        self.pool.release(slot)
+                        del resident[slot]
+                rec.status = "cancelled"
+                rec.finished = now
             # admission by HBM budget, FIFO with backfill
             still = []
             for r in queue:
@@ -86,26 +118,35 @@ class Server:
                 r = resident.pop(slot)
                 rec = records[r.rid]
                 rec.finished = done_at
-                if self.keep_results:
-                    rec.result = self.pool.read(slot)
                 c = self.pool.counters(slot)
                 if c["unphysical"]:
-                    raise binding.WombatError(binding.WB_ERR_UNPHYSICAL, f"run {r.rid} became unphysical")
+                    rec.status = "failed"
+                    rec.error = f"unphysical state after {c.get('steps', '?')} steps"
+                else:
+                    rec.status = "done"
+                    if self.keep_results:
+                        rec.result = self.pool.read(slot)
                 self.pool.release(slot)
         return [records[k] for k in sorted(records)]
 
 
 def summarize(records):
-    lat = np.array([r.finished - r.arrival for r in records])
-    wall = max(r.finished for r in records) - min(r.arrival for r in records)
-    cells = float(sum(np.prod(r.n) * r.steps for r in records))
+    """Latency and throughput over the runs that completed; failed and
+    cancelled runs are counted apart."""
+    done = [r for r in records if r.status == "done"]
+    lat = np.array([r.finished - r.arrival for r in done])
+    wall = max(r.finished for r in done) - min(r.arrival for r in done)
+    cells = float(sum(np.prod(r.n) * r.steps for r in done))
     return {
         "requests": len(records),
+        "completed": len(done),
+        "failed": sum(r.status == "failed" for r in records),
+        "cancelled": sum(r.status == "cancelled" for r in records),
         "p50_s": float(np.percentile(lat, 50)),
         "p99_s": float(np.percentile(lat, 99)),
         "mean_s": float(lat.mean()),
         "wall_s": float(wall),
         "cell_updates": cells,
         "cell_updates_per_s": cells / wall,
-        "solves_per_s": len(records) / wall,
+        "solves_per_s": len(done) / wall,
     }

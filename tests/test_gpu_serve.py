@@ -62,3 +62,29 @@ def test_pool_admission_accounting(mods):
     assert d is not None
     with pytest.raises(binding.WombatError):
         pool.admit((40, 40, 40))                      # beyond max_n
+
+
+def test_an_unphysical_run_fails_alone(mods):
+    """Fault injection on the host: one request's loaded state carries a NaN
+    density.  Its own time step fails on the device, it is released and
+    recorded as failed, and the runs sharing its launches still equal their
+    results served alone."""
+    binding, serve = mods
+    reqs = requests()
+    bad = reqs[1]
+    W = bad.state["W"].copy()
+    W[0, 2, 3, 4] = float("nan")
+    reqs[1] = serve.Request(bad.rid, bad.arrival, bad.n, bad.steps, dict(bad.state, W=W), bad.length)
+    srv = serve.Server(state_bytes=1 << 26, work_bytes=64 << 20, max_boxes=8, max_n=32, tick_steps=2,
+                       keep_results=True)
+    recs = srv.run(reqs)
+    assert recs[1].status == "failed" and recs[1].result is None
+    for r, rec in zip(reqs, recs):
+        if r.rid == 1:
+            continue
+        assert rec.status == "done"
+        alone = serve.Server(state_bytes=1 << 25, work_bytes=64 << 20, max_boxes=2, max_n=32,
+                             tick_steps=3, keep_results=True)
+        (arec,) = alone.run([serve.Request(r.rid, 0.0, r.n, r.steps, r.state, r.length)])
+        for a, b in zip(arec.result, rec.result):
+            assert np.array_equal(a, b), r.rid

@@ -15,6 +15,8 @@ class FakePool:
         self.loaded = set()
         self.max_resident = 0
         self.advances = 0
+        self.bad = set()       # slots whose run fails on the device
+        self.released = []
 
     @staticmethod
     def size(n):
@@ -32,8 +34,10 @@ class FakePool:
         self.max_resident = max(self.max_resident, len(self.used))
         return slot
 
-    def load(self, slot, *a, **k):
+    def load(self, slot, W, *a, **k):
         self.loaded.add(slot)
+        if isinstance(W, str) and W == "unphysical":
+            self.bad.add(slot)
 
     def set_steps(self, slot, n):
         self.left[slot] = n
@@ -41,7 +45,8 @@ class FakePool:
     def advance(self, k, use_graph=True):
         self.advances += 1
         for s in self.left:
-            self.left[s] = max(0, self.left[s] - k)
+            # a failed box stops: its dt fails and its steps left drop to 0
+            self.left[s] = 0 if s in self.bad else max(0, self.left[s] - k)
 
     def steps_left(self):
         out = [0] * 64
@@ -53,11 +58,13 @@ class FakePool:
         return ("result", slot)
 
     def counters(self, slot):
-        return {"unphysical": 0}
+        return {"unphysical": 1 if slot in self.bad else 0, "steps": 0}
 
     def release(self, slot):
         del self.used[slot]
         del self.left[slot]
+        self.bad.discard(slot)
+        self.released.append(slot)
 
 
 class FakeClock:
@@ -118,3 +125,37 @@ def test_ticks_cover_the_longest_run():
     recs = srv.run(reqs, clock=clk, sleep=clk.sleep)
     assert srv.ticks == 4            # ceil(7 / 2)
     assert recs[1].finished < recs[0].finished
+
+
+def test_a_failed_run_is_isolated():
+    """A run whose state becomes unphysical is recorded as failed and released;
+    every other run completes and the loop does not stop."""
+    empty = {"W": None, "bx": None, "by": None, "bz": None}
+    bad = {"W": "unphysical", "bx": None, "by": None, "bz": None}
+    reqs = [serve.Request(i, 0.001 * i, (8, 8, 8), 6, bad if i == 2 else empty) for i in range(5)]
+    srv = make_server(budget=10 ** 6, tick=2)
+    clk = FakeClock()
+    recs = srv.run(reqs, clock=clk, sleep=clk.sleep)
+    assert [r.status for r in recs] == ["done", "done", "failed", "done", "done"]
+    assert recs[2].result is None and "unphysical" in recs[2].error
+    assert all(r.result is not None for r in recs if r.status == "done")
+    assert not srv.pool.used                       # every slot given back
+    summ = serve.summarize(recs)
+    assert summ["completed"] == 4 and summ["failed"] == 1
+
+
+def test_cancellation_of_queued_and_resident_runs():
+    """A resident run cancelled mid-run gives its slot back at the next tick
+    and the run that waited for memory is admitted; a run cancelled before it
+    arrives never enters."""
+    empty = {"W": None, "bx": None, "by": None, "bz": None}
+    reqs = [serve.Request(0, 0.0, (16, 16, 16), 100, empty),     # fills the budget
+            serve.Request(1, 0.0005, (16, 16, 16), 4, empty),    # waits for memory
+            serve.Request(2, 0.5, (8, 8, 8), 4, empty)]          # cancelled before arrival
+    srv = make_server(budget=16 ** 3, tick=2)
+    clk = FakeClock()
+    recs = srv.run(reqs, clock=clk, sleep=clk.sleep, cancellations=[(0.01, 0), (0.02, 2)])
+    assert recs[0].status == "cancelled" and recs[0].result is None
+    assert recs[1].status == "done" and recs[1].admitted >= recs[0].finished
+    assert recs[2].status == "cancelled" and recs[2].admitted != recs[2].admitted   # never admitted
+    assert srv.ticks < 50                          # the long run did not run to its end
