@@ -747,9 +747,17 @@ int rebuild(wb_batch* b) {
   size_t cur = 0;
   double* work = b->work_base;
   b->nbox = 0;
-  for (int i = 0; i < b->cap; ++i) {
-    if (!b->alive[i]) continue;
-    b->nbox = i + 1;
+  // boxes in decreasing size: within a stage the work list then starts with
+  // the longest items (the big boxes' pencil segments) and ends with the
+  // shortest, so the blocks that finish last leave little idle time
+  std::vector<int> order;
+  for (int i = 0; i < b->cap; ++i)
+    if (b->alive[i]) {
+      order.push_back(i);
+      b->nbox = i + 1;
+    }
+  std::stable_sort(order.begin(), order.end(), [b](int x, int y) { return b->geo[x].V > b->geo[y].V; });
+  for (int i : order) {
     const WbGeo& g = b->geo[i];
     const size_t w = work_doubles(g);
     if (cur > 0 && cur + w > b->work_cap) {

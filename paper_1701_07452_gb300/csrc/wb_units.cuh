@@ -759,7 +759,7 @@ __device__ __forceinline__ void eref_half(const WbView& v, long long qo, long lo
 
 // sqrt for the CFL rate; inputs below the normal range (or not > 0) give 0
 __device__ __forceinline__ double wb_sqrt_fast(double x) {
-  return wb_normal_pos(x) ? x * wb_rsqrt(x) : 0.0;
+  return wb_normal_pos(x) ? __dmul_rn(x, wb_rsqrt(x)) : 0.0;
 }
 
 // CFL signal rate sum_d (|v_d| + c_f,d)/dx_d of one zone (Sec. 3 fast speed)
@@ -767,23 +767,27 @@ __device__ __forceinline__ double wb_sqrt_fast(double x) {
 // speed along d: c_f^2 = (S + sqrt(disc_d))/2 with S = a^2 + |B|^2/rho and
 // disc_d = (a^2 - c_n^2)^2 + c_t^2 (c_t^2 + 2 (a^2 + c_n^2)) (the sum of
 // non-negative terms), c_n^2 = B_d^2/rho, c_t^2 = |B|^2/rho - c_n^2.
+//
+// Written with explicit rounding: the final update (for the next step) and
+// the rate of a freshly loaded state are inlined in different kernels and
+// must give the same bits, or a resumed run would take a different dt.
 __device__ __forceinline__ double signal_rate_core(double ir, const double vv[3], double p,
                                                    const double B[3], const WbPhys& P,
                                                    const WbGeo& g) {
-  const double a2 = P.gamma * p * ir;
+  const double a2 = __dmul_rn(__dmul_rn(P.gamma, p), ir);
   double cn2[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) cn2[d] = (B[d] * B[d]) * ir;
-  const double bbi = (cn2[0] + cn2[1]) + cn2[2];
-  const double S = a2 + bbi;
+  for (int d = 0; d < 3; ++d) cn2[d] = __dmul_rn(__dmul_rn(B[d], B[d]), ir);
+  const double bbi = __dadd_rn(__dadd_rn(cn2[0], cn2[1]), cn2[2]);
+  const double S = __dadd_rn(a2, bbi);
   double w = 0.0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double ct2 = bbi - cn2[d];
-    const double dd = a2 - cn2[d];
-    const double disc = fma(dd, dd, ct2 * fma(2.0, a2 + cn2[d], ct2));
-    const double cf = wb_sqrt_fast(wb_half(S + wb_sqrt_fast(disc)));
-    w = fma(fabs(vv[d]) + cf, g.idx[d], w);
+    const double ct2 = __dsub_rn(bbi, cn2[d]);
+    const double dd = __dsub_rn(a2, cn2[d]);
+    const double disc = __fma_rn(dd, dd, __dmul_rn(ct2, __fma_rn(2.0, __dadd_rn(a2, cn2[d]), ct2)));
+    const double cf = wb_sqrt_fast(wb_half(__dadd_rn(S, wb_sqrt_fast(disc))));
+    w = __fma_rn(__dadd_rn(fabs(vv[d]), cf), g.idx[d], w);
   }
   return w;
 }

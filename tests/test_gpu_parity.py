@@ -252,3 +252,24 @@ def test_screened_cfl_rate_finds_the_exact_max(wb, oracle_mod, case):
     o.load_primitive(W, bx, by, bz)
     dg, do = g.dt(), o.dt()
     assert abs(dg - do) <= 1e-14 * do, (dg, do)
+
+
+def test_checkpoint_resume_bit_exact(wb):
+    """wb_read_state / wb_load_state are the checkpoint: 10 steps equal 5
+    steps, a read to host, a fresh grid loaded from it, and 5 more steps,
+    bit for bit (the loaded state's dt is the one the running grid takes)."""
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box
+    n = (24, 20, 16)
+    st = turbulence_box(n, seed=8)
+    a = wb.Grid(n, length=st["length"])
+    a.load_state(st)
+    a.advance(10)
+    b = wb.Grid(n, length=st["length"])
+    b.load_state(st)
+    b.advance(5)
+    U, bx, by, bz, _ = b.read()
+    c = wb.Grid(n, length=st["length"])
+    c.load(U, bx, by, bz)
+    c.advance(5)
+    for x, y in zip(a.read(), c.read()):
+        assert np.array_equal(x, y)
