@@ -245,6 +245,13 @@ def run_mode(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t_batch = e0.elapsed_time(e1) * 1e-3
+        # per-stage breakdown of the persistent kernel (stage timer, no graph),
+        # one more step of every box, outside the timed region
+        bt.set_steps(-1, 1)
+        bt.stage_timer(True)
+        bt.advance(1, use_graph=False)
+        stage_ms = {k: round(v, 3) for k, v in bt.stage_times().items()}
+        bt.stage_timer(False)
         # the plain path: one box at a time through the single-grid API
         t_plain = 0.0
         worst = 0.0
@@ -277,7 +284,8 @@ def run_mode(args):
                 "config": {"workload": f"{args.nbox} periodic boxes, edges from {{16..128}} (seed 4), "
                                        f"random data seed 4000+b, {steps} steps each (solve = one box x "
                                        f"{steps} steps)", "autotuned": cfg},
-                "batch_vs_grid_max_rel_err": worst}
+                "batch_vs_grid_max_rel_err": worst,
+                "stage_ms_one_step": stage_ms}
         print(json.dumps(line), flush=True)
         return 0
     if args.mode == "serve":

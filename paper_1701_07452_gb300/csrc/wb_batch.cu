@@ -237,42 +237,6 @@ __device__ __forceinline__ int sweep_item(const BoxInfo& bi, bool corr, const Wb
                                fa, fb, dt, P, rec);
 }
 
-// One shell point of a periodic-image stage: copy every array the stage fills
-// (the arrays the grid path's enqueue_pass_wrap lists at the same point).
-__device__ __forceinline__ void wrap_item(const WbView& v, int s, long long item) {
-  long long dst, src;
-  wbu::wrap_shell_point(v.geo, s == BS_W_QH ? 2 : 1, item, &dst, &src);
-  switch (s) {
-    case BS_W_FP:
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c != F_BX + d) v.Fp[d][c][dst] = v.Fp[d][c][src];
-        v.Eref[d][dst] = v.Eref[d][src];
-      }
-      break;
-    case BS_W_FC:
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c != F_BX + d) v.Fc[d][c][dst] = v.Fc[d][c][src];
-      break;
-    case BS_W_QH:
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) v.qh[d][c][dst] = v.qh[d][c][src];
-      break;
-    default: {
-      double* const* a = s == BS_W_EE ? v.Eedge : (s == BS_W_BH ? v.bh : (s == BS_W_ERH ? v.Erefh : v.Eedgeh));
-#pragma unroll
-      for (int d = 0; d < 3; ++d) a[d][dst] = a[d][src];
-    }
-  }
-}
-
 template <int EZ, bool PROT>
 __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, int box,
                                           const BoxInfo& bi, long long item, double dt,
@@ -289,14 +253,8 @@ __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, in
     else *hll += sweep_item<2, EZ, PROT>(bi, corr, b, item, B.seg_len, dt, B.phys, rec);
     return;
   }
-  if (s == BS_HALO) {
-    wbu::halo_self(v, 0, bi.bc, item);
-    return;
-  }
-  if (stage_is_wrap(s)) {
-    wrap_item(v, s, item);
-    return;
-  }
+  // the remaining stages (transverse states, half-step EMF, update); the
+  // cheap ones go through unit_pair
   const WbBox b = stage_box(s, d, n, wrap);
   const int nx = b.hi[0] - b.lo[0] + 1, ny = b.hi[1] - b.lo[1] + 1;
   const int i = b.lo[0] + (int)(item % nx);
@@ -304,23 +262,6 @@ __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, in
   const int j = b.lo[1] + (int)(r % ny);
   const int k = b.lo[2] + (int)(r / ny);
   switch (s) {
-    case BS_EREF: wbu::eref(v, 0, 0, i, j, k); break;
-    case BS_EDGE_P:
-    case BS_EDGE_C: {
-      const bool corr = s == BS_EDGE_C;
-      if (d == 0) wbu::edge<0>(v, 0, corr, i, j, k);
-      else if (d == 1) wbu::edge<1>(v, 0, corr, i, j, k);
-      else wbu::edge<2>(v, 0, corr, i, j, k);
-      break;
-    }
-    case BS_CT_H:
-    case BS_CT_F: {
-      const bool fin = s == BS_CT_F;
-      if (d == 0) wbu::ct<0>(v, 0, 0, fin, dt, i, j, k);
-      else if (d == 1) wbu::ct<1>(v, 0, 0, fin, dt, i, j, k);
-      else wbu::ct<2>(v, 0, 0, fin, dt, i, j, k);
-      break;
-    }
     case BS_TRANS: {
       const int mask = trans_mask(n, i, j, k);
       if (mask) wbu::transverse_set(v, 0, 0, dt, mask, i, j, k);
