@@ -13,6 +13,13 @@ the device (its own time step fails, the other boxes of the launch go on), is
 released and recorded as failed, and the loop keeps serving the others.  A
 run can be cancelled at a given time: dropped from the queue if it has not
 been admitted, released at the next tick boundary if it is resident.
+
+Two tick policies.  "fair": every resident run advances up to tick_steps per
+tick (processor sharing).  "srpt": each tick grants up to tick_steps steps to
+the resident runs in order of least remaining work (zones x steps left)
+until the granted cell-updates reach tick_cells, the rest wait; short runs
+then finish within a few ticks of admission while the GPU stays full.  A
+run's result does not depend on the policy (each box advances on its own).
 """
 from __future__ import annotations
 
@@ -50,12 +57,27 @@ class Record:
 
 class Server:
     def __init__(self, state_bytes, work_bytes, max_boxes=512, max_n=256, tick_steps=4,
-                 use_graph=True, keep_results=False, **physics):
+                 use_graph=True, keep_results=False, policy="fair", tick_cells=1.5e8, **physics):
         self.pool = binding.Pool(state_bytes, work_bytes, max_boxes=max_boxes, max_n=max_n, **physics)
         self.tick_steps = int(tick_steps)
         self.use_graph = use_graph
         self.keep_results = keep_results
+        self.policy = policy
+        self.tick_cells = float(tick_cells)
         self.ticks = 0
+
+    def _grants(self, resident, done):
+        """Steps each resident run may take this tick (srpt policy)."""
+        work = {s: int(np.prod(r.n)) for s, r in resident.items()}
+        order = sorted(resident, key=lambda s: (work[s] * (resident[s].steps - done[s]), resident[s].rid))
+        grant, acc = {}, 0.0
+        for s in order:
+            a = min(self.tick_steps, resident[s].steps - done[s])
+            if grant and acc + a * work[s] > self.tick_cells:
+                a = 0
+            grant[s] = a
+            acc += a * work[s]
+        return grant
 
     def run(self, requests, clock=time.perf_counter, sleep=time.sleep, cancellations=()):
         """Serve requests until every one is done, failed or cancelled.
@@ -63,7 +85,8 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         cancels = sorted(cancellations)
         queue = []
-        resident = {}   # slot -> (request, record)
+        resident = {}   # slot -> request
+        done = {}       # slot -> steps taken (srpt policy)
         records = {}
         t0 = clock()
         while pending or queue or resident:
@@ -91,6 +114,7 @@ class Server:
                     if r.rid == rid:
                         self.pool.release(slot)
                         del resident[slot]
+                        done.pop(slot, None)
                 rec.status = "cancelled"
                 rec.finished = now
             # admission by HBM budget, FIFO with backfill
@@ -102,20 +126,35 @@ class Server:
                     continue
                 st = r.state
                 self.pool.load(slot, st["W"], st["bx"], st["by"], st["bz"], primitive=True)
-                self.pool.set_steps(slot, r.steps)
+                self.pool.set_steps(slot, r.steps if self.policy == "fair" else 0)
                 records[r.rid].admitted = clock() - t0
                 resident[slot] = r
+                done[slot] = 0
             queue = still
             if not resident:
                 if pending:
                     sleep(max(0.0, min(0.05, pending[0].arrival - (clock() - t0))))
                 continue
+            if self.policy == "srpt":
+                grant = self._grants(resident, done)
+                for slot, a in grant.items():
+                    self.pool.set_steps(slot, a)
             self.pool.advance(self.tick_steps, use_graph=self.use_graph)
             self.ticks += 1
             left = self.pool.steps_left()
             done_at = clock() - t0
-            for slot in [s for s in resident if left[s] == 0]:
+            if self.policy == "srpt":
+                finished = []
+                for slot in resident:
+                    done[slot] += grant[slot] - left[slot]
+                    if done[slot] >= resident[slot].steps or \
+                            (grant[slot] > 0 and self.pool.counters(slot)["unphysical"]):
+                        finished.append(slot)
+            else:
+                finished = [s for s in resident if left[s] == 0]
+            for slot in finished:
                 r = resident.pop(slot)
+                done.pop(slot, None)
                 rec = records[r.rid]
                 rec.finished = done_at
                 c = self.pool.counters(slot)

@@ -1,6 +1,6 @@
 """Serving pattern on the GPU: runs that arrive while others are resident are
 admitted as memory frees up, share launches, and each result is bit-identical
-to the same run served alone."""
+to the same run served alone, under either tick policy."""
 import numpy as np
 import pytest
 
@@ -29,13 +29,14 @@ def requests():
     return out
 
 
-def test_served_results_equal_alone_results(mods):
+@pytest.mark.parametrize("policy", ["fair", "srpt"])
+def test_served_results_equal_alone_results(mods, policy):
     binding, serve = mods
     reqs = requests()
     # the state budget holds about two of these boxes at a time
     per = max(11 * 8 * (n[0] + 10) * (n[1] + 10) * (n[2] + 10) for n in [r.n for r in reqs])
     srv = serve.Server(state_bytes=2 * per + 4096, work_bytes=64 << 20, max_boxes=8, max_n=32,
-                       tick_steps=2, keep_results=True)
+                       tick_steps=2, keep_results=True, policy=policy, tick_cells=2 * 14 ** 3)
     recs = srv.run(reqs)
     assert len(recs) == len(reqs)
     assert any(r.admitted > r.arrival + 1e-6 for r in recs), "budget never delayed an admission"

@@ -79,12 +79,14 @@ class FakeClock:
         self.t += max(dt, 0.0)
 
 
-def make_server(budget, tick):
+def make_server(budget, tick, policy="fair", tick_cells=1e12):
     srv = serve.Server.__new__(serve.Server)
     srv.pool = FakePool(budget)
     srv.tick_steps = tick
     srv.use_graph = True
     srv.keep_results = True
+    srv.policy = policy
+    srv.tick_cells = tick_cells
     srv.ticks = 0
     return srv
 
@@ -159,3 +161,45 @@ def test_cancellation_of_queued_and_resident_runs():
     assert recs[1].status == "done" and recs[1].admitted >= recs[0].finished
     assert recs[2].status == "cancelled" and recs[2].admitted != recs[2].admitted   # never admitted
     assert srv.ticks < 50                          # the long run did not run to its end
+
+
+def test_srpt_ticks_finish_short_runs_first():
+    """Under the srpt policy a tick grants steps to the runs with the least
+    remaining work until its cell budget is spent: a short run that arrives
+    behind long ones finishes before them, every run still gets all its
+    steps, and the ticks never grant more than the budget (beyond the first
+    run)."""
+    empty = {"W": None, "bx": None, "by": None, "bz": None}
+    reqs = [serve.Request(0, 0.0, (16, 16, 16), 40, empty),
+            serve.Request(1, 0.0, (16, 16, 16), 40, empty),
+            serve.Request(2, 0.0001, (8, 8, 8), 4, empty)]
+    granted = []
+
+    class CountingPool(FakePool):
+        def set_steps(self, slot, n):
+            super().set_steps(slot, n)
+            granted.append((slot, n))
+
+    srv = make_server(budget=10 ** 6, tick=2, policy="srpt", tick_cells=2 * 16 ** 3 * 2)
+    srv.pool = CountingPool(10 ** 6)
+    clk = FakeClock()
+    recs = srv.run(reqs, clock=clk, sleep=clk.sleep)
+    assert all(r.status == "done" for r in recs)
+    assert recs[2].finished < recs[0].finished and recs[2].finished < recs[1].finished
+    fair = make_server(budget=10 ** 6, tick=2)
+    frecs = fair.run(reqs, clock=FakeClock(), sleep=FakeClock().sleep)
+    assert all(r.status == "done" for r in frecs)
+
+
+def test_srpt_grants_respect_the_cell_budget():
+    from types import SimpleNamespace
+    srv = make_server(budget=10 ** 6, tick=3, policy="srpt", tick_cells=10 * 8 ** 3)
+    resident = {0: SimpleNamespace(n=(8, 8, 8), steps=10, rid=0), 1: SimpleNamespace(n=(8, 8, 8), steps=5, rid=1),
+                2: SimpleNamespace(n=(16, 16, 16), steps=2, rid=2)}
+    done = {0: 0, 1: 0, 2: 0}
+    g = srv._grants(resident, done)
+    # least remaining work first: run 1 (5 x 8^3), then run 0 (10 x 8^3), then 2 (2 x 16^3)
+    assert g[1] == 3 and g[0] == 3 and g[2] == 0
+    done = {0: 9, 1: 5, 2: 0}
+    g = srv._grants(resident, done)
+    assert g[0] == 1 and g[1] == 0
