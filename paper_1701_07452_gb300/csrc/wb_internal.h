@@ -21,6 +21,7 @@ struct SweepArgs {
   WbScalars* scal;
   int nseg;                // segments per pencil (0: chosen at launch)
   int seg_len;             // faces per segment (set at launch)
+  int balanced;            // 1: equal runs of (32-pencil group, face) units per warp
 };
 
 // Pointers of one pipeline pass over a batch of patches: the view holds the

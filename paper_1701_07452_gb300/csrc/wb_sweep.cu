@@ -58,20 +58,53 @@ __global__ void __launch_bounds__(kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs
   const int nu_ = A.box.hi[U] - A.box.lo[U] + 1;
   const int nw_ = A.box.hi[W] - A.box.lo[W] + 1;
   const long long npen = (long long)nu_ * nw_;
-  const long long item = blockIdx.x * (long long)kBlock + threadIdx.x;
-  if (item >= npen * A.nseg) return;
-  const int seg = (int)(item / npen);
-  const long long pen = item - seg * npen;
+  const int len = A.box.hi[D] - A.box.lo[D] + 1;
   const long long slot = blockIdx.y;
-  // faces of this segment: [fa, fb] within [box.lo[D], box.hi[D]]
-  const int fa = A.box.lo[D] + seg * A.seg_len;
-  int fb = fa + A.seg_len - 1;
-  if (fb > A.box.hi[D]) fb = A.box.hi[D];
-  if (fa > fb) return;
   const SRec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
-  const int nhll = wbu::sweep_segment<D, true, EZ, PROT>(A.geo, A.q, A.bn, A.F, slot * A.slot_in, slot * A.slot_out,
-                                        A.box.lo[U] + (int)(pen % nu_), A.box.lo[W] + (int)(pen / nu_),
-                                        fa, fb, dt, A.phys, rec);
+  // Balanced: the work is the list of units (group of 32 adjacent pencils,
+  // face), group-major; warp w takes units [w U / C, (w+1) U / C) of the C
+  // warps of the launch and marches one segment per group it touches, its 32
+  // lanes on the 32 pencils of the group (adjacent pencils: coalesced rows).
+  // Otherwise one segment per thread: item = segment x pencils + pencil.
+  const long long ngroups = (npen + 31) / 32;
+  const long long units = ngroups * len;
+  const long long C = (long long)gridDim.x * (kBlock / 32);
+  const long long wid = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  long long u = wid * units / C;
+  const long long u1 = (wid + 1) * units / C;
+  const long long item = blockIdx.x * (long long)kBlock + threadIdx.x;
+  bool once = !A.balanced;
+  int nhll = 0;
+  for (;;) {
+    long long pen;
+    int fa, fb;
+    bool ok;
+    if (A.balanced) {
+      if (u >= u1) break;
+      const long long grp = u / len;
+      const int off = (int)(u - grp * len);
+      const int take = (int)((len - off) < (u1 - u) ? (len - off) : (u1 - u));
+      pen = grp * 32 + lane;
+      fa = A.box.lo[D] + off;
+      fb = fa + take - 1;
+      ok = pen < npen;
+      u += take;
+    } else {
+      if (!once) break;
+      once = false;
+      const int seg = (int)(item / npen);
+      pen = item - seg * npen;
+      fa = A.box.lo[D] + seg * A.seg_len;
+      fb = fa + A.seg_len - 1;
+      if (fb > A.box.hi[D]) fb = A.box.hi[D];
+      ok = item < npen * A.nseg && fa <= fb;
+    }
+    if (ok)
+      nhll += wbu::sweep_segment<D, true, EZ, PROT>(A.geo, A.q, A.bn, A.F, slot * A.slot_in, slot * A.slot_out,
+                                                    A.box.lo[U] + (int)(pen % nu_), A.box.lo[W] + (int)(pen / nu_),
+                                                    fa, fb, dt, A.phys, rec);
+  }
   if (nhll) atomicAdd((unsigned long long*)&A.scal->hll_faces, (unsigned long long)nhll);
 }
 
@@ -124,6 +157,16 @@ static void launch_sweep(SweepArgs a, int nslots, cudaStream_t s) {
   long long npen = (long long)(a.box.hi[U] - a.box.lo[U] + 1) * (a.box.hi[W] - a.box.lo[W] + 1);
   int len = a.box.hi[D] - a.box.lo[D] + 1;
   int resident = blocks_per_sm<D, EZ, PROT>() * sm_count() * kBlock;
+  // big launches: equal runs of units per resident warp, so every warp
+  // finishes with the others (no partial last wave); one grid row per slot
+  const long long units = (npen + 31) / 32 * (long long)len;
+  const long long warps = resident / 32 / nslots;
+  if (a.nseg == 0 && warps >= 1 && units >= 64 * warps) {
+    a.balanced = 1;
+    k_sweep<D, EZ, PROT><<<dim3((unsigned)(warps * 32 / kBlock), (unsigned)nslots), kBlock, 0, s>>>(a);
+    return;
+  }
+  a.balanced = 0;
   int nseg = a.nseg > 0 ? a.nseg : choose_segments(npen * nslots, len, resident);
   a.nseg = nseg;
   a.seg_len = (len + nseg - 1) / nseg;
