@@ -21,7 +21,8 @@ struct SweepArgs {
   WbScalars* scal;
   int nseg;                // segments per pencil (0: chosen at launch)
   int seg_len;             // faces per segment (set at launch)
-  int balanced;            // 1: equal runs of (32-pencil group, face) units per warp
+  int balanced;            // 1: equal runs of (slot, 32-pencil group, face) units per warp
+  int nslots;              // slots of the pass (balanced launches take them all in one row)
 };
 
 // Pointers of one pipeline pass over a batch of patches: the view holds the

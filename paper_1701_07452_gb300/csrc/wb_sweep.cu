@@ -59,15 +59,17 @@ __global__ void __launch_bounds__(kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs
   const int nw_ = A.box.hi[W] - A.box.lo[W] + 1;
   const long long npen = (long long)nu_ * nw_;
   const int len = A.box.hi[D] - A.box.lo[D] + 1;
-  const long long slot = blockIdx.y;
+  long long slot = blockIdx.y;
   const SRec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
-  // Balanced: the work is the list of units (group of 32 adjacent pencils,
-  // face), group-major; warp w takes units [w U / C, (w+1) U / C) of the C
-  // warps of the launch and marches one segment per group it touches, its 32
-  // lanes on the 32 pencils of the group (adjacent pencils: coalesced rows).
-  // Otherwise one segment per thread: item = segment x pencils + pencil.
+  // Balanced: the work is the list of units (slot, group of 32 adjacent
+  // pencils, face), slot- then group-major, over every slot of the pass; warp
+  // w takes units [w U / C, (w+1) U / C) of the C warps of the launch (one
+  // grid row) and marches one segment per group it touches, its 32 lanes on
+  // the 32 pencils of the group (adjacent pencils: coalesced rows).
+  // Otherwise one segment per thread: item = segment x pencils + pencil, one
+  // grid row per slot.
   const long long ngroups = (npen + 31) / 32;
-  const long long units = ngroups * len;
+  const long long units = ngroups * len * (A.balanced ? A.nslots : 1);
   const long long C = (long long)gridDim.x * (kBlock / 32);
   const long long wid = ((long long)blockIdx.x * kBlock + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
@@ -82,8 +84,10 @@ __global__ void __launch_bounds__(kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs
     bool ok;
     if (A.balanced) {
       if (u >= u1) break;
-      const long long grp = u / len;
-      const int off = (int)(u - grp * len);
+      const long long sg = u / len;          // slot x ngroups + group
+      slot = sg / ngroups;
+      const long long grp = sg - slot * ngroups;
+      const int off = (int)(u - sg * len);
       const int take = (int)((len - off) < (u1 - u) ? (len - off) : (u1 - u));
       pen = grp * 32 + lane;
       fa = A.box.lo[D] + off;
@@ -157,13 +161,14 @@ static void launch_sweep(SweepArgs a, int nslots, cudaStream_t s) {
   long long npen = (long long)(a.box.hi[U] - a.box.lo[U] + 1) * (a.box.hi[W] - a.box.lo[W] + 1);
   int len = a.box.hi[D] - a.box.lo[D] + 1;
   int resident = blocks_per_sm<D, EZ, PROT>() * sm_count() * kBlock;
-  // big launches: equal runs of units per resident warp, so every warp
-  // finishes with the others (no partial last wave); one grid row per slot
-  const long long units = (npen + 31) / 32 * (long long)len;
-  const long long warps = resident / 32 / nslots;
-  if (a.nseg == 0 && warps >= 1 && units >= 64 * warps) {
+  // big launches: equal runs of units per resident warp over every slot of
+  // the pass, so every warp finishes with the others (no partial last wave)
+  const long long units = (npen + 31) / 32 * (long long)len * nslots;
+  const long long warps = resident / 32;
+  if (a.nseg == 0 && units >= 64 * warps) {
     a.balanced = 1;
-    k_sweep<D, EZ, PROT><<<dim3((unsigned)(warps * 32 / kBlock), (unsigned)nslots), kBlock, 0, s>>>(a);
+    a.nslots = nslots;
+    k_sweep<D, EZ, PROT><<<dim3((unsigned)(resident / kBlock), 1), kBlock, 0, s>>>(a);
     return;
   }
   a.balanced = 0;
