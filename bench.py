@@ -50,7 +50,7 @@ FLOPS_PER_FACE = 513.0
 # DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the mean
 # of the six sweeps of a step from one ncu capture of this kernel
 # (profiles/k_sweep_256cube_dram.md); the algorithmic figure is 128 B per face.
-SWEEP_DRAM_BYTES_256 = 3.197e9
+SWEEP_DRAM_BYTES_256 = 3.681e9
 SWEEP_BYTES_PER_FACE = 128.0
 # FP64 issue rate of one GB300 SM: 2 DFMA per clock (measured with the DFMA
 # probe: 1196 GFLOP/s at 1995 MHz on 152 SMs), i.e. 4 flops per clock per SM.
