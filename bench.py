@@ -253,8 +253,22 @@ def run_mode(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t_batch = e0.elapsed_time(e1) * 1e-3
-        # per-stage breakdown of the persistent kernel (stage timer, no graph),
-        # one more step of every box, outside the timed region
+        # the other form (persistent kernel / one launch per stage) with the
+        # same segment length and block count, for comparison
+        other = "staged" if cfg["form"] == "persistent" else "persistent"
+        bt.set_form(other)
+        bt.set_steps(-1, 1)
+        bt.advance(1, use_graph=True)
+        bt.set_steps(-1, steps)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bt.advance(steps, use_graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_other = e0.elapsed_time(e1) * 1e-3
+        bt.set_form(cfg["form"])
+        # per-stage breakdown of the tuned form (stage timer, no graph), one
+        # more step of every box, outside the timed region
         bt.set_steps(-1, 1)
         bt.stage_timer(True)
         bt.advance(1, use_graph=False)
@@ -292,6 +306,7 @@ def run_mode(args):
                 "config": {"workload": f"{args.nbox} periodic boxes, edges from {{16..128}} (seed 4), "
                                        f"random data seed 4000+b, {steps} steps each (solve = one box x "
                                        f"{steps} steps)", "autotuned": cfg},
+                "other_form": {"form": other, "solves_per_s": args.nbox / t_other},
                 "batch_vs_grid_max_rel_err": worst,
                 "stage_ms_one_step": stage_ms}
         print(json.dumps(line), flush=True)

@@ -228,7 +228,8 @@ const char* wb_noalloc_last_error(void);
  * replays it from a captured CUDA graph (captured on first use per nsteps).
  * Synchronises the stream; returns WB_ERR_TIMEOUT if a barrier wait ran out.
  * wb_batch_autotune: times trial_steps real steps per candidate segment
- * length and blocks per SM, keeps the fastest (cached per box-size mix).
+ * length and blocks per SM in each form (below), keeps the fastest (cached
+ * per box-size mix).
  * wb_batch_config: set them explicitly (0 = keep); barrier_budget_cycles is
  * the per-barrier wait limit in SM clock cycles (default 20 s worth).
  * wb_batch_stage_timer: on != 0 zeroes and starts the per-stage timer (one
@@ -241,7 +242,18 @@ const char* wb_noalloc_last_error(void);
  * corner EMFs (9), their images, final CT (11), update (10), ghost fill;
  * *count = the number of stages (19).  The image stages copy periodic
  * images of intermediates for boxes periodic on every axis, whose other
- * stages then cover the interior only.  It synchronises the stream. */
+ * stages then cover the interior only.  It synchronises the stream.
+ * wb_batch_set_form: how wb_batch_advance runs the stages.
+ * WB_BATCH_PERSISTENT (the default): the one persistent cooperative launch
+ * above.  WB_BATCH_STAGED: one ordinary launch per stage of each step over
+ * all boxes of a workspace group (the same work lists and results bit for
+ * bit), each stage class compiled into its own kernel so that the zone
+ * stages run with their own occupancy; no grid barrier, so no
+ * WB_ERR_TIMEOUT.  With the stage timer on, the staged form times every
+ * stage but dt.  Drops a captured graph.  wb_batch_autotune tries both forms
+ * and keeps the faster; wb_batch_get_form reports the current one. */
+#define WB_BATCH_PERSISTENT 0
+#define WB_BATCH_STAGED 1
 typedef struct wb_batch wb_batch;
 int wb_batch_bytes(int nbox, const wb_desc* descs, size_t work_budget, size_t* bytes);
 int wb_batch_create(int nbox, const wb_desc* descs, size_t work_budget, void* dev_mem,
@@ -259,6 +271,8 @@ int wb_batch_config(wb_batch* b, int seg_len, int blocks_per_sm, long long barri
 int wb_batch_get_config(wb_batch* b, int* seg_len, int* blocks_per_sm, int* groups);
 int wb_batch_stage_timer(wb_batch* b, int on);
 int wb_batch_stage_times(wb_batch* b, double* ms, int n, int* count);
+int wb_batch_set_form(wb_batch* b, int form);
+int wb_batch_get_form(wb_batch* b, int* form);
 const char* wb_batch_last_error(const wb_batch* b);
 
 /* ---- serving: a batch as a pool boxes join and leave between launches ----

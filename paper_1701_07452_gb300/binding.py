@@ -29,8 +29,11 @@ EXPORTED = (
     "wb_batch_set_steps", "wb_batch_advance", "wb_batch_read", "wb_batch_counters",
     "wb_batch_autotune", "wb_batch_config", "wb_batch_get_config", "wb_batch_last_error",
     "wb_pool_bytes", "wb_pool_create", "wb_pool_admit", "wb_pool_release", "wb_pool_free_bytes",
-    "wb_batch_steps_left", "wb_batch_stage_timer", "wb_batch_stage_times",
+    "wb_batch_steps_left", "wb_batch_stage_timer", "wb_batch_stage_times", "wb_batch_set_form",
+    "wb_batch_get_form",
 )
+
+BATCH_FORMS = {"persistent": 0, "staged": 1}
 
 
 class WbDesc(ctypes.Structure):
@@ -126,6 +129,8 @@ def lib(build: bool = True):
             L.wb_batch_stage_times.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
             L.wb_batch_get_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]
+            L.wb_batch_set_form.argtypes = [vp, ctypes.c_int]
+            L.wb_batch_get_form.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
             L.wb_batch_last_error.argtypes = [vp]
             L.wb_batch_last_error.restype = ctypes.c_char_p
             L.wb_pool_bytes.argtypes = [ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
@@ -420,10 +425,18 @@ class Batch:
                  "wrap_erefh", "edges_corr", "wrap_edgesh", "ct_final", "update", "halo"]
         return {names[i] if i < len(names) else str(i): ms[i] for i in range(cnt.value)}
 
+    def set_form(self, form):
+        """"persistent" (one cooperative launch per advance) or "staged" (one
+        launch per stage); results are identical."""
+        self._check(lib().wb_batch_set_form(self._h, BATCH_FORMS[form]))
+
     def get_config(self):
         a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
         self._check(lib().wb_batch_get_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return {"seg_len": a.value, "blocks_per_sm": b.value, "groups": c.value}
+        f = ctypes.c_int(0)
+        self._check(lib().wb_batch_get_form(self._h, ctypes.byref(f)))
+        form = {v: k for k, v in BATCH_FORMS.items()}[f.value]
+        return {"seg_len": a.value, "blocks_per_sm": b.value, "groups": c.value, "form": form}
 
 
 class Pool(Batch):

@@ -169,6 +169,10 @@ struct BatchParams {
   int dt_lag;                 // dt from the previous step's start state
   int seg_len;
   long long budget;           // barrier wait budget in SM clock cycles
+  // staged form: k_batch runs only stage `stage` of group `stage_grp` (no
+  // barrier), launch stage_seq of the sequence; stage < 0: persistent form
+  int stage, stage_grp;
+  unsigned stage_seq;
 };
 
 // Grid-wide barrier with a bounded wait.  Returns false when the error word is
@@ -344,24 +348,29 @@ __device__ __forceinline__ void copy_stage(const WbView& v, int s, long long d0,
   }
 }
 
-// Items it0 and it1 (it1 < 0: none) of a pairing stage for one box.
-__device__ __forceinline__ void unit_pair(int s, int d, const BoxInfo& bi, long long it0, long long it1,
-                                          double dt) {
+// Items it0 and it1 (it1 < 0: none) of a copy stage (ghost fill, periodic
+// images) for one box.
+__device__ __forceinline__ void unit_pair_copy(int s, const BoxInfo& bi, long long it0, long long it1) {
   const WbView& v = bi.v;
   const bool two = it1 >= 0;
-  if (s == BS_HALO || stage_is_wrap(s)) {
-    long long d0, s0, d1 = 0, s1 = 0;
-    if (s == BS_HALO) {
-      wbu::halo_self_offsets(v.geo, bi.bc, it0, &d0, &s0);
-      if (two) wbu::halo_self_offsets(v.geo, bi.bc, it1, &d1, &s1);
-    } else {
-      const int depth = s == BS_W_QH ? 2 : 1;
-      wbu::wrap_shell_point(v.geo, depth, it0, &d0, &s0);
-      if (two) wbu::wrap_shell_point(v.geo, depth, it1, &d1, &s1);
-    }
-    copy_stage(v, s, d0, s0, d1, s1, two);
-    return;
+  long long d0, s0, d1 = 0, s1 = 0;
+  if (s == BS_HALO) {
+    wbu::halo_self_offsets(v.geo, bi.bc, it0, &d0, &s0);
+    if (two) wbu::halo_self_offsets(v.geo, bi.bc, it1, &d1, &s1);
+  } else {
+    const int depth = s == BS_W_QH ? 2 : 1;
+    wbu::wrap_shell_point(v.geo, depth, it0, &d0, &s0);
+    if (two) wbu::wrap_shell_point(v.geo, depth, it1, &d1, &s1);
   }
+  copy_stage(v, s, d0, s0, d1, s1, two);
+}
+
+// Items it0 and it1 (it1 < 0: none) of the reference EMF, corner EMF or CT
+// stages for one box.
+__device__ __forceinline__ void unit_pair_emf(int s, int d, const BoxInfo& bi, long long it0, long long it1,
+                                              double dt) {
+  const WbView& v = bi.v;
+  const bool two = it1 >= 0;
   const WbBox b = stage_box(s, d, v.geo.n, bi.wrap != 0);
   int i0, j0, k0, i1 = 0, j1 = 0, k1 = 0;
   item_ijk(b, it0, &i0, &j0, &k0);
@@ -403,6 +412,35 @@ __device__ __forceinline__ void unit_pair(int s, int d, const BoxInfo& bi, long 
   }
 }
 
+// One item of the reference EMF, corner EMF or CT stages (staged form: the
+// latency is hidden by resident warps rather than by pairs of items).
+__device__ __forceinline__ void unit_emf(int s, int d, const BoxInfo& bi, long long it, double dt) {
+  const WbView& v = bi.v;
+  const WbBox b = stage_box(s, d, v.geo.n, bi.wrap != 0);
+  int i, j, k;
+  item_ijk(b, it, &i, &j, &k);
+  if (s == BS_EREF) {
+    wbu::eref(v, 0, 0, i, j, k);
+  } else if (s == BS_EDGE_P || s == BS_EDGE_C) {
+    const bool corr = s == BS_EDGE_C;
+    if (d == 0) wbu::edge<0>(v, 0, corr, i, j, k);
+    else if (d == 1) wbu::edge<1>(v, 0, corr, i, j, k);
+    else wbu::edge<2>(v, 0, corr, i, j, k);
+  } else {
+    const bool fin = s == BS_CT_F;
+    if (d == 0) wbu::ct<0>(v, 0, 0, fin, dt, i, j, k);
+    else if (d == 1) wbu::ct<1>(v, 0, 0, fin, dt, i, j, k);
+    else wbu::ct<2>(v, 0, 0, fin, dt, i, j, k);
+  }
+}
+
+// Items it0 and it1 (it1 < 0: none) of a pairing stage for one box.
+__device__ __forceinline__ void unit_pair(int s, int d, const BoxInfo& bi, long long it0, long long it1,
+                                          double dt) {
+  if (s == BS_HALO || stage_is_wrap(s)) unit_pair_copy(s, bi, it0, it1);
+  else unit_pair_emf(s, d, bi, it0, it1, dt);
+}
+
 // dt of one box for the coming step (reading R3 of the design notes)
 __device__ void box_dt(const BatchParams& B, int box) {
   WbScalars* s = B.scal + box;
@@ -438,24 +476,65 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // EZ: compile-time mask of waves with eps_k = 0 (their Q-branch arithmetic is
 // dropped); PROT: the protection-floor test is compiled in.  The launch picks
 // the variant from the physics, as the grid path's sweep launches do.
+// Launch seq of a sequence uses chunk counter seq & 1 (and done counter
+// 5 + (seq & 1) when timing); its block 0 clears the other pair, which the
+// launch before it (complete by stream order) used.
+__device__ __forceinline__ unsigned* stage_counter(const BatchParams& B, unsigned seq) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicExch(B.sync + 3 + ((seq + 1) & 1u), 0u);
+    atomicExch(B.sync + 5 + ((seq + 1) & 1u), 0u);
+  }
+  return B.sync + 3 + (seq & 1u);
+}
+
+// Stage timer of the staged form: the last block to finish a launch adds the
+// time since the previous launch's end to the stage (the dt launch only sets
+// the mark, so time between advances is not counted).
+__device__ __forceinline__ void stage_stamp(const BatchParams& B, int s, unsigned seq) {
+  if (!B.prof) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(B.sync + 5 + (seq & 1u), 1u);
+    if (done == gridDim.x - 1) {
+      const unsigned long long t = global_ns();
+      unsigned long long* mark = B.prof + BS_COUNT;
+      if (s != BS_DT && *mark) B.prof[s] += t - *mark;
+      *mark = t;
+    }
+  }
+}
+
 template <int EZ, bool PROT>
 __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nsteps) {
   __shared__ double srec[2][wbu::R_WORDS][wbu::kBlock];
   __shared__ long long s_chunk;
   const wbu::Rec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
   const unsigned nblocks = gridDim.x;
+  // one stage of the staged form, or every stage of nsteps steps; the stage
+  // body below is the one copy of it either way, so both forms compute the
+  // same bits
+  const bool one = B.stage >= 0;
+  const int step_end = one ? 1 : nsteps;
+  const int grp0 = one ? B.stage_grp : 0, grp_end = one ? B.stage_grp + 1 : B.ngroups;
+  const int s0 = one ? B.stage : 0, s_end = one ? B.stage + 1 : BS_COUNT;
   unsigned stage_seq = 0;
   // stage timer: block 0 stamps the end of every stage (after its barrier)
-  const bool timer = B.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+  const bool timer = !one && B.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
   unsigned long long t_prev = timer ? global_ns() : 0ULL;
-  for (int step = 0; step < nsteps; ++step) {
-    for (int grp = 0; grp < B.ngroups; ++grp) {
+  for (int step = 0; step < step_end; ++step) {
+    for (int grp = grp0; grp < grp_end; ++grp) {
       const int gb0 = B.gfirst[grp];
       const int nbox = B.gfirst[grp + 1] - gb0;
-      for (int s = 0; s < BS_COUNT; ++s, ++stage_seq) {
-        unsigned* ctr = B.sync + 3 + (stage_seq & 1u);
-        // the other counter is idle during this stage: block 0 clears it
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(B.sync + 3 + ((stage_seq + 1) & 1u), 0u);
+      for (int s = s0; s < s_end; ++s, ++stage_seq) {
+        unsigned* ctr;
+        if (one) {
+          ctr = stage_counter(B, B.stage_seq);
+        } else {
+          ctr = B.sync + 3 + (stage_seq & 1u);
+          // the other counter is idle during this stage: block 0 clears it
+          if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(B.sync + 3 + ((stage_seq + 1) & 1u), 0u);
+        }
         const long long* pre = B.pre + B.pre_off[grp * BS_COUNT + s];
         const int nsub = stage_nsub(s);
         const int nent = nbox * nsub;
@@ -500,6 +579,10 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
           if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
           if (hll) atomicAdd((unsigned long long*)&B.scal[box].hll_faces, (unsigned long long)hll);
         }
+        if (one) {
+          stage_stamp(B, s, B.stage_seq);
+          return;
+        }
         if (!grid_barrier(B, nblocks)) return;
         if (timer) {
           const unsigned long long t = global_ns();
@@ -509,6 +592,115 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
       }
     }
   }
+}
+
+// ------------------------------------------------------------ staged form
+// The same stages as separate launches, one per stage and workspace group: a
+// kernel boundary takes the place of each grid barrier, and blocks drain the
+// same chunk lists from the stage's counter.  The sweeps run in k_batch (one
+// stage per launch); the zone stages run in kernels compiled per stage class,
+// with as many resident warps as their own registers allow (inside the
+// persistent kernel every stage keeps the sweep's 4 blocks of 64 threads per
+// SM).  The zone stages' arithmetic is written with explicit rounding, so
+// both forms compute the same bits.
+enum { SC_SWEEP = 0, SC_COPY, SC_PAIR, SC_TRANS, SC_EREF_H, SC_FINAL, SC_DT, SC_COUNT };
+
+__host__ __device__ inline int stage_class(int s) {
+  if (stage_is_sweep(s)) return SC_SWEEP;
+  if (s == BS_HALO || stage_is_wrap(s)) return SC_COPY;  // copies of up to 24 arrays
+  if (stage_pairs(s)) return SC_PAIR;                    // reference EMF, corner EMFs, CT (one item a thread)
+  if (s == BS_TRANS) return SC_TRANS;
+  if (s == BS_EREF_H) return SC_EREF_H;
+  if (s == BS_FINAL) return SC_FINAL;
+  return SC_DT;
+}
+
+constexpr int kNtZone = 256;  // threads per block of the zone-stage kernels
+
+// resident blocks per SM each zone-stage kernel is compiled for (its register
+// budget: 64 registers a thread at 4 blocks of 256 threads)
+__host__ __device__ constexpr int zone_min_blocks(int cls) {
+  return cls == SC_TRANS ? 2 : ((cls == SC_EREF_H || cls == SC_FINAL) ? 3 : 4);
+}
+
+// Chunks of stage s for the boxes of group grp, claimed by whole blocks:
+// body(box, sub, chunk index within the (box, sub) entry).
+template <class Body>
+__device__ __forceinline__ void drain_stage(const BatchParams& B, int grp, int s, unsigned* ctr,
+                                            Body&& body) {
+  __shared__ long long s_chunk;
+  const int gb0 = B.gfirst[grp];
+  const int nbox = B.gfirst[grp + 1] - gb0;
+  const long long* pre = B.pre + B.pre_off[grp * BS_COUNT + s];
+  const int nsub = stage_nsub(s);
+  const int nent = nbox * nsub;
+  const long long nchunks = pre[nent];
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(ctr, 1u);
+    __syncthreads();
+    const long long c = s_chunk;
+    __syncthreads();
+    if (c >= nchunks) break;
+    int lo = 0, hi = nent - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    body(B.gbox[gb0 + lo / nsub], lo % nsub, c - pre[lo]);
+  }
+}
+
+template <int CLS>
+__global__ void __launch_bounds__(kNtZone, zone_min_blocks(CLS))
+    k_bstage_zone(BatchParams B, int grp, int s, unsigned seq) {
+  constexpr int NT = kNtZone;
+  unsigned* ctr = stage_counter(B, seq);
+  const int ipc = items_per_chunk(s);
+  drain_stage(B, grp, s, ctr, [&](int box, int d, long long cc) {
+    if (CLS == SC_DT) {
+      if (threadIdx.x == 0) box_dt(B, box);
+      return;
+    }
+    const double dt = B.scal[box].dt;
+    if (!(dt > 0.0)) return;
+    const BoxInfo& bi = B.boxes[box];
+    const long long nitems = stage_items(s, d, bi.v.geo, bi.wrap != 0, B.seg_len);
+    const long long i0 = cc * ipc;
+    const long long i1 = i0 + ipc < nitems ? i0 + ipc : nitems;
+    if (CLS == SC_COPY) {
+      for (long long it = i0 + threadIdx.x; it < i1; it += 2 * NT)
+        unit_pair_copy(s, bi, it, it + NT < i1 ? it + NT : -1);
+      return;
+    }
+    if (CLS == SC_PAIR) {
+      for (long long it = i0 + threadIdx.x; it < i1; it += NT) unit_emf(s, d, bi, it, dt);
+      return;
+    }
+    const WbView& v = bi.v;
+    const WbBox b = stage_box(s, d, v.geo.n, bi.wrap != 0);
+    double wmax = 0.0;
+    int hits = 0, bad = 0;
+    for (long long it = i0 + threadIdx.x; it < i1; it += NT) {
+      int i, j, k;
+      item_ijk(b, it, &i, &j, &k);
+      if (CLS == SC_TRANS) {
+        const int mask = trans_mask(v.geo.n, i, j, k);
+        if (mask) wbu::transverse_set(v, 0, 0, dt, mask, i, j, k);
+      } else if (CLS == SC_EREF_H) {
+        wbu::eref_half(v, 0, 0, dt, i, j, k);
+      } else {
+        const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, &hits, &bad);
+        wmax = fmax(wmax, w);
+        if (w != w) wmax = w;
+      }
+    }
+    if (CLS == SC_FINAL) {
+      warp_max_atomic(wmax, &B.scal[box].wmax_next);
+      if (hits) atomicAdd((unsigned long long*)&B.scal[box].floor_hits, (unsigned long long)hits);
+      if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
+    }
+  });
+  stage_stamp(B, s, seq);
 }
 
 // initial signal rate of one box (the view is passed by value: the device box
@@ -536,7 +728,10 @@ struct TuneKey {
   bool operator<(const TuneKey& o) const { return sizes < o.sizes; }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;  // -> (seg_len, blocks per SM)
+struct TuneVal {
+  int seg_len, blocks_per_sm, form;
+};
+std::map<TuneKey, TuneVal> g_tune_cache;
 
 }  // namespace
 
@@ -578,6 +773,8 @@ struct wb_batch {
   double* staging;
   size_t pre_cap;
   // launch configuration
+  int form = WB_BATCH_PERSISTENT;
+  int zone_blocks[SC_COUNT];  // resident blocks per SM of each zone-stage kernel (staged form)
   int seg_len;
   int blocks_per_sm;
   int max_blocks_per_sm;
@@ -652,7 +849,7 @@ PoolSizes pool_sizes(size_t state_bytes, size_t work_bytes, int cap, int max_n) 
   P.tables = al(sizeof(BoxInfo) * cap) + al(sizeof(WbScalars) * cap) + al(sizeof(int) * cap) +
              al(sizeof(int) * cap) + al(sizeof(int) * (cap + 1)) + al(sizeof(long long) * P.pre_cap) +
              al(sizeof(long long) * (size_t)cap * BS_COUNT) + al(sizeof(unsigned) * 8) +
-             al(sizeof(unsigned long long) * BS_COUNT);
+             al(sizeof(unsigned long long) * (BS_COUNT + 1));
   P.staging = al(sizeof(double) * (size_t)(max_n + 1) * (max_n + 1) * (max_n + 1));
   P.total = P.state + P.work + P.tables + P.staging;
   return P;
@@ -771,6 +968,9 @@ BatchParams params(const wb_batch* b) {
   p.dt_lag = b->dt_lag;
   p.seg_len = b->seg_len;
   p.budget = b->budget;
+  p.stage = -1;
+  p.stage_grp = 0;
+  p.stage_seq = 0;
   return p;
 }
 
@@ -783,8 +983,61 @@ const void* batch_kernel(const WbPhys& ph) {
   return (const void*)k_batch<0, true>;
 }
 
-// enqueue one persistent launch of nsteps steps (no synchronisation)
+const void* bstage_zone_kernel(int cls) {
+  switch (cls) {
+    case SC_COPY: return (const void*)k_bstage_zone<SC_COPY>;
+    case SC_PAIR: return (const void*)k_bstage_zone<SC_PAIR>;
+    case SC_TRANS: return (const void*)k_bstage_zone<SC_TRANS>;
+    case SC_EREF_H: return (const void*)k_bstage_zone<SC_EREF_H>;
+    case SC_FINAL: return (const void*)k_bstage_zone<SC_FINAL>;
+    default: return (const void*)k_bstage_zone<SC_DT>;
+  }
+}
+
+// enqueue the staged form of nsteps steps: one launch per (step, group,
+// stage), no synchronisation
+cudaError_t enqueue_staged(wb_batch* b, int nsteps) {
+  cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * 8, b->stream);
+  if (e != cudaSuccess) return e;
+  BatchParams p = params(b);
+  unsigned seq = 0;
+  for (int step = 0; step < nsteps; ++step)
+    for (int grp = 0; grp < p.ngroups; ++grp)
+      for (int s = 0; s < BS_COUNT; ++s, ++seq) {
+        const int cls = stage_class(s);
+        const void* fn;
+        unsigned nt, nblocks;
+        if (cls == SC_SWEEP) {
+          fn = batch_kernel(b->phys);
+          nt = kB;
+          nblocks = (unsigned)(b->blocks_per_sm * b->sms);
+        } else {
+          fn = bstage_zone_kernel(cls);
+          nt = kNtZone;
+          nblocks = (unsigned)((cls == SC_DT ? 1 : b->zone_blocks[cls]) * b->sms);
+        }
+        if (cls == SC_SWEEP) {
+          // the sweeps run in k_batch itself (one stage, no barrier): the
+          // same compiled sweep as the persistent form
+          p.stage = s;
+          p.stage_grp = grp;
+          p.stage_seq = seq;
+          int one = 1;
+          void* args[] = {&p, &one};
+          e = cudaLaunchKernel(fn, dim3(nblocks), dim3(nt), args, 0, b->stream);
+        } else {
+          void* args[] = {&p, &grp, &s, &seq};
+          e = cudaLaunchKernel(fn, dim3(nblocks), dim3(nt), args, 0, b->stream);
+        }
+        if (e != cudaSuccess) return e;
+      }
+  return cudaSuccess;
+}
+
+// enqueue nsteps steps in the batch's form (no synchronisation); the
+// persistent form is one cooperative launch
 cudaError_t enqueue_advance(wb_batch* b, int nsteps) {
+  if (b->form == WB_BATCH_STAGED) return enqueue_staged(b, nsteps);
   cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * 8, b->stream);
   if (e != cudaSuccess) return e;
   BatchParams p = params(b);
@@ -835,8 +1088,9 @@ void apply_tune_cache(wb_batch* b) {
   std::sort(key.sizes.begin(), key.sizes.end());
   auto it = g_tune_cache.find(key);
   if (it != g_tune_cache.end()) {
-    b->seg_len = it->second.first;
-    b->blocks_per_sm = std::min(it->second.second, b->max_blocks_per_sm);
+    b->seg_len = it->second.seg_len;
+    b->blocks_per_sm = std::min(it->second.blocks_per_sm, b->max_blocks_per_sm);
+    b->form = it->second.form;
   }
 }
 
@@ -893,7 +1147,7 @@ int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes
   b->d_pre = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * P.pre_cap);
   b->d_pre_off = reinterpret_cast<long long*>(t); t += al(sizeof(long long) * (size_t)max_boxes * BS_COUNT);
   b->d_sync = reinterpret_cast<unsigned*>(t); t += al(sizeof(unsigned) * 8);
-  b->d_prof = reinterpret_cast<unsigned long long*>(t); t += al(sizeof(unsigned long long) * BS_COUNT);
+  b->d_prof = reinterpret_cast<unsigned long long*>(t); t += al(sizeof(unsigned long long) * (BS_COUNT + 1));
   b->staging = reinterpret_cast<double*>(b->mem + P.state + P.work + P.tables);
   b->staging_elems = P.staging / sizeof(double);
   int dev = 0;
@@ -903,6 +1157,11 @@ int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel(b->phys), kB, 0);
   b->max_blocks_per_sm = nb > 0 ? nb : 1;
   b->blocks_per_sm = b->max_blocks_per_sm;
+  for (int c = 0; c < SC_COUNT; ++c) {
+    nb = 0;
+    if (c != SC_SWEEP) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bstage_zone_kernel(c), kNtZone, 0);
+    b->zone_blocks[c] = nb > 0 ? nb : 1;
+  }
   b->seg_len = 32;
   int clk_khz = 0;
   cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
@@ -1243,7 +1502,7 @@ int wb_batch_stage_timer(wb_batch* b, int on) {
   drop_graph(b);
   b->prof = on != 0;
   if (b->prof) {
-    cudaError_t e = cudaMemsetAsync(b->d_prof, 0, sizeof(unsigned long long) * BS_COUNT, b->stream);
+    cudaError_t e = cudaMemsetAsync(b->d_prof, 0, sizeof(unsigned long long) * (BS_COUNT + 1), b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "stage timer");
   }
   return WB_OK;
@@ -1257,6 +1516,20 @@ int wb_batch_stage_times(wb_batch* b, double* ms, int n, int* count) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(b, e, "stage times");
   for (int i = 0; i < n && i < BS_COUNT; ++i) ms[i] = 1e-6 * (double)ns[i];
+  return WB_OK;
+}
+
+int wb_batch_set_form(wb_batch* b, int form) {
+  if (!b || (form != WB_BATCH_PERSISTENT && form != WB_BATCH_STAGED))
+    return bfail(b, WB_ERR_INVALID, "unknown batch form");
+  if (form != b->form) drop_graph(b);
+  b->form = form;
+  return WB_OK;
+}
+
+int wb_batch_get_form(wb_batch* b, int* form) {
+  if (!b || !form) return WB_ERR_INVALID;
+  *form = b->form;
   return WB_OK;
 }
 
@@ -1297,21 +1570,28 @@ int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms) {
     cudaEventElapsedTime(ms, e0, e1);
     return WB_OK;
   };
-  int best_seg = b->seg_len, best_b = b->max_blocks_per_sm;
+  int best_seg = b->seg_len, best_b = b->max_blocks_per_sm, best_form = b->form;
   float best = 1e30f, ms = 0.f;
   int rc = WB_OK;
-  for (int seg : segs) {
-    rc = trial(seg, b->max_blocks_per_sm, &ms);
-    if (rc) break;
-    if (ms < best) { best = ms; best_seg = seg; }
-  }
-  for (int bps = 1; rc == WB_OK && bps < b->max_blocks_per_sm; ++bps) {
-    rc = trial(best_seg, bps, &ms);
-    if (rc) break;
-    if (ms < best) { best = ms; best_b = bps; }
+  for (int form = WB_BATCH_PERSISTENT; rc == WB_OK && form <= WB_BATCH_STAGED; ++form) {
+    b->form = form;
+    int fseg = b->seg_len, fb = b->max_blocks_per_sm;
+    float fbest = 1e30f;
+    for (int seg : segs) {
+      rc = trial(seg, b->max_blocks_per_sm, &ms);
+      if (rc) break;
+      if (ms < fbest) { fbest = ms; fseg = seg; }
+    }
+    for (int bps = 1; rc == WB_OK && bps < b->max_blocks_per_sm; ++bps) {
+      rc = trial(fseg, bps, &ms);
+      if (rc) break;
+      if (ms < fbest) { fbest = ms; fb = bps; }
+    }
+    if (rc == WB_OK && fbest < best) { best = fbest; best_seg = fseg; best_b = fb; best_form = form; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->form = best_form;
   if (rc) return rc;
   rc = wb_batch_config(b, best_seg, best_b, 0);
   if (rc) return rc;
@@ -1321,7 +1601,7 @@ int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms) {
     for (int i = 0; i < b->cap; ++i)
       if (b->alive[i]) key.sizes.push_back(b->d[i].n[0] * 1000000 + b->d[i].n[1] * 1000 + b->d[i].n[2]);
     std::sort(key.sizes.begin(), key.sizes.end());
-    g_tune_cache[key] = {best_seg, best_b};
+    g_tune_cache[key] = {best_seg, best_b, best_form};
   }
   if (best_ms) *best_ms = best;
   return WB_OK;

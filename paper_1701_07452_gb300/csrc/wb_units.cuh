@@ -628,6 +628,8 @@ __device__ __forceinline__ void ct(const WbView& v, long long qo, long long wo, 
 // the face-field differences scaled by dt/2 (h db_e = dt/2 (b_e+ - b_e)/dx_e;
 // minmod commutes with the positive factor dt/2), the flux-difference factors
 // c_e = dt/2 / dx_e and the transverse flux differences dF_e = F_e+ - F_e.
+// The arithmetic is written with explicit rounding: the same bits in every
+// kernel it is inlined into (the grid path, both forms of the batch path).
 struct TransZone {
   double qn[8];
   double vv[3], B[3], Bv[3], hdb[3], c[3];
@@ -644,18 +646,18 @@ __device__ __forceinline__ void trans_zone(const WbView& v, long long q, long lo
   const double ir = wb_rcp(z.qn[F_RHO]);
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    z.vv[e] = z.qn[F_MX + e] * ir;
+    z.vv[e] = __dmul_rn(z.qn[F_MX + e], ir);
     z.B[e] = z.qn[F_BX + e];
-    z.Bv[e] = z.B[e] * z.vv[e];
-    z.c[e] = hdt * g.idx[e];
-    z.hdb[e] = (v.b[e][q + s[e]] - v.b[e][q]) * z.c[e];
+    z.Bv[e] = __dmul_rn(z.B[e], z.vv[e]);
+    z.c[e] = __dmul_rn(hdt, g.idx[e]);
+    z.hdb[e] = __dmul_rn(__dsub_rn(v.b[e][q + s[e]], v.b[e][q]), z.c[e]);
   }
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
 #pragma unroll
     for (int cc = 0; cc < 8; ++cc) {
       if (cc == F_BX + e || !(need & (1 << e))) { z.dF[e][cc] = 0.0; continue; }
-      z.dF[e][cc] = v.Fp[e][cc][w + s[e]] - v.Fp[e][cc][w];
+      z.dF[e][cc] = __dsub_rn(v.Fp[e][cc][w + s[e]], v.Fp[e][cc][w]);
     }
   }
 }
@@ -668,18 +670,19 @@ __device__ __forceinline__ void trans_dir(const WbView& v, long long w, const Tr
   const long long sD = D == 0 ? 1 : (D == 1 ? v.geo.sy : v.geo.sz);
   const double hm2 = wb_minmod(z.hdb[D], -z.hdb[t1]);  // for the t2 field component
   const double hm1 = wb_minmod(z.hdb[D], -z.hdb[t2]);  // for the t1 field component
-  double hS[8];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) hS[F_MX + e] = z.B[e] * z.hdb[D];
-  hS[F_EN] = fma(z.Bv[D], z.hdb[D], fma(z.Bv[t1], hm1, z.Bv[t2] * hm2));
+  const double hSe = __fma_rn(z.Bv[D], z.hdb[D], __fma_rn(z.Bv[t1], hm1, __dmul_rn(z.Bv[t2], hm2)));
   const double c1 = z.c[t1], c2 = z.c[t2];
-  v.qh[D][F_RHO][w] = fma(-c2, z.dF[t2][F_RHO], fma(-c1, z.dF[t1][F_RHO], z.qn[F_RHO]));
+  double u[8];
 #pragma unroll
-  for (int cc = F_MX; cc <= F_EN; ++cc)
-    v.qh[D][cc][w] = fma(-c2, z.dF[t2][cc], fma(-c1, z.dF[t1][cc], z.qn[cc])) + hS[cc];
-  v.qh[D][F_BX + t1][w] = fma(-c2, z.dF[t2][F_BX + t1], z.qn[F_BX + t1]) + z.vv[t1] * hm1;
-  v.qh[D][F_BX + t2][w] = fma(-c1, z.dF[t1][F_BX + t2], z.qn[F_BX + t2]) + z.vv[t2] * hm2;
-  v.qh[D][F_BX + D][w] = wb_half(v.bh[D][w] + v.bh[D][w + sD]);
+  for (int cc = F_RHO; cc <= F_EN; ++cc)
+    u[cc] = __fma_rn(-c2, z.dF[t2][cc], __fma_rn(-c1, z.dF[t1][cc], z.qn[cc]));
+  v.qh[D][F_RHO][w] = u[F_RHO];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) v.qh[D][F_MX + e][w] = __fma_rn(z.B[e], z.hdb[D], u[F_MX + e]);
+  v.qh[D][F_EN][w] = __dadd_rn(u[F_EN], hSe);
+  v.qh[D][F_BX + t1][w] = __fma_rn(z.vv[t1], hm1, __fma_rn(-c2, z.dF[t2][F_BX + t1], z.qn[F_BX + t1]));
+  v.qh[D][F_BX + t2][w] = __fma_rn(z.vv[t2], hm2, __fma_rn(-c1, z.dF[t1][F_BX + t2], z.qn[F_BX + t2]));
+  v.qh[D][F_BX + D][w] = wb_half(__dadd_rn(v.bh[D][w], v.bh[D][w + sD]));
 }
 
 // The directions in mask (bit d) at one zone, sharing the zone quantities and
@@ -859,7 +862,7 @@ __device__ __forceinline__ double screened_rate(double ir, const double vv[3], d
 
 // kinetic energy density rho v^2 / 2 from the momentum and the velocity
 __device__ __forceinline__ double kinetic(const double m[3], const double vv[3]) {
-  return wb_half(fma(m[2], vv[2], fma(m[1], vv[1], m[0] * vv[0])));
+  return wb_half(__fma_rn(m[2], vv[2], __fma_rn(m[1], vv[1], __dmul_rn(m[0], vv[0]))));
 }
 
 // The signal rate of one stored zone (conserved state and zone field), or 0
@@ -889,32 +892,33 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
   const long long q = qo + wb_at(g, i, j, k);
   const long long wi = wo + wb_at(g, i, j, k);
   const long long s[3] = {1, g.sy, g.sz};
-  const double cx = dt * g.idx[0], cy = dt * g.idx[1], cz = dt * g.idx[2];
+  // explicit rounding: the same bits in every kernel this is inlined into
+  const double cx = __dmul_rn(dt, g.idx[0]), cy = __dmul_rn(dt, g.idx[1]), cz = __dmul_rn(dt, g.idx[2]);
   double u[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     double x = v.q[c][q];
-    x = x - cx * (v.Fc[0][c][wi + 1] - v.Fc[0][c][wi]);
-    x = x - cy * (v.Fc[1][c][wi + s[1]] - v.Fc[1][c][wi]);
-    x = x - cz * (v.Fc[2][c][wi + s[2]] - v.Fc[2][c][wi]);
+    x = __fma_rn(-cx, __dsub_rn(v.Fc[0][c][wi + 1], v.Fc[0][c][wi]), x);
+    x = __fma_rn(-cy, __dsub_rn(v.Fc[1][c][wi + s[1]], v.Fc[1][c][wi]), x);
+    x = __fma_rn(-cz, __dsub_rn(v.Fc[2][c][wi + s[2]], v.Fc[2][c][wi]), x);
     u[c] = x;
   }
   double B[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    B[e] = wb_half(v.b[e][q] + v.b[e][q + s[e]]);
+    B[e] = wb_half(__dadd_rn(v.b[e][q], v.b[e][q + s[e]]));
     v.q[F_BX + e][q] = B[e];
   }
   if (u[0] < P.rho_floor) { u[0] = P.rho_floor; ++*hits; }
   const double ir = wb_rcp(u[0]);
   const double m[3] = {u[1], u[2], u[3]};
-  const double vv[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
+  const double vv[3] = {__dmul_rn(u[1], ir), __dmul_rn(u[2], ir), __dmul_rn(u[3], ir)};
   const double ke = kinetic(m, vv);
-  const double me = wb_half(fma(B[2], B[2], fma(B[1], B[1], B[0] * B[0])));
-  double p = P.gm1 * (u[4] - ke - me);
+  const double me = wb_half(__fma_rn(B[2], B[2], __fma_rn(B[1], B[1], __dmul_rn(B[0], B[0]))));
+  double p = __dmul_rn(P.gm1, __dsub_rn(__dsub_rn(u[4], ke), me));
   if (p < P.p_floor) {
-    u[4] = P.p_floor * P.inv_gm1 + ke + me;
-    p = P.gm1 * (u[4] - ke - me);
+    u[4] = __dadd_rn(__fma_rn(P.p_floor, P.inv_gm1, ke), me);
+    p = __dmul_rn(P.gm1, __dsub_rn(__dsub_rn(u[4], ke), me));
     ++*hits;
   }
   const bool fin = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]) &&

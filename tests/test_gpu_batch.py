@@ -1,6 +1,7 @@
 """Batching pattern: many independent boxes of uneven sizes advanced by one
-persistent kernel with per-box dt (wb_batch_*), compared with the single-box
-grid path, alone vs in the mix, graph vs direct launch, after autotuning, and
+persistent kernel with per-box dt (wb_batch_*), or by one launch per stage
+(the staged form), compared with the single-box grid path, alone vs in the
+mix, graph vs direct launch, persistent vs staged, after autotuning, and
 with a barrier wait forced to run out (error status, context still usable)."""
 import numpy as np
 import pytest
@@ -50,9 +51,12 @@ def test_batch_matches_single_box_grids(wb):
         assert abs(c["t"] - g.counters()["t"]) <= 1e-13 * c["t"]
 
 
-def test_alone_and_in_the_mix_are_bit_identical(wb):
+@pytest.mark.parametrize("form", ["persistent", "staged"])
+def test_alone_and_in_the_mix_are_bit_identical(wb, form):
     boxes, states = boxes_and_states(SIZES)
     mix = wb.Batch(boxes, work_budget=8 << 20)  # several workspace groups
+    mix.set_form(form)
+    assert mix.get_config()["groups"] > 1
     for i, st in enumerate(states):
         mix.load_state(i, st)
     mix.set_steps(-1, 3)
@@ -71,22 +75,25 @@ def test_alone_and_in_the_mix_are_bit_identical(wb):
 def test_graph_direct_and_autotuned_runs_agree(wb):
     boxes, states = boxes_and_states(SIZES[:4], seed0=200)
     runs = []
-    for mode in ("graph", "direct", "tuned"):
+    for mode in ("graph", "direct", "tuned", "staged", "staged_direct"):
         bt = wb.Batch(boxes)
+        if mode.startswith("staged"):
+            bt.set_form("staged")
         for i, st in enumerate(states):
             bt.load_state(i, st)
         if mode == "tuned":
             bt.set_steps(-1, 1000)
             bt.autotune(trial_steps=1)          # real steps, any configuration
             done = bt.counters(0)["steps"]
-            bt.set_steps(-1, 12 - done)
-            bt.advance(12 - done)
+            assert done <= 30
+            bt.set_steps(-1, 30 - done)
+            bt.advance(30 - done)
         else:
-            bt.set_steps(-1, 12)
+            bt.set_steps(-1, 30)
             for _ in range(3):
-                bt.advance(4, use_graph=(mode == "graph"))
+                bt.advance(10, use_graph=mode in ("graph", "staged"))
         runs.append([bt.read(i) for i in range(len(boxes))])
-        assert all(bt.counters(i)["steps"] == 12 for i in range(len(boxes)))
+        assert all(bt.counters(i)["steps"] == 30 for i in range(len(boxes)))
     for other in runs[1:]:
         for ra, rb in zip(runs[0], other):
             for a, b in zip(ra, rb):
@@ -110,3 +117,24 @@ def test_barrier_timeout_returns_status_and_context_survives(wb):
     ok.set_steps(-1, 2)
     ok.advance(2)
     assert ok.counters(0)["steps"] == 2
+
+
+def test_staged_stage_timer(wb):
+    """The staged form times every stage but dt; its stage times add up to
+    no more than the wall time of the advance."""
+    import time
+    boxes, states = boxes_and_states(SIZES[:3], seed0=400)
+    bt = wb.Batch(boxes)
+    bt.set_form("staged")
+    for i, st in enumerate(states):
+        bt.load_state(i, st)
+    bt.set_steps(-1, 3)
+    bt.stage_timer(True)
+    t0 = time.perf_counter()
+    bt.advance(3, use_graph=False)
+    wall = time.perf_counter() - t0
+    ms = bt.stage_times()
+    assert len(ms) == 19 and ms["dt"] == 0.0
+    assert ms["pred_sweeps"] > 0 and ms["corr_sweeps"] > 0 and ms["update"] > 0
+    assert sum(ms.values()) <= wall * 1e3
+    assert all(bt.counters(i)["steps"] == 3 for i in range(3))

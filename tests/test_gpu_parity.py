@@ -98,6 +98,31 @@ def test_patches_bit_exact(wb, n, patches, batch):
         assert np.array_equal(a, b)
 
 
+def test_balanced_sweep_split(wb, oracle_mod):
+    """Boxes large enough that every sweep launch hands each resident warp an
+    equal run of (slot, 32-pencil group, face) units (at least 64 units per
+    warp on a 152-SM GPU at 4 resident 64-thread blocks per SM), with a ragged
+    last group of pencils: one step against the oracle, and 2^3 resident
+    patches against the single grid bit for bit (the runs then span slots)."""
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box
+    n = (150, 136, 144)   # z sweep: 20400 pencils, the last group holds 16
+    st = turbulence_box(n, seed=11)
+    g, o = make_pair(wb, oracle_mod, st, n)
+    g.advance(1)
+    o.advance(1)
+    assert state_err(g.read(), o.read()) < 1e-11
+    n = (140, 140, 140)   # 4900 pencils per patch, the last group holds 4
+    st = turbulence_box(n, seed=12)
+    ref = wb.Grid(n, length=st["length"])
+    ref.load_state(st)
+    ref.advance(2)
+    pg = wb.Grid(n, patches=(2, 2, 2), length=st["length"], batch_patches=0)
+    pg.load_state(st)
+    pg.advance(2)
+    for a, b in zip(ref.read(), pg.read()):
+        assert np.array_equal(a, b)
+
+
 def test_uniform_state_bit_exact(wb):
     n = (10, 9, 8)
     W = np.zeros((5, n[2], n[1], n[0]))
