@@ -14,6 +14,10 @@ released and recorded as failed, and the loop keeps serving the others.  A
 run can be cancelled at a given time: dropped from the queue if it has not
 been admitted, released at the next tick boundary if it is resident.
 
+Each tick runs in the pool's staged form by default (one launch per stage;
+form="persistent" selects the one cooperative launch); results do not depend
+on the form.
+
 Two tick policies.  "fair": every resident run advances up to tick_steps per
 tick (processor sharing).  "srpt": each tick grants up to tick_steps steps to
 the resident runs in order of least remaining work (zones x steps left)
@@ -57,8 +61,10 @@ class Record:
 
 class Server:
     def __init__(self, state_bytes, work_bytes, max_boxes=512, max_n=256, tick_steps=4,
-                 use_graph=True, keep_results=False, policy="fair", tick_cells=1.5e8, **physics):
+                 use_graph=True, keep_results=False, policy="fair", tick_cells=1.5e8,
+                 form="staged", **physics):
         self.pool = binding.Pool(state_bytes, work_bytes, max_boxes=max_boxes, max_n=max_n, **physics)
+        self.pool.set_form(form)
         self.tick_steps = int(tick_steps)
         self.use_graph = use_graph
         self.keep_results = keep_results

@@ -1,6 +1,7 @@
 """Serving pattern on the GPU: runs that arrive while others are resident are
 admitted as memory frees up, share launches, and each result is bit-identical
-to the same run served alone, under either tick policy."""
+to the same run served alone, under either tick policy and either batch
+form."""
 import numpy as np
 import pytest
 
@@ -41,8 +42,10 @@ def test_served_results_equal_alone_results(mods, policy):
     assert len(recs) == len(reqs)
     assert any(r.admitted > r.arrival + 1e-6 for r in recs), "budget never delayed an admission"
     for r, rec in zip(reqs, recs):
+        # alone in the other batch form for the fair policy: forms give the same bits
         alone = serve.Server(state_bytes=per + 4096, work_bytes=64 << 20, max_boxes=2, max_n=32,
-                             tick_steps=3, keep_results=True)
+                             tick_steps=3, keep_results=True,
+                             form="persistent" if policy == "fair" else "staged")
         (arec,) = alone.run([serve.Request(r.rid, 0.0, r.n, r.steps, r.state, r.length)])
         for a, b in zip(arec.result, rec.result):
             assert np.array_equal(a, b), r.rid
