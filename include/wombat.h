@@ -75,7 +75,14 @@ extern "C" {
  *  dt_lag      0: each step's dt comes from its start state; 1: from the
  *              previous step's start state (the paper delays the dt
  *              reduction by one step to overlap it with work, Sec. on the
- *              MPI-RMA engine); the first two steps use the loaded state. */
+ *              MPI-RMA engine); the first two steps use the loaded state.
+ *  keep_stages 0 (default): the corrector fluxes, the half-step reference
+ *              EMF and the corrector corner EMFs reuse the arrays of their
+ *              predictor counterparts, whose last reader has run by then
+ *              (54 doubles of workspace per padded zone and patch of a pass);
+ *              1: every intermediate of the step keeps its own array (81),
+ *              so that wb_debug_stage can also return the predictor fluxes.
+ *              Batches and pools ignore it (they always reuse). */
 typedef struct wb_desc {
   int n[3];
   int patches[3];
@@ -91,6 +98,7 @@ typedef struct wb_desc {
   double prot_rho;
   double prot_p;
   int dt_lag;
+  int keep_stages;
 } wb_desc;
 
 typedef struct wb_counters_t {
@@ -166,9 +174,11 @@ int wb_counters(wb_grid* g, wb_counters_t* c);
 const char* wb_last_error(const wb_grid* g);
 
 /* Stage dump of the last step (debugging and parity tests): which = 0..2
- * predictor fluxes F, G, H; 3..5 corrector fluxes; 6..8 b^{n+1/2}; 9..11
- * q^{n+1/2}_x,y,z -- same layouts as the oracle's dump (single patch only).
- * Copies to host memory out (cap doubles); *written = doubles written. */
+ * predictor fluxes F, G, H (only for a grid created with keep_stages = 1;
+ * WB_ERR_INVALID otherwise, the corrector has overwritten them); 3..5
+ * corrector fluxes; 6..8 b^{n+1/2}; 9..11 q^{n+1/2}_x,y,z -- same layouts as
+ * the oracle's dump (single patch only).  Copies to host memory out (cap
+ * doubles); *written = doubles written. */
 int wb_debug_stage(wb_grid* g, int which, double* out, long long cap, long long* written);
 
 /* Kernel timing of the MHDTVD sweep launches (Steps 1, 6, 7): enable != 0
@@ -186,10 +196,10 @@ int wb_profile_read(wb_grid* g, double* sweep_ms, long long* launches);
  * device buffers), so it cannot size a wb_grid workspace for them.  Its
  * intermediates live in a static device array of 24 MiB inside this library
  * (held by every GPU that loads the library until process exit).  A box
- * needs about 736 (nx+10)(ny+10)(nz+10) + 8 (nx+1)(ny+1)(nz+1) bytes of it
- * (state, one step's intermediates, reductions), so cubes up to 22^3
- * interior zones fit; larger boxes return WB_ERR_INVALID with a message in
- * wb_noalloc_last_error().
+ * needs about 520 (nx+10)(ny+10)(nz+10) + 8 (nx+1)(ny+1)(nz+1) bytes of it
+ * (state, one step's intermediates with keep_stages = 0, reductions), so
+ * cubes up to 25^3 interior zones fit; larger boxes return WB_ERR_INVALID
+ * with a message in wb_noalloc_last_error().
  *  d        descriptor of one box: patches must be (1,1,1); batch_patches is
  *           ignored
  *  U, bx, by, bz          device input state (layouts above)

@@ -52,6 +52,7 @@ class WbDesc(ctypes.Structure):
         ("prot_rho", ctypes.c_double),
         ("prot_p", ctypes.c_double),
         ("dt_lag", ctypes.c_int),
+        ("keep_stages", ctypes.c_int),
     ]
 
 
@@ -149,7 +150,7 @@ def lib(build: bool = True):
 
 def make_desc(n, patches=(1, 1, 1), length=None, gamma=5.0 / 3.0, cfl=0.8, bc=(0, 0, 0),
               eps=DEFAULT_EPS, sweby=1.0, rho_floor=1e-20, p_floor=1e-20, batch_patches=0,
-              prot_rho=0.0, prot_p=0.0, dt_lag=False):
+              prot_rho=0.0, prot_p=0.0, dt_lag=False, keep_stages=False):
     d = WbDesc()
     lib().wb_desc_default(ctypes.byref(d), int(n[0]), int(n[1]), int(n[2]))
     for a in range(3):
@@ -163,6 +164,7 @@ def make_desc(n, patches=(1, 1, 1), length=None, gamma=5.0 / 3.0, cfl=0.8, bc=(0
     d.batch_patches = int(batch_patches)
     d.prot_rho, d.prot_p = float(prot_rho), float(prot_p)
     d.dt_lag = int(bool(dt_lag))
+    d.keep_stages = int(bool(keep_stages))
     return d
 
 

@@ -80,6 +80,7 @@ bool valid_desc(const wb_desc* d, std::string* why) {
     if (!(d->eps[k] >= 0.0) || !(d->eps[k] < 0.5)) { *why = "eps_k must be in [0, 0.5)"; return false; }
   if (!(d->sweby_beta >= 1.0) || d->sweby_beta > 2.0) { *why = "sweby_beta must be in [1, 2]"; return false; }
   if (d->batch_patches < 0) { *why = "batch_patches must be >= 0"; return false; }
+  if (d->keep_stages != 0 && d->keep_stages != 1) { *why = "keep_stages must be 0 or 1"; return false; }
   {
     // padded zones of all patches (sizes beyond any device are refused before
     // a byte count could overflow)
@@ -121,11 +122,36 @@ WbGeo make_geo(const wb_desc* d) {
   return g;
 }
 
-const int kWorkArrays = 3 * 7 + 3 * 7 + 3 + 3 + 3 + 3 * 8 + 3 + 3;  // 81
+// workspace arrays per padded zone and patch slot: predictor fluxes (3 x 7),
+// reference EMF, corner EMFs, b^{n+1/2} (3 each), q^{n+1/2} (3 x 8), and with
+// keep_stages the corrector fluxes, half-step EMF and corrector corner EMFs in
+// arrays of their own (3 x 7 + 3 + 3) instead of their predictor counterparts'
+int work_arrays(const wb_desc* d) { return 3 * 7 + 3 + 3 + 3 + 3 * 8 + (d->keep_stages ? 3 * 7 + 3 + 3 : 0); }
 
 // blocks of the conserved-totals reduction (a fixed count: the summation
 // order, and so the result, do not depend on the device)
 constexpr int kTotalsBlocks = 256;
+
+// Point a grid's intermediates into the workspace w (slab doubles per array).
+// Without keep, the corrector fluxes, the half-step reference EMF and the
+// corrector corner EMFs take the arrays of the predictor fluxes, the reference
+// EMF and the predictor corner EMFs: each is written (Steps 6, 8, 9) after the
+// last stage that reads its counterpart (Steps 7, 3, 4).
+void carve_work(wb_grid* g, double* w, size_t slab, bool keep) {
+  size_t k = 0;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c) g->Fp[dd][c] = (c == F_BX + dd) ? nullptr : w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd) g->Eref[dd] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd) g->Eedge[dd] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd) g->bh[dd] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c) g->qh[dd][c] = w + slab * k++;
+  for (int dd = 0; dd < 3; ++dd)
+    for (int c = 0; c < 8; ++c)
+      g->Fc[dd][c] = !keep ? g->Fp[dd][c] : ((c == F_BX + dd) ? nullptr : w + slab * k++);
+  for (int dd = 0; dd < 3; ++dd) g->Erefh[dd] = keep ? w + slab * k++ : g->Eref[dd];
+  for (int dd = 0; dd < 3; ++dd) g->Eedgeh[dd] = keep ? w + slab * k++ : g->Eedge[dd];
+}
 
 Layout layout(const wb_desc* d) {
   Layout L;
@@ -136,7 +162,7 @@ Layout layout(const wb_desc* d) {
   if (S > L.npatch) S = L.npatch;
   L.S = (int)S;
   L.state = align_up(sizeof(double) * (size_t)L.V * L.npatch * 11);
-  L.work = align_up(sizeof(double) * (size_t)L.V * S * kWorkArrays);
+  L.work = align_up(sizeof(double) * (size_t)L.V * S * work_arrays(d));
   size_t gmax = (size_t)(d->n[0] + 1) * (d->n[1] + 1) * (d->n[2] + 1);
   L.staging = align_up(sizeof(double) * gmax);
   // device scalars, 64 reduction words, the 8 totals and the totals' partials
@@ -500,17 +526,7 @@ int wb_grid_create(const wb_desc* d, void* dev_mem, size_t bytes, void* stream, 
   double* w = reinterpret_cast<double*>(g->mem + L.state);
   size_t slab = V * (size_t)L.S;
   size_t k = 0;
-  for (int dd = 0; dd < 3; ++dd)
-    for (int c = 0; c < 8; ++c) g->Fp[dd][c] = (c == F_BX + dd) ? nullptr : w + slab * k++;
-  for (int dd = 0; dd < 3; ++dd)
-    for (int c = 0; c < 8; ++c) g->Fc[dd][c] = (c == F_BX + dd) ? nullptr : w + slab * k++;
-  for (int dd = 0; dd < 3; ++dd) g->Eref[dd] = w + slab * k++;
-  for (int dd = 0; dd < 3; ++dd) g->Eedge[dd] = w + slab * k++;
-  for (int dd = 0; dd < 3; ++dd) g->bh[dd] = w + slab * k++;
-  for (int dd = 0; dd < 3; ++dd)
-    for (int c = 0; c < 8; ++c) g->qh[dd][c] = w + slab * k++;
-  for (int dd = 0; dd < 3; ++dd) g->Erefh[dd] = w + slab * k++;
-  for (int dd = 0; dd < 3; ++dd) g->Eedgeh[dd] = w + slab * k++;
+  carve_work(g, w, slab, d->keep_stages != 0);
   g->staging = reinterpret_cast<double*>(g->mem + L.state + L.work);
   g->scal = reinterpret_cast<WbScalars*>(g->mem + L.state + L.work + L.staging);
   g->red = reinterpret_cast<unsigned long long*>(g->scal + 1);
@@ -727,6 +743,9 @@ int wb_debug_stage(wb_grid* g, int which, double* out, long long cap, long long*
   const int* n = g->geo.n;
   std::vector<const double*> arrays;
   WbBox bx = box(0, n[0] - 1, 0, n[1] - 1, 0, n[2] - 1);
+  if (which >= 0 && which < 3 && !g->d.keep_stages)
+    return fail(g, WB_ERR_INVALID, "predictor fluxes are overwritten by the corrector; "
+                                   "create the grid with keep_stages = 1");
   if (which >= 0 && which < 6) {
     int d = which % 3;
     for (int c = 0; c < 8; ++c) arrays.push_back(which < 3 ? g->Fp[d][c] : g->Fc[d][c]);
@@ -843,12 +862,13 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
     return noalloc_fail(WB_ERR_INVALID, "null state pointer");
   wb_desc one = *d;
   one.batch_patches = 0;
+  one.keep_stages = 0;
   Layout L = layout(&one);
   if (L.total > kNoallocBytes) {
     char buf[200];
     std::snprintf(buf, sizeof(buf),
                   "box %dx%dx%d needs %zu bytes of scratch; the static limit is %zu bytes "
-                  "(24 MiB, cubes up to 22^3 zones)",
+                  "(24 MiB, cubes up to 25^3 zones)",
                   d->n[0], d->n[1], d->n[2], L.total, kNoallocBytes);
     return noalloc_fail(WB_ERR_INVALID, buf);
   }
@@ -890,18 +910,7 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
   for (int c = 0; c < 8; ++c) g.q[c] = st + (size_t)c * V;
   for (int c = 0; c < 3; ++c) g.b[c] = st + (size_t)(8 + c) * V;
   double* w = reinterpret_cast<double*>(g.mem + L.state);
-  size_t k = 0;
-  for (int dd = 0; dd < 3; ++dd)
-    for (int c = 0; c < 8; ++c) g.Fp[dd][c] = (c == F_BX + dd) ? nullptr : w + V * k++;
-  for (int dd = 0; dd < 3; ++dd)
-    for (int c = 0; c < 8; ++c) g.Fc[dd][c] = (c == F_BX + dd) ? nullptr : w + V * k++;
-  for (int dd = 0; dd < 3; ++dd) g.Eref[dd] = w + V * k++;
-  for (int dd = 0; dd < 3; ++dd) g.Eedge[dd] = w + V * k++;
-  for (int dd = 0; dd < 3; ++dd) g.bh[dd] = w + V * k++;
-  for (int dd = 0; dd < 3; ++dd)
-    for (int c = 0; c < 8; ++c) g.qh[dd][c] = w + V * k++;
-  for (int dd = 0; dd < 3; ++dd) g.Erefh[dd] = w + V * k++;
-  for (int dd = 0; dd < 3; ++dd) g.Eedgeh[dd] = w + V * k++;
+  carve_work(&g, w, V, false);
   g.staging = reinterpret_cast<double*>(g.mem + L.state + L.work);
   g.scal = reinterpret_cast<WbScalars*>(g.mem + L.state + L.work + L.staging);
   g.red = reinterpret_cast<unsigned long long*>(g.scal + 1);

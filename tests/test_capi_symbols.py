@@ -46,6 +46,27 @@ def test_descriptor_validation_without_gpu():
         raise AssertionError("uneven patches accepted")
 
 
+def test_workspace_size_with_and_without_kept_stages():
+    """Workspace bytes follow the documented count of intermediate arrays:
+    54 doubles per padded zone when the corrector stages reuse the predictor
+    arrays, 81 with keep_stages (state: 11)."""
+    from paper_1701_07452_gb300 import binding
+    n = (40, 40, 40)
+    V = 50 ** 3
+    lean = binding.grid_bytes(binding.make_desc(n))
+    keep = binding.grid_bytes(binding.make_desc(n, keep_stages=True))
+    assert abs((keep - lean) - (81 - 54) * 8 * V) < 4096   # the work region is rounded up
+    assert (11 + 54) * 8 * V <= lean < (11 + 54) * 8 * V + (1 << 22)
+    d = binding.make_desc(n)
+    d.keep_stages = 2
+    try:
+        binding.grid_bytes(d)
+    except binding.WombatError as e:
+        assert e.code == binding.WB_ERR_INVALID
+    else:
+        raise AssertionError("keep_stages = 2 accepted")
+
+
 def test_descriptor_edge_cases_rejected_without_gpu():
     """Empty, ragged and out-of-range descriptors fail with WB_ERR_INVALID
     before any device work (no GPU needed)."""

@@ -23,7 +23,8 @@ def wb():
 def make_pair(wb, oracle_mod, st, n, patches=(1, 1, 1), **kw):
     g = wb.Grid(n, patches=patches, length=st["length"], **kw)
     g.load_state(st)
-    o = oracle_mod.Grid(n, st["length"], **{k: v for k, v in kw.items() if k != "batch_patches"})
+    o = oracle_mod.Grid(n, st["length"], **{k: v for k, v in kw.items()
+                                            if k not in ("batch_patches", "keep_stages")})
     o.load_state(st)
     return g, o
 
@@ -40,7 +41,7 @@ def test_stage_parity_one_step(wb, oracle_mod):
     from paper_1701_07452_gb300.initial_conditions import random_box
     st = random_box((13, 11, 12), seed=5)
     n = (13, 11, 12)
-    g, o = make_pair(wb, oracle_mod, st, n)
+    g, o = make_pair(wb, oracle_mod, st, n, keep_stages=True)
     dt = o.dt()
     g.advance(1)
     assert o.step(dt) == 0
@@ -298,3 +299,23 @@ def test_checkpoint_resume_bit_exact(wb):
     c.advance(5)
     for x, y in zip(a.read(), c.read()):
         assert np.array_equal(x, y)
+
+
+def test_reused_workspace_arrays(wb):
+    """The default workspace reuses the predictor arrays for the corrector
+    stages (54 arrays a zone instead of 81); the step is the same bit for bit,
+    and the overwritten predictor fluxes are not offered for dumping."""
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box
+    n = (20, 18, 16)
+    st = turbulence_box(n, seed=13)
+    keep = wb.Grid(n, length=st["length"], keep_stages=True)
+    lean = wb.Grid(n, length=st["length"])
+    assert lean.nbytes < keep.nbytes
+    for g in (keep, lean):
+        g.load_state(st)
+        g.advance(3)
+    for a, b in zip(keep.read(), lean.read()):
+        assert np.array_equal(a, b)
+    with pytest.raises(wb.WombatError):
+        lean.stage(0)
+    assert np.array_equal(keep.stage(4), lean.stage(4))
