@@ -351,7 +351,7 @@ def run_mode(args):
     if args.mode in ("patches", "big"):
         n, p = (512, 8) if args.mode == "patches" else (768, 12)
         st = turbulence_box_device(n, SEED, dev)
-        def run(patches, batch):
+        def run(patches, batch, read=True):
             g = wb.Grid((n, n, n), patches=(patches,) * 3, length=st["length"], batch_patches=batch)
             g.load(st["W"], st["bx"], st["by"], st["bz"], on_device=True, primitive=True)
             g.advance(1)
@@ -363,7 +363,7 @@ def run_mode(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
-            out = g.read(on_device=True)
+            out = g.read(on_device=True) if read else None
             assert g.counters()["unphysical"] == 0
             del g
             torch.cuda.empty_cache()
@@ -373,12 +373,26 @@ def run_mode(args):
             ms_p, out_p = run(p, 0)
             how = "all patches resident, neighbour images between stages"
         else:
-            ms_p, out_p = run(p, 152)
+            ms_p, out_p = run(p, 152, read=False)
             how = "152 patches per pipeline pass, ghost rings recomputed"
         line = {"metric": METRIC, "mode": args.mode, "value": n ** 3 * args.steps / (ms_p * 1e-3),
                 "unit": UNIT, "higher_is_better": True, "steps": args.steps, "dtype": "f64",
                 "ms_per_step": ms_p / args.steps, "data": "synthetic",
                 "config": {"workload": f"{n}^3 periodic turbulence box in {p}^3 patches of {n // p}^3, " + how}}
+        if args.mode == "big":
+            # the same box as one resident grid with periodic images, when the
+            # device holds it (about 250 GB at 768^3 besides the initial data)
+            del out_p
+            torch.cuda.empty_cache()
+            need = wb.grid_bytes(wb.make_desc((n, n, n), length=st["length"])) + (4 << 30)
+            free = torch.cuda.mem_get_info()[0]
+            if free > need:
+                ms_s, _ = run(1, 0, read=False)
+                line["single_grid_value"] = n ** 3 * args.steps / (ms_s * 1e-3)
+                line["single_grid_config"] = f"one {n}^3 grid, all resident, periodic images between stages"
+            else:
+                line["single_grid_value"] = None
+                line["single_grid_config"] = f"not run: {need / 2**30:.0f} GiB needed, {free / 2**30:.0f} GiB free"
         if args.mode == "patches":
             ms_q, out_q = run(p, 152)
             ms_s, out_s = run(1, 0)
