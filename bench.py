@@ -233,14 +233,19 @@ def run_mode(args):
         states = [random_box(int(e), seed=4000 + b) for b, e in enumerate(edges)]
         boxes = [{"n": (int(e),) * 3, "length": st["length"]} for e, st in zip(edges, states)]
         steps = args.steps
-        tune = wb.Batch(boxes)
-        for i, st in enumerate(states):
-            tune.load_state(i, st)
-        tune.set_steps(-1, 1000)
-        tune.autotune(trial_steps=1)
-        cfg = tune.get_config()
-        del tune
+        if args.form == "auto":
+            tune = wb.Batch(boxes)
+            for i, st in enumerate(states):
+                tune.load_state(i, st)
+            tune.set_steps(-1, 1000)
+            tune.autotune(trial_steps=1)
+            cfg = tune.get_config()
+            del tune
         bt = wb.Batch(boxes)
+        if args.form != "auto":
+            # a given form with the default segment length and block count
+            bt.set_form(args.form)
+            cfg = bt.get_config()
         for i, st in enumerate(states):
             bt.load_state(i, st)
         bt.set_steps(-1, steps)
@@ -305,7 +310,7 @@ def run_mode(args):
                 "steps": steps, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"{args.nbox} periodic boxes, edges from {{16..128}} (seed 4), "
                                        f"random data seed 4000+b, {steps} steps each (solve = one box x "
-                                       f"{steps} steps)", "autotuned": cfg},
+                                       f"{steps} steps)", "autotuned" if args.form == "auto" else "given": cfg},
                 "other_form": {"form": other, "solves_per_s": args.nbox / t_other},
                 "batch_vs_grid_max_rel_err": worst,
                 "stage_ms_one_step": stage_ms}
@@ -421,6 +426,8 @@ def main():
                          "one at a time; serve: request stream; patches: 512^3 in 64^3 patches vs "
                          "the single grid; big: 768^3 in 12^3 patches")
     ap.add_argument("--nbox", type=int, default=64)
+    ap.add_argument("--form", default="auto", choices=["auto", "persistent", "staged"],
+                    help="batch mode: the autotuned form, or a given one without autotuning")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--steps-scale", type=float, default=0.1)
     args = ap.parse_args()
