@@ -52,6 +52,14 @@ FLOPS_PER_FACE = 513.0
 # (profiles/k_sweep_256cube_dram.md); the algorithmic figure is 128 B per face.
 SWEEP_DRAM_BYTES_256 = 3.681e9
 SWEEP_BYTES_PER_FACE = 128.0
+# FP64 flops of the other stages of a step per zone: 459 from the ncu counters
+# of the corner EMFs, CT, transverse states, half-step EMF and update kernels
+# on the 96^3 box (profiles/stages_96cube_ncu_full.md), plus 18 for the
+# reference EMF (its source: one reciprocal, three products, three pairs).
+STAGE_FLOPS_PER_ZONE = 477.0
+# algorithmic state bytes per cell-update: 5 conserved fields and 3 face fields
+# read and written once (the step's HBM roofline)
+STEP_BYTES_PER_CELL = 128.0
 # FP64 issue rate of one GB300 SM: 2 DFMA per clock (measured with the DFMA
 # probe: 1196 GFLOP/s at 1995 MHz on 152 SMs), i.e. 4 flops per clock per SM.
 FP64_FLOPS_PER_CLK_PER_SM = 4.0
@@ -81,6 +89,26 @@ def l2_note(n):
     state = 11 * 8 * (n + 10) ** 3
     side = ">" if state > 129e6 else "<"
     return f"state {state / 1e9:.2f} GB {side} L2 (129 MB), no flush"
+
+
+def step_roofline(value, fp64_peak_tflops):
+    """The whole step against the slower of its two ceilings: FP64 flops per
+    cell-update at the FP64 peak, and its state bytes at the measured HBM
+    copy bandwidth."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = float(json.load(f)["hbm_gbs"])
+        src = "MEASURED_PEAKS.json (measured copy)"
+    except (OSError, KeyError, ValueError):
+        hbm, src = 6800.0, "fallback 6.8 TB/s"
+    flops = 6 * FLOPS_PER_FACE + STAGE_FLOPS_PER_ZONE
+    fp64_rate = fp64_peak_tflops * 1e12 / flops
+    hbm_rate = hbm * 1e9 / STEP_BYTES_PER_CELL
+    bound = min(fp64_rate, hbm_rate)
+    return {"bound": "fp64" if fp64_rate <= hbm_rate else "hbm", "unit": UNIT,
+            "fp64_rate": fp64_rate, "hbm_rate": hbm_rate, "frac": value / bound,
+            "flops_per_cell_update": flops, "bytes_per_cell_update": STEP_BYTES_PER_CELL,
+            "hbm_gbs": hbm, "hbm_source": src, "hbm_frac": value * STEP_BYTES_PER_CELL / (hbm * 1e9)}
 
 
 def sweep_faces_per_step(n):
@@ -533,6 +561,7 @@ def main():
                                         "DFMA probe in this process: %.3f TFLOP/s" % (fp64_peak / 1e12),
                          "sweep_ms_per_launch": per_launch_ms,
                          "sweep_share_of_step": sweep_ms / ms},
+            "step_roofline": step_roofline(value, peak),
             "cpu_baseline": cpu,
             "clocks": clk_summary,
             "gpu_launches": launches_per_step * args.steps,
