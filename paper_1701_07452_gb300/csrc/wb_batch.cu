@@ -13,6 +13,11 @@
 // block returns, so a stalled launch ends with WB_ERR_TIMEOUT instead of a
 // hang.  The stage bodies are the same device functions the per-stage kernels
 // of a grid use (wb_units.cuh).
+//
+// The staged form runs the same stages as one ordinary launch each (the
+// sweeps in k_batch limited to one stage, the zone stages in kernels compiled
+// per stage class with their own occupancy), all captured in one CUDA graph;
+// both forms give the same bits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
