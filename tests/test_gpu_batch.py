@@ -138,3 +138,31 @@ def test_staged_stage_timer(wb):
     assert ms["pred_sweeps"] > 0 and ms["corr_sweeps"] > 0 and ms["update"] > 0
     assert sum(ms.values()) <= wall * 1e3
     assert all(bt.counters(i)["steps"] == 3 for i in range(3))
+
+
+def test_mixed_boundaries_both_forms(wb):
+    """Periodic boxes (interior-only stages with images) and outflow boxes
+    (ghost-ring regions, zero-gradient ghost fill) in one batch: each box
+    matches its single grid, and the staged form gives the persistent form's
+    bits."""
+    sizes = [(12, 10, 9), (10, 12, 8), (8, 8, 8)]
+    bcs = [(0, 0, 0), (1, 1, 1), (0, 1, 0)]
+    boxes, states = boxes_and_states(sizes, seed0=500)
+    for b, bc in zip(boxes, bcs):
+        b["bc"] = bc
+    runs = []
+    for form in ("persistent", "staged"):
+        bt = wb.Batch(boxes)
+        bt.set_form(form)
+        for i, st in enumerate(states):
+            bt.load_state(i, st)
+        bt.set_steps(-1, 4)
+        bt.advance(4)
+        runs.append([bt.read(i) for i in range(len(boxes))])
+    for i, (b, st) in enumerate(zip(boxes, states)):
+        g = wb.Grid(b["n"], length=b["length"], bc=b["bc"])
+        g.load_state(st)
+        g.advance(4)
+        assert state_err(runs[0][i], g.read()) < 1e-11, i
+        for a, c in zip(runs[0][i], runs[1][i]):
+            assert np.array_equal(a, c), i

@@ -93,6 +93,14 @@ def test_expansion_box_batch_matches_grid(wb):
         bt.load_state(i, s)
     bt.set_steps(-1, 12)
     bt.advance(12)
+    # the staged form (general kernel variant with the protection test) gives
+    # the persistent form's bits and HLL count
+    bs = wb.Batch(boxes, **PROT)
+    bs.set_form("staged")
+    for i, s in enumerate(st):
+        bs.load_state(i, s)
+    bs.set_steps(-1, 12)
+    bs.advance(12)
     for i, s in enumerate(st):
         g = wb.Grid(boxes[i]["n"], length=boxes[i]["length"], **PROT)
         g.load_state(s)
@@ -100,6 +108,9 @@ def test_expansion_box_batch_matches_grid(wb):
         assert state_err(bt.read(i), g.read()) < 1e-11, i
         cb, cg = bt.counters(i), g.counters()
         assert cb["hll_faces"] == cg["hll_faces"] > 0 and cb["unphysical"] == 0
+        for a, b in zip(bt.read(i), bs.read(i)):
+            assert np.array_equal(a, b), i
+        assert bs.counters(i)["hll_faces"] == cb["hll_faces"]
 
 
 def test_unreached_floors_change_nothing(wb):
