@@ -68,6 +68,7 @@ def lib():
             L.or_stage.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ctypes.c_longlong]
             L.or_face_eigen.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
             L.or_set_protection.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+            L.or_set_source_scale.argtypes = [ctypes.c_void_p, ctypes.c_double]
             L.or_flux_pencil.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, dp, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, dp]
@@ -204,6 +205,11 @@ class Grid:
         """Protection floors of App. A (faces next to a zone below them use HLL)."""
         if lib().or_set_protection(self._h, float(prot_rho), float(prot_p)):
             raise ValueError("oracle: invalid protection floors")
+
+    def set_source_scale(self, s: float):
+        """Test ablation: multiply the div B source of Steps 5 and 7 by s."""
+        if lib().or_set_source_scale(self._h, float(s)):
+            raise ValueError("oracle: invalid source scale")
 
     def stage(self, which: int):
         nx, ny, nz = self.n

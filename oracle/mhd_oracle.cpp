@@ -19,6 +19,10 @@
 //   hll_flux, protection      App. A, the protection floor and the HLL flux
 //                             (Eqs. for u-bar of the HLL scheme, b+ and b-)
 // Readings where the paper is silent are tagged R1..R21 as in the design notes.
+//
+// Parity unpinned: the sign and size of the div B source term of Steps 5 and 7
+// (reading R13, after GS08, which is not available).  Tests pin only that it
+// vanishes for data varying along one axis and acts on oblique data.
 
 #include "mhd_oracle.h"
 
@@ -39,6 +43,7 @@ const double NaN = std::numeric_limits<double>::quiet_NaN();
 struct Params {
   double gamma, cfl, eps[7], sweby, rho_floor, p_floor;
   double prot_rho = 0.0, prot_p = 0.0;  // protection floors (App. A)
+  double source_scale = 1.0;            // factor on the div B source (test ablation only)
 };
 
 // 3D array over the padded box [-NG, n+NG) per dimension, x fastest.
@@ -763,7 +768,7 @@ void transverse_state(or_grid* g, int d, double dt, const Range& r) {
           if (c == BX + d) continue;
           double div = (g->Fp[t1][c](p1[0], p1[1], p1[2]) - g->Fp[t1][c](p[0], p[1], p[2])) / g->dxv[t1] +
                        (g->Fp[t2][c](p2[0], p2[1], p2[2]) - g->Fp[t2][c](p[0], p[1], p[2])) / g->dxv[t2];
-          out[c](i, j, k) = g->q[c](i, j, k) - hdt * div + hdt * S[c];
+          out[c](i, j, k) = g->q[c](i, j, k) - hdt * div + hdt * (g->P.source_scale * S[c]);
         }
         out[BX + d](i, j, k) = 0.5 * (g->bh[d](i, j, k) + g->bh[d](pd[0], pd[1], pd[2]));
       }
@@ -1109,6 +1114,12 @@ int or_counters(const or_grid* g, long long out[3]) {
   out[0] = g->floor_hits;
   out[1] = g->unphysical;
   out[2] = g->hll_faces;
+  return 0;
+}
+
+int or_set_source_scale(or_grid* g, double s) {
+  if (!g || !std::isfinite(s)) return 1;
+  g->P.source_scale = s;
   return 0;
 }
 

@@ -55,6 +55,9 @@ double or_divb_max(const or_grid* g);
 int or_counters(const or_grid* g, long long out[3]);
 /* Protection floors (>= 0; 0 and 0, the default, turn protection off). */
 int or_set_protection(or_grid* g, double prot_rho, double prot_p);
+/* Test ablation of the div B source term of Steps 5 and 7: S is multiplied by
+ * s (1 = the scheme; 0 drops the term, -1 flips its sign). */
+int or_set_source_scale(or_grid* g, double s);
 int or_set_threads(int n);
 
 /* Stage dump: copy an intermediate of the last step, on interior cells

@@ -235,3 +235,34 @@ def test_lagged_dt_sequence(oracle_mod):
     for n in range(2, 5):
         assert used[n] == cfl_dts[n - 1]
     assert len(set(cfl_dts)) == 5   # the state's rate changes, so the lag matters
+
+
+def test_div_b_source_is_multi_dimensional_only(oracle_mod):
+    """The div B source of the transverse states (Steps 5, 7; reading R13)
+    is proportional to the face-field differences along the state's own axis:
+    it must vanish exactly for data varying along x only (every face-field
+    difference is zero there), and it must act on an oblique wave, where the
+    differences are not.  A source term that was dropped, or that carried a
+    part not proportional to the differences, fails one of the two.  (Its sign
+    and size are a reading of GS08, which is not available: parity unpinned
+    beyond this.)"""
+    lam, U, bx, by, bz = lw.state_1d("alfven", 32)
+    runs = []
+    for s in (1.0, 0.0):
+        g = oracle_mod.Grid((32, 1, 1), (1.0, 1.0, 1.0))
+        g.load(U, bx, by, bz)
+        g.set_source_scale(s)
+        g.advance(5)
+        runs.append(g.read())
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+    lam, U, bx, by, bz = lw.state_oblique("alfven", 8)
+    runs = []
+    for s in (1.0, 0.0):
+        g = oracle_mod.Grid((16, 8, 8), (3.0, 1.5, 1.5))
+        g.load(U, bx, by, bz)
+        g.set_source_scale(s)
+        g.advance(3)
+        runs.append(g.read())
+    diff = max(np.abs(a - b).max() for a, b in zip(*runs))
+    assert diff > 1e-10
