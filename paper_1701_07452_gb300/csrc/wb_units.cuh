@@ -109,19 +109,31 @@ struct RecT {
 };
 using Rec = RecT<kBlock>;
 
+// The flux arithmetic below is written with explicit rounding: every product
+// that feeds a sum is one fused multiply-add (__fma_rn), every other operation
+// is rounded on its own (__dmul_rn, __dadd_rn, __dsub_rn), and nothing is left
+// to the compiler's contraction.  An interface then gives the same bits in
+// every kernel this code is inlined into (the grid sweeps, both forms of the
+// batch path), whatever else the kernel holds.  Shorthands:
+#define WB_FMA __fma_rn
+#define WB_MUL __dmul_rn
+#define WB_ADD __dadd_rn
+#define WB_SUB __dsub_rn
+
 // Q_k(nu) - nu^2 for the g-tilde of App. A.  Waves in the compile-time mask
 // EZ have eps_k = 0, where Q is |nu|; the branch test runs on the integer pipe.
 template <int EZ>
 __device__ __forceinline__ double Qk_m_nu2(double nu, int k, const WbPhys& P) {
-  const double n2 = nu * nu;
-  if (EZ & (1 << k)) return fabs(nu) - n2;
-  return (wb_abs_less(nu, P.two_eps[k]) ? fma(n2, P.inv4eps[k], P.eps[k]) : fabs(nu)) - n2;
+  if (EZ & (1 << k)) return WB_FMA(-nu, nu, fabs(nu));
+  const double q = wb_abs_less(nu, P.two_eps[k]) ? WB_FMA(WB_MUL(nu, nu), P.inv4eps[k], P.eps[k]) : fabs(nu);
+  return WB_FMA(-nu, nu, q);
 }
 
 // Gas pressure of a zone from its sweep-frame fields (Sec. 3, Eq. totenergy)
 __device__ __forceinline__ double zone_pressure(const Cell& c, const WbPhys& P) {
-  return P.gm1 * (c.eref - 0.5 * (c.mn * c.vn + c.mt1 * c.vt1 + c.mt2 * c.vt2) -
-                  0.5 * (c.bt1 * c.bt1 + c.bt2 * c.bt2));
+  const double mv = WB_FMA(c.mt2, c.vt2, WB_FMA(c.mt1, c.vt1, WB_MUL(c.mn, c.vn)));
+  const double bb = WB_FMA(c.bt2, c.bt2, WB_MUL(c.bt1, c.bt1));
+  return WB_MUL(P.gm1, WB_SUB(WB_SUB(c.eref, wb_half(mv)), wb_half(bb)));
 }
 
 // Protection floor of App. A: true when a zone state, or an intermediate
@@ -134,24 +146,25 @@ __device__ __forceinline__ bool protection_hit(const Cell& L, const Cell& R, dou
                                                const WbPhys& P) {
   const double pL = zone_pressure(L, P), pR = zone_pressure(R, P);
   if (L.rho < P.prot_rho || pL < P.prot_p || R.rho < P.prot_rho || pR < P.prot_p) return true;
-  const double r1 = L.rho + al[0] * (rho * af), p1 = pL + al[0] * (ra2 * af);
+  const double r1 = WB_FMA(al[0], WB_MUL(rho, af), L.rho), p1 = WB_FMA(al[0], WB_MUL(ra2, af), pL);
   if (r1 < P.prot_rho || p1 < P.prot_p) return true;
-  const double r3 = r1 + al[2] * (rho * as), p3 = p1 + al[2] * (ra2 * as);
+  const double r3 = WB_FMA(al[2], WB_MUL(rho, as), r1), p3 = WB_FMA(al[2], WB_MUL(ra2, as), p1);
   if (r3 < P.prot_rho || p3 < P.prot_p) return true;
-  const double r4 = r3 + al[3];
+  const double r4 = WB_ADD(r3, al[3]);
   if (r4 < P.prot_rho) return true;
-  const double r5 = r4 + al[4] * (rho * as), p5 = p3 + al[4] * (ra2 * as);
+  const double r5 = WB_FMA(al[4], WB_MUL(rho, as), r4), p5 = WB_FMA(al[4], WB_MUL(ra2, as), p3);
   return r5 < P.prot_rho || p5 < P.prot_p;
 }
 
 // Fast speed of one zone along the sweep axis with its own zone field (Sec. 3)
 __device__ __forceinline__ double zone_fast_speed(const Cell& c, double bn, const WbPhys& P) {
-  const double a2 = P.gamma * zone_pressure(c, P) / c.rho;
-  const double b2 = (bn * bn + c.bt1 * c.bt1 + c.bt2 * c.bt2) / c.rho;
-  const double s = a2 + b2;
-  double disc = s * s - 4.0 * a2 * bn * bn / c.rho;
+  const double a2 = WB_MUL(P.gamma, zone_pressure(c, P)) / c.rho;
+  const double bn2 = WB_MUL(bn, bn);
+  const double b2 = WB_FMA(c.bt2, c.bt2, WB_FMA(c.bt1, c.bt1, bn2)) / c.rho;
+  const double s = WB_ADD(a2, b2);
+  double disc = WB_FMA(s, s, -(WB_MUL(WB_MUL(4.0, a2), bn2) / c.rho));
   if (disc < 0.0) disc = 0.0;
-  return sqrt(0.5 * (s + sqrt(disc)));
+  return sqrt(wb_half(WB_ADD(s, sqrt(disc))));
 }
 
 // Marker of a face record that holds a finished HLL flux (a Roe density is > 0)
@@ -167,25 +180,26 @@ template <class Rc>
 __device__ __forceinline__ void hll_face(const Cell& L, const Cell& R, double bnL, double bnR, bool roe,
                                       const WbPhys& P, const Rc& f) {
   const double cfL = zone_fast_speed(L, bnL, P), cfR = zone_fast_speed(R, bnR, P);
-  double bp = fmax(R.vn + cfR, 0.0);
-  double bm = fmin(L.vn - cfL, 0.0);
+  double bp = fmax(WB_ADD(R.vn, cfR), 0.0);
+  double bm = fmin(WB_SUB(L.vn, cfL), 0.0);
   if (roe) {
-    bp = fmax(bp, f[R_VN] + f[R_CF]);
-    bm = fmin(bm, f[R_VN] - f[R_CF]);
+    bp = fmax(bp, WB_ADD(f[R_VN], f[R_CF]));
+    bm = fmin(bm, WB_SUB(f[R_VN], f[R_CF]));
   }
-  if (!(bp - bm > 0.0)) {
-    const double sp = fmax(fabs(L.vn) + cfL, fabs(R.vn) + cfR);
+  if (!(WB_SUB(bp, bm) > 0.0)) {
+    const double sp = fmax(WB_ADD(fabs(L.vn), cfL), WB_ADD(fabs(R.vn), cfR));
     bp = sp;
     bm = -sp;
   }
-  const double dq[7] = {R.rho - L.rho, R.mn - L.mn, R.mt1 - L.mt1, R.mt2 - L.mt2,
-                        R.bt1 - L.bt1, R.bt2 - L.bt2, R.eref - L.eref};
-  const double inv = 1.0 / (bp - bm);
+  const double dq[7] = {WB_SUB(R.rho, L.rho), WB_SUB(R.mn, L.mn), WB_SUB(R.mt1, L.mt1), WB_SUB(R.mt2, L.mt2),
+                        WB_SUB(R.bt1, L.bt1), WB_SUB(R.bt2, L.bt2), WB_SUB(R.eref, L.eref)};
+  const double inv = 1.0 / WB_SUB(bp, bm);
+  const double bpm = WB_MUL(bp, bm);
 #pragma unroll
   for (int m = 0; m < 7; ++m) {
     // the zone fluxes hold F/2
-    const double FL = 2.0 * L.F[m], FR = 2.0 * R.F[m];
-    f[R_FAVG + m] = (bp * FL - bm * FR + bp * bm * dq[m]) * inv;
+    const double FL = WB_MUL(2.0, L.F[m]), FR = WB_MUL(2.0, R.F[m]);
+    f[R_FAVG + m] = WB_MUL(WB_FMA(bpm, dq[m], WB_FMA(bp, FL, -WB_MUL(bm, FR))), inv);
   }
   f[R_RHO] = kHllFace;
 }
@@ -198,125 +212,130 @@ __device__ __forceinline__ void hll_face(const Cell& L, const Cell& R, double bn
 template <int EZ, bool PROT, class Rc>
 __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double b, double dtdx,
                                            const WbPhys& P, const Rc& f, double gt[7]) {
-  const double iD = wb_rcp(L.sr + R.sr);
-  const double wL = L.sr * iD, wR = R.sr * iD;
-  const double rho = L.sr * R.sr;
-  const double irho = L.isr * R.isr;
-  const double vn = wL * L.vn + wR * R.vn;
-  const double vt1 = wL * L.vt1 + wR * R.vt1;
-  const double vt2 = wL * L.vt2 + wR * R.vt2;
-  const double bt1 = wR * L.bt1 + wL * R.bt1;
-  const double bt2 = wR * L.bt2 + wL * R.bt2;
-  const double b2 = b * b;
+  const double iD = wb_rcp(WB_ADD(L.sr, R.sr));
+  const double wL = WB_MUL(L.sr, iD), wR = WB_MUL(R.sr, iD);
+  const double rho = WB_MUL(L.sr, R.sr);
+  const double irho = WB_MUL(L.isr, R.isr);
+  const double vn = WB_FMA(wL, L.vn, WB_MUL(wR, R.vn));
+  const double vt1 = WB_FMA(wL, L.vt1, WB_MUL(wR, R.vt1));
+  const double vt2 = WB_FMA(wL, L.vt2, WB_MUL(wR, R.vt2));
+  const double bt1 = WB_FMA(wR, L.bt1, WB_MUL(wL, R.bt1));
+  const double bt2 = WB_FMA(wR, L.bt2, WB_MUL(wL, R.bt2));
+  const double b2 = WB_MUL(b, b);
   // H = wL (h_L + b^2)/rho_L + wR (h_R + b^2)/rho_R, with wL/rho_L + wR/rho_R = 1/rho_
-  const double H = fma(b2, irho, wL * L.hr + wR * R.hr);
-  const double dbt1 = R.bt1 - L.bt1, dbt2 = R.bt2 - L.bt2;
-  const double gX = P.hgm2 * ((dbt1 * dbt1 + dbt2 * dbt2) * (iD * iD));  // (gamma-2) X
-  const double hv2 = wb_half(vn * vn + vt1 * vt1 + vt2 * vt2);
-  const double bt2s = bt1 * bt1 + bt2 * bt2;
-  const double a2 = P.gm1 * (H - hv2 - (b2 + bt2s) * irho) - gX;
+  const double H = WB_FMA(b2, irho, WB_FMA(wL, L.hr, WB_MUL(wR, R.hr)));
+  const double dbt1 = WB_SUB(R.bt1, L.bt1), dbt2 = WB_SUB(R.bt2, L.bt2);
+  const double gX = WB_MUL(P.hgm2, WB_MUL(WB_FMA(dbt1, dbt1, WB_MUL(dbt2, dbt2)), WB_MUL(iD, iD)));  // (gamma-2) X
+  const double hv2 = wb_half(WB_FMA(vn, vn, WB_FMA(vt1, vt1, WB_MUL(vt2, vt2))));
+  const double bt2s = WB_FMA(bt1, bt1, WB_MUL(bt2, bt2));
+  const double a2 = WB_FMA(P.gm1, WB_FMA(-WB_ADD(b2, bt2s), irho, WB_SUB(H, hv2)), -gX);
   if (!wb_normal_pos(a2)) return 2;
   const double isrho = wb_rsqrt(rho);
-  const double srho = rho * isrho;
-  const double ca2 = b2 * irho, ct2 = bt2s * irho;
-  const double dac = a2 - ca2;
-  const double disc = dac * dac + ct2 * (ct2 + 2.0 * (a2 + ca2));
-  const double sum = a2 + ca2 + ct2;
+  const double srho = WB_MUL(rho, isrho);
+  const double ca2 = WB_MUL(b2, irho), ct2 = WB_MUL(bt2s, irho);
+  const double dac = WB_SUB(a2, ca2);
+  const double disc = WB_FMA(dac, dac, WB_MUL(ct2, WB_FMA(2.0, WB_ADD(a2, ca2), ct2)));
+  const double sum = WB_ADD(WB_ADD(a2, ca2), ct2);
   double rsd = 0.0, sd = 0.0;
   if (wb_normal_pos(disc)) {  // a subnormal discriminant is degenerate (sd ~ 0)
     rsd = wb_rsqrt(disc);
-    sd = disc * rsd;
+    sd = WB_MUL(disc, rsd);
   }
-  const double cf2 = wb_half(sum + sd);
+  const double cf2 = wb_half(WB_ADD(sum, sd));
   const double icf = wb_rsqrt(cf2);
   const double ia = wb_rsqrt(a2);
-  const double a = a2 * ia;
-  const double ca = fabs(b) * isrho;
-  const double cf = cf2 * icf;
-  const double cs = a * ca * icf;  // c_f c_s = a c_a
+  const double a = WB_MUL(a2, ia);
+  const double ca = WB_MUL(fabs(b), isrho);
+  const double cf = WB_MUL(cf2, icf);
+  const double cs = WB_MUL(WB_MUL(a, ca), icf);  // c_f c_s = a c_a
   double af, as;
-  if (wb_le_nonneg(sd, 1e-12 * sum)) {
+  if (wb_le_nonneg(sd, WB_MUL(1e-12, sum))) {
     const bool fast = wb_le_nonneg(ca2, a2);
     af = fast ? 1.0 : 0.0;
     as = fast ? 0.0 : 1.0;
   } else {
     // cf^2 - a^2 and cf^2 - ca^2 without cancellation; at most one of the
     // two needs a quotient
-    const double t1 = ca2 + ct2 - a2;
-    const double t2 = a2 - ca2 + ct2;
+    const double t1 = WB_SUB(WB_ADD(ca2, ct2), a2);
+    const double t2 = WB_ADD(WB_SUB(a2, ca2), ct2);
     const bool n1 = wb_neg(t1), n2 = wb_neg(t2);
     double qd = 0.0;
     if (n1 || n2) {
-      const double num = n1 ? 2.0 * a2 * ct2 : 2.0 * ca2 * ct2;
-      const double den = n1 ? sd - t1 : sd - t2;
-      qd = num * wb_rcp(den);
+      const double num = n1 ? WB_MUL(WB_MUL(2.0, a2), ct2) : WB_MUL(WB_MUL(2.0, ca2), ct2);
+      const double den = n1 ? WB_SUB(sd, t1) : WB_SUB(sd, t2);
+      qd = WB_MUL(num, wb_rcp(den));
     }
-    const double cf2_a2 = n1 ? qd : wb_half(t1 + sd);
-    const double cf2_ca2 = n2 ? qd : wb_half(t2 + sd);
-    const double af2 = wb_clamp01(a2 * cf2_ca2 * (icf * icf) * rsd);
-    const double as2 = wb_clamp01(cf2_a2 * rsd);
+    const double cf2_a2 = n1 ? qd : wb_half(WB_ADD(t1, sd));
+    const double cf2_ca2 = n2 ? qd : wb_half(WB_ADD(t2, sd));
+    const double af2 = wb_clamp01(WB_MUL(WB_MUL(WB_MUL(a2, cf2_ca2), WB_MUL(icf, icf)), rsd));
+    const double as2 = wb_clamp01(WB_MUL(cf2_a2, rsd));
     // subnormal squares (from underflowing transverse fields) count as 0
-    af = wb_normal_pos(af2) ? af2 * wb_rsqrt(af2) : 0.0;
-    as = wb_normal_pos(as2) ? as2 * wb_rsqrt(as2) : 0.0;
+    af = wb_normal_pos(af2) ? WB_MUL(af2, wb_rsqrt(af2)) : 0.0;
+    as = wb_normal_pos(as2) ? WB_MUL(as2, wb_rsqrt(as2)) : 0.0;
   }
-  const double ra2 = rho * a2;
+  const double ra2 = WB_MUL(rho, a2);
   double b1n, b2n;
-  if (wb_le_nonneg(bt2s, 1e-24 * (ra2 + b2 + bt2s))) {
+  if (wb_le_nonneg(bt2s, WB_MUL(1e-24, WB_ADD(WB_ADD(ra2, b2), bt2s)))) {
     b1n = b2n = 0.70710678118654752440;
   } else {
     const double ib = wb_rsqrt(bt2s);
-    b1n = bt1 * ib;
-    b2n = bt2 * ib;
+    b1n = WB_MUL(bt1, ib);
+    b2n = WB_MUL(bt2, ib);
   }
   const double S = wb_sgn(b);
   // primitive differences of the 7-variable system; the velocity differences
   // are kept times rho_ (dv' = rho_ dv), the 1/rho_ goes into the coefficients
-  const double drho = R.rho - L.rho;
-  const double dmn = R.mn - L.mn, dmt1 = R.mt1 - L.mt1, dmt2 = R.mt2 - L.mt2;
-  const double de = R.eref - L.eref;
-  const double dvn = dmn - vn * drho;
-  const double dvt1 = dmt1 - vt1 * drho;
-  const double dvt2 = dmt2 - vt2 * drho;
-  const double dp = P.gm1 * (de - (vn * dmn + vt1 * dmt1 + vt2 * dmt2) + hv2 * drho -
-                             (bt1 * dbt1 + bt2 * dbt2)) - gX * drho;
+  const double drho = WB_SUB(R.rho, L.rho);
+  const double dmn = WB_SUB(R.mn, L.mn), dmt1 = WB_SUB(R.mt1, L.mt1), dmt2 = WB_SUB(R.mt2, L.mt2);
+  const double de = WB_SUB(R.eref, L.eref);
+  const double dvn = WB_FMA(-vn, drho, dmn);
+  const double dvt1 = WB_FMA(-vt1, drho, dmt1);
+  const double dvt2 = WB_FMA(-vt2, drho, dmt2);
+  const double vdm = WB_FMA(vn, dmn, WB_FMA(vt1, dmt1, WB_MUL(vt2, dmt2)));
+  const double bdb = WB_FMA(bt1, dbt1, WB_MUL(bt2, dbt2));
+  const double dp = WB_FMA(-gX, drho, WB_MUL(P.gm1, WB_SUB(WB_FMA(hv2, drho, WB_SUB(de, vdm)), bdb)));
   // projections on the transverse field direction beta and its normal; S = sign(b)
-  const double dvbS = wb_xsgn(b1n * dvt1 + b2n * dvt2, S), dvp = -b2n * dvt1 + b1n * dvt2;
-  const double dbb = b1n * dbt1 + b2n * dbt2, dbpS = wb_xsgn(-b2n * dbt1 + b1n * dbt2, S);
-  const double ia2 = ia * ia;
+  const double dvbS = wb_xsgn(WB_FMA(b1n, dvt1, WB_MUL(b2n, dvt2)), S);
+  const double dvp = WB_FMA(-b2n, dvt1, WB_MUL(b1n, dvt2));
+  const double dbb = WB_FMA(b1n, dbt1, WB_MUL(b2n, dbt2));
+  const double dbpS = wb_xsgn(WB_FMA(-b2n, dbt1, WB_MUL(b1n, dbt2)), S);
+  const double ia2 = WB_MUL(ia, ia);
   const double hir = wb_half(irho), hisr = wb_half(isrho);
-  const double i2ra = hisr * ia;         // 1 / (2 sqrt(rho) a)
-  const double ri2a2 = hir * ia2;        // 1 / (2 rho a^2)
-  const double dpr = dp * ri2a2;
-  const double afcf = af * cf, ascs = as * cs;
-  const double Af = (afcf * dvn - ascs * dvbS) * ri2a2;
-  const double Cf = as * dbb * i2ra + af * dpr;
-  const double As = (ascs * dvn + afcf * dvbS) * ri2a2;
-  const double Cs = -af * dbb * i2ra + as * dpr;
-  const double hAa = hisr * dbpS;
+  const double i2ra = WB_MUL(hisr, ia);   // 1 / (2 sqrt(rho) a)
+  const double ri2a2 = WB_MUL(hir, ia2);  // 1 / (2 rho a^2)
+  const double dpr = WB_MUL(dp, ri2a2);
+  const double afcf = WB_MUL(af, cf), ascs = WB_MUL(as, cs);
+  const double dbbi = WB_MUL(dbb, i2ra);
+  const double Af = WB_MUL(WB_FMA(afcf, dvn, -WB_MUL(ascs, dvbS)), ri2a2);
+  const double Cf = WB_FMA(as, dbbi, WB_MUL(af, dpr));
+  const double As = WB_MUL(WB_FMA(ascs, dvn, WB_MUL(afcf, dvbS)), ri2a2);
+  const double Cs = WB_FMA(-af, dbbi, WB_MUL(as, dpr));
+  const double hAa = WB_MUL(hisr, dbpS);
   double al[7];
-  al[0] = Cf - Af;
-  al[6] = Cf + Af;
-  al[2] = Cs - As;
-  al[4] = Cs + As;
-  al[1] = fma(hir, dvp, hAa);
-  al[5] = fma(hir, dvp, -hAa);
-  al[3] = fma(-dp, ia2, drho);
+  al[0] = WB_SUB(Cf, Af);
+  al[6] = WB_ADD(Cf, Af);
+  al[2] = WB_SUB(Cs, As);
+  al[4] = WB_ADD(Cs, As);
+  al[1] = WB_FMA(hir, dvp, hAa);
+  al[5] = WB_FMA(hir, dvp, -hAa);
+  al[3] = WB_FMA(-dp, ia2, drho);
   // nu_k = (dt/dx) a_k for the eigenvalues a_1..a_7 (Sec. 3)
-  const double tvn = dtdx * vn, tcf = dtdx * cf, tca = dtdx * ca, tcs = dtdx * cs;
-  const double nuk[7] = {tvn - tcf, tvn - tca, tvn - tcs, tvn, tvn + tcs, tvn + tca, tvn + tcf};
+  const double tvn = WB_MUL(dtdx, vn);
+  const double nuk[7] = {WB_FMA(-dtdx, cf, tvn), WB_FMA(-dtdx, ca, tvn), WB_FMA(-dtdx, cs, tvn), tvn,
+                         WB_FMA(dtdx, cs, tvn),  WB_FMA(dtdx, ca, tvn),  WB_FMA(dtdx, cf, tvn)};
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
     const double nu = nuk[k];
     f[R_AL + k] = al[k];
     f[R_NU + k] = nu;
-    gt[k] = Qk_m_nu2<EZ>(nu, k, P) * wb_half(al[k]);
+    gt[k] = WB_MUL(Qk_m_nu2<EZ>(nu, k, P), wb_half(al[k]));
   }
-  f[R_RHO] = rho; f[R_SRHO] = srho; f[R_A] = a; f[R_PG] = ra2 * P.inv_gm1; f[R_CF] = cf;
+  f[R_RHO] = rho; f[R_SRHO] = srho; f[R_A] = a; f[R_PG] = WB_MUL(ra2, P.inv_gm1); f[R_CF] = cf;
   f[R_ASCS] = ascs; f[R_AFCF] = afcf; f[R_AF] = af; f[R_AS] = as; f[R_B1] = b1n; f[R_B2] = b2n; f[R_S] = S;
   f[R_VN] = vn; f[R_VT1] = vt1; f[R_VT2] = vt2; f[R_BT1] = bt1; f[R_BT2] = bt2;
-  f[R_KX] = fma(gX, P.inv_gm1, hv2);
+  f[R_KX] = WB_FMA(gX, P.inv_gm1, hv2);
 #pragma unroll
-  for (int m = 0; m < 7; ++m) f[R_FAVG + m] = L.F[m] + R.F[m];
+  for (int m = 0; m < 7; ++m) f[R_FAVG + m] = WB_ADD(L.F[m], R.F[m]);
   if (PROT && P.prot && protection_hit(L, R, rho, ra2, af, as, al, P)) return 1;
   return 0;
 }
@@ -327,18 +346,18 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
 template <int EZ>
 __device__ __forceinline__ double beta_k(double al, double nu, double gi, double gi1, int k,
                                          const WbPhys& P) {
-  const double w = fma(nu, al, gi1 - gi);             // (nu + gamma) alpha
+  const double w = WB_FMA(nu, al, WB_SUB(gi1, gi));  // (nu + gamma) alpha
   double qa;
   if (wb_zero(al)) {
     qa = 0.0;                                           // gamma = 0, Q(nu) 0
-  } else if ((EZ & (1 << k)) || !wb_abs_less(w, P.two_eps[k] * al)) {
+  } else if ((EZ & (1 << k)) || !wb_abs_less(w, WB_MUL(P.two_eps[k], al))) {
     qa = wb_copysign_abs(w, al);                        // |nu + gamma| >= 2 eps
   } else if (wb_abs_less(al, 1e-290)) {
-    qa = P.eps[k] * al;                                 // w^2/(4 eps alpha) < eps |alpha|
+    qa = WB_MUL(P.eps[k], al);                          // w^2/(4 eps alpha) < eps |alpha|
   } else {
-    qa = fma(w * w * P.inv4eps[k], wb_rcp(al), P.eps[k] * al);
+    qa = WB_FMA(WB_MUL(WB_MUL(w, w), P.inv4eps[k]), wb_rcp(al), WB_MUL(P.eps[k], al));
   }
-  return qa - (gi + gi1);
+  return WB_SUB(qa, WB_ADD(gi, gi1));
 }
 
 // u-bar = (F_L + F_R)/2 - (dx/(2 dt)) sum_k beta_k R_k  (App. A)
@@ -351,33 +370,34 @@ __device__ __forceinline__ void face_flux(const Rc& f, const double gi[7], const
   const double rho = f[R_RHO], af = f[R_AF], as = f[R_AS];
   const double S = f[R_S], b1 = f[R_B1], b2 = f[R_B2];
   // sum_k beta_k r_k in w = (rho, vn, vt, Bt, p)
-  const double sf = be[0] + be[6], df = be[6] - be[0];
-  const double ss = be[2] + be[4], ds = be[4] - be[2];
-  const double tfs = af * sf + as * ss;
-  const double wr = rho * tfs + be[3];
+  const double sf = WB_ADD(be[0], be[6]), df = WB_SUB(be[6], be[0]);
+  const double ss = WB_ADD(be[2], be[4]), ds = WB_SUB(be[4], be[2]);
+  const double tfs = WB_FMA(af, sf, WB_MUL(as, ss));
+  const double wr = WB_FMA(rho, tfs, be[3]);
   const double afcf = f[R_AFCF], ascs = f[R_ASCS];
-  const double wvn = afcf * df + ascs * ds;
-  const double vb = wb_xsgn(afcf * ds - ascs * df, S);   // along beta
-  const double vp = be[1] + be[5];                       // along beta-perp
-  const double ra = f[R_SRHO] * f[R_A];
-  const double bb = ra * (as * sf - af * ss);
-  const double bp = wb_xsgn(f[R_SRHO] * (be[1] - be[5]), S);
-  const double wvt1 = b1 * vb - b2 * vp, wvt2 = b2 * vb + b1 * vp;
-  const double wbt1 = b1 * bb - b2 * bp, wbt2 = b2 * bb + b1 * bp;
+  const double wvn = WB_FMA(afcf, df, WB_MUL(ascs, ds));
+  const double vb = wb_xsgn(WB_FMA(afcf, ds, -WB_MUL(ascs, df)), S);  // along beta
+  const double vp = WB_ADD(be[1], be[5]);                             // along beta-perp
+  const double ra = WB_MUL(f[R_SRHO], f[R_A]);
+  const double bb = WB_MUL(ra, WB_FMA(as, sf, -WB_MUL(af, ss)));
+  const double bp = wb_xsgn(WB_MUL(f[R_SRHO], WB_SUB(be[1], be[5])), S);
+  const double wvt1 = WB_FMA(b1, vb, -WB_MUL(b2, vp)), wvt2 = WB_FMA(b2, vb, WB_MUL(b1, vp));
+  const double wbt1 = WB_FMA(b1, bb, -WB_MUL(b2, bp)), wbt2 = WB_FMA(b2, bb, WB_MUL(b1, bp));
   // to conserved variables (the pressure row enters the energy as p/(gamma-1))
   const double vn = f[R_VN], vt1 = f[R_VT1], vt2 = f[R_VT2];
-  const double u1 = vn * wr + rho * wvn;
-  const double u2 = vt1 * wr + rho * wvt1;
-  const double u3 = vt2 * wr + rho * wvt2;
-  const double u6 = f[R_PG] * tfs + f[R_KX] * wr + rho * (vn * wvn + vt1 * wvt1 + vt2 * wvt2) +
-                    f[R_BT1] * wbt1 + f[R_BT2] * wbt2;
-  out[0] = f[R_FAVG + 0] - dx_2dt * wr;
-  out[1] = f[R_FAVG + 1] - dx_2dt * u1;
-  out[2] = f[R_FAVG + 2] - dx_2dt * u2;
-  out[3] = f[R_FAVG + 3] - dx_2dt * u3;
-  out[4] = f[R_FAVG + 4] - dx_2dt * wbt1;
-  out[5] = f[R_FAVG + 5] - dx_2dt * wbt2;
-  out[6] = f[R_FAVG + 6] - dx_2dt * u6;
+  const double u1 = WB_FMA(vn, wr, WB_MUL(rho, wvn));
+  const double u2 = WB_FMA(vt1, wr, WB_MUL(rho, wvt1));
+  const double u3 = WB_FMA(vt2, wr, WB_MUL(rho, wvt2));
+  const double vw = WB_FMA(vn, wvn, WB_FMA(vt1, wvt1, WB_MUL(vt2, wvt2)));
+  const double u6 = WB_FMA(f[R_BT2], wbt2, WB_FMA(f[R_BT1], wbt1,
+                    WB_FMA(rho, vw, WB_FMA(f[R_PG], tfs, WB_MUL(f[R_KX], wr)))));
+  out[0] = WB_FMA(-dx_2dt, wr, f[R_FAVG + 0]);
+  out[1] = WB_FMA(-dx_2dt, u1, f[R_FAVG + 1]);
+  out[2] = WB_FMA(-dx_2dt, u2, f[R_FAVG + 2]);
+  out[3] = WB_FMA(-dx_2dt, u3, f[R_FAVG + 3]);
+  out[4] = WB_FMA(-dx_2dt, wbt1, f[R_FAVG + 4]);
+  out[5] = WB_FMA(-dx_2dt, wbt2, f[R_FAVG + 5]);
+  out[6] = WB_FMA(-dx_2dt, u6, f[R_FAVG + 6]);
 }
 
 // One pencil segment of an MHDTVD sweep along D: fluxes of faces [fa, fb]
@@ -403,8 +423,8 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
   const long long base = wb_at(g, pos[0], pos[1], pos[2]);
   const long long off_in = qo + base;
   const long long off_out = wo + base;
-  const double dtdx = dt * g.idx[D];
-  const double dx_2dt = 0.5 * g.dx[D] * wb_rcp(dt);
+  const double dtdx = WB_MUL(dt, g.idx[D]);
+  const double dx_2dt = WB_MUL(wb_half(g.dx[D]), wb_rcp(dt));
   Cell cL, cR;
   load_cell<D, NC>(q, off_in, P, cL);
   double gt_p[7], g_p[7];  // g-tilde of face f-1; g of zone f-2

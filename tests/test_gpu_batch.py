@@ -6,7 +6,6 @@ with a barrier wait forced to run out (error status, context still usable)."""
 import numpy as np
 import pytest
 
-from parity import state_err
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +44,9 @@ def test_batch_matches_single_box_grids(wb):
         g = wb.Grid(boxes[i]["n"], length=boxes[i]["length"])
         g.load_state(st)
         g.advance(4)
-        assert state_err(bt.read(i), g.read()) < 1e-11, i
+        # the stage arithmetic is explicitly rounded: the same bits as the grid
+        for a, b in zip(bt.read(i), g.read()):
+            assert np.array_equal(a, b), i
         c = bt.counters(i)
         assert c["steps"] == 4 and c["unphysical"] == 0
         assert abs(c["t"] - g.counters()["t"]) <= 1e-13 * c["t"]
@@ -143,8 +144,7 @@ def test_staged_stage_timer(wb):
 def test_mixed_boundaries_both_forms(wb):
     """Periodic boxes (interior-only stages with images) and outflow boxes
     (ghost-ring regions, zero-gradient ghost fill) in one batch: each box
-    matches its single grid, and the staged form gives the persistent form's
-    bits."""
+    gives its single grid's bits in both forms."""
     sizes = [(12, 10, 9), (10, 12, 8), (8, 8, 8)]
     bcs = [(0, 0, 0), (1, 1, 1), (0, 1, 0)]
     boxes, states = boxes_and_states(sizes, seed0=500)
@@ -163,6 +163,5 @@ def test_mixed_boundaries_both_forms(wb):
         g = wb.Grid(b["n"], length=b["length"], bc=b["bc"])
         g.load_state(st)
         g.advance(4)
-        assert state_err(runs[0][i], g.read()) < 1e-11, i
-        for a, c in zip(runs[0][i], runs[1][i]):
-            assert np.array_equal(a, c), i
+        for a, c, e in zip(runs[0][i], runs[1][i], g.read()):
+            assert np.array_equal(a, c) and np.array_equal(a, e), i
