@@ -46,11 +46,11 @@ SEED = 2
 # system it computes, from the ncu FP64 instruction counters of k_sweep on the
 # 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full.md): 492 M flops over
 # 9216 pencils x 4 segments x 26 interface systems.
-FLOPS_PER_FACE = 513.0
+FLOPS_PER_FACE = 514.0
 # DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the mean
 # of the six sweeps of a step from one ncu capture of this kernel
 # (profiles/k_sweep_256cube_dram.md); the algorithmic figure is 128 B per face.
-SWEEP_DRAM_BYTES_256 = 3.681e9
+SWEEP_DRAM_BYTES_256 = 3.677e9
 SWEEP_BYTES_PER_FACE = 128.0
 # FP64 flops of the other stages of a step per zone: 459 from the ncu counters
 # of the corner EMFs, CT, transverse states, half-step EMF and update kernels
