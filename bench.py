@@ -213,10 +213,11 @@ def cpu_sample(n_sample, steps, threads=0, st=None):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    # each bench step: one oracle step of a 128^3 box of the same turbulence
-    # data (about a second on 16 cores), so a default run ends in under a minute
+    # each bench step: one oracle step of a 128^3 box (--ref-sample) of the
+    # same turbulence data (about a second on 16 cores), so a default run ends
+    # in under a minute
     from paper_1701_07452_gb300.initial_conditions import turbulence_box
-    n_sample, steps_per = 128, 1
+    n_sample, steps_per = args.ref_sample, 1
     st = turbulence_box(n_sample, SEED)
     for _ in range(args.warmup):
         cpu_sample(n_sample, steps_per, st=st)
@@ -456,6 +457,8 @@ def main():
     ap.add_argument("--nbox", type=int, default=64)
     ap.add_argument("--form", default="auto", choices=["auto", "persistent", "staged"],
                     help="batch mode: the autotuned form, or a given one without autotuning")
+    ap.add_argument("--ref-sample", type=int, default=128,
+                    help="reference arm: edge of the box the oracle steps per bench step")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--steps-scale", type=float, default=0.1)
     args = ap.parse_args()
