@@ -71,3 +71,19 @@ def test_full_size_ten_steps_properties(wb, oracle_mod, state):
     o.load(U, bx, by, bz)
     d_or = o.dt()
     assert abs(g.dt() - d_or) <= 1e-14 * d_or
+
+
+def test_full_size_batch_equals_grid(wb, state):
+    """The bench's box advanced through the batch path (staged form, the
+    sweep inside the batch kernel) gives the single grid's bits."""
+    n = (N, N, N)
+    g = wb.Grid(n, length=state["length"])
+    g.load_state(state)
+    g.advance(2)
+    bt = wb.Batch([{"n": n, "length": state["length"]}])
+    bt.set_form("staged")
+    bt.load_state(0, state)
+    bt.set_steps(0, 2)
+    bt.advance(2)
+    for a, b in zip(bt.read(0), g.read()):
+        assert np.array_equal(a, b)
