@@ -15,9 +15,10 @@
 // of a grid use (wb_units.cuh).
 //
 // The staged form runs the same stages as one ordinary launch each (the
-// sweeps in k_batch limited to one stage, the zone stages in kernels compiled
-// per stage class with their own occupancy), all captured in one CUDA graph;
-// both forms give the same bits.
+// sweeps in a kernel that holds only the sweep, the zone stages in kernels
+// compiled per stage class with their own occupancy), all captured in one
+// CUDA graph; the stage arithmetic is explicitly rounded, so both forms (and
+// the single-grid path) give the same bits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -174,10 +175,6 @@ struct BatchParams {
   int dt_lag;                 // dt from the previous step's start state
   int seg_len;
   long long budget;           // barrier wait budget in SM clock cycles
-  // staged form: k_batch runs only stage `stage` of group `stage_grp` (no
-  // barrier), launch stage_seq of the sequence; stage < 0: persistent form
-  int stage, stage_grp;
-  unsigned stage_seq;
 };
 
 // Grid-wide barrier with a bounded wait.  Returns false when the error word is
@@ -516,30 +513,18 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
   __shared__ long long s_chunk;
   const wbu::Rec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
   const unsigned nblocks = gridDim.x;
-  // one stage of the staged form, or every stage of nsteps steps; the stage
-  // body below is the one copy of it either way, so both forms compute the
-  // same bits
-  const bool one = B.stage >= 0;
-  const int step_end = one ? 1 : nsteps;
-  const int grp0 = one ? B.stage_grp : 0, grp_end = one ? B.stage_grp + 1 : B.ngroups;
-  const int s0 = one ? B.stage : 0, s_end = one ? B.stage + 1 : BS_COUNT;
   unsigned stage_seq = 0;
   // stage timer: block 0 stamps the end of every stage (after its barrier)
-  const bool timer = !one && B.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+  const bool timer = B.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
   unsigned long long t_prev = timer ? global_ns() : 0ULL;
-  for (int step = 0; step < step_end; ++step) {
-    for (int grp = grp0; grp < grp_end; ++grp) {
+  for (int step = 0; step < nsteps; ++step) {
+    for (int grp = 0; grp < B.ngroups; ++grp) {
       const int gb0 = B.gfirst[grp];
       const int nbox = B.gfirst[grp + 1] - gb0;
-      for (int s = s0; s < s_end; ++s, ++stage_seq) {
-        unsigned* ctr;
-        if (one) {
-          ctr = stage_counter(B, B.stage_seq);
-        } else {
-          ctr = B.sync + 3 + (stage_seq & 1u);
-          // the other counter is idle during this stage: block 0 clears it
-          if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(B.sync + 3 + ((stage_seq + 1) & 1u), 0u);
-        }
+      for (int s = 0; s < BS_COUNT; ++s, ++stage_seq) {
+        unsigned* ctr = B.sync + 3 + (stage_seq & 1u);
+        // the other counter is idle during this stage: block 0 clears it
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(B.sync + 3 + ((stage_seq + 1) & 1u), 0u);
         const long long* pre = B.pre + B.pre_off[grp * BS_COUNT + s];
         const int nsub = stage_nsub(s);
         const int nent = nbox * nsub;
@@ -584,10 +569,6 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
           if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
           if (hll) atomicAdd((unsigned long long*)&B.scal[box].hll_faces, (unsigned long long)hll);
         }
-        if (one) {
-          stage_stamp(B, s, B.stage_seq);
-          return;
-        }
         if (!grid_barrier(B, nblocks)) return;
         if (timer) {
           const unsigned long long t = global_ns();
@@ -602,12 +583,12 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
 // ------------------------------------------------------------ staged form
 // The same stages as separate launches, one per stage and workspace group: a
 // kernel boundary takes the place of each grid barrier, and blocks drain the
-// same chunk lists from the stage's counter.  The sweeps run in k_batch (one
-// stage per launch); the zone stages run in kernels compiled per stage class,
-// with as many resident warps as their own registers allow (inside the
+// same chunk lists from the stage's counter.  The sweeps run in a kernel that
+// holds only the sweep; the zone stages run in kernels compiled per stage
+// class, with as many resident warps as their own registers allow (inside the
 // persistent kernel every stage keeps the sweep's 4 blocks of 64 threads per
-// SM).  The zone stages' arithmetic is written with explicit rounding, so
-// both forms compute the same bits.
+// SM).  All stage arithmetic is written with explicit rounding, so both forms
+// compute the same bits.
 enum { SC_SWEEP = 0, SC_COPY, SC_PAIR, SC_TRANS, SC_EREF_H, SC_FINAL, SC_DT, SC_COUNT };
 
 __host__ __device__ inline int stage_class(int s) {
@@ -653,6 +634,33 @@ __device__ __forceinline__ void drain_stage(const BatchParams& B, int grp, int s
     }
     body(B.gbox[gb0 + lo / nsub], lo % nsub, c - pre[lo]);
   }
+}
+
+// The sweep stages of the staged form: the same chunks and per-item code as
+// the persistent kernel's sweep stage, in a kernel that holds nothing else
+// (the flux arithmetic is explicitly rounded, so the bits do not depend on
+// which kernel runs it).
+template <int EZ, bool PROT>
+__global__ void __launch_bounds__(kB, 4) k_bstage_sweep(BatchParams B, int grp, int s, unsigned seq) {
+  __shared__ double srec[2][wbu::R_WORDS][kB];
+  const wbu::Rec rec[2] = {{&srec[0][0][threadIdx.x]}, {&srec[1][0][threadIdx.x]}};
+  unsigned* ctr = stage_counter(B, seq);
+  const bool corr = s == BS_CORR;
+  drain_stage(B, grp, s, ctr, [&](int box, int d, long long cc) {
+    const double dt = B.scal[box].dt;
+    if (!(dt > 0.0)) return;
+    const BoxInfo& bi = B.boxes[box];
+    const long long nitems = stage_items(s, d, bi.v.geo, bi.wrap != 0, B.seg_len);
+    const long long it = cc * kB + threadIdx.x;
+    if (it >= nitems) return;
+    const WbBox b = stage_box(s, d, bi.v.geo.n, bi.wrap != 0);
+    int hll;
+    if (d == 0) hll = sweep_item<0, EZ, PROT>(bi, corr, b, it, B.seg_len, dt, B.phys, rec);
+    else if (d == 1) hll = sweep_item<1, EZ, PROT>(bi, corr, b, it, B.seg_len, dt, B.phys, rec);
+    else hll = sweep_item<2, EZ, PROT>(bi, corr, b, it, B.seg_len, dt, B.phys, rec);
+    if (hll) atomicAdd((unsigned long long*)&B.scal[box].hll_faces, (unsigned long long)hll);
+  });
+  stage_stamp(B, s, seq);
 }
 
 template <int CLS>
@@ -780,6 +788,7 @@ struct wb_batch {
   // launch configuration
   int form = WB_BATCH_PERSISTENT;
   int zone_blocks[SC_COUNT];  // resident blocks per SM of each zone-stage kernel (staged form)
+  int sweep_blocks = 1;       // resident blocks per SM of the staged form's sweep kernel
   int seg_len;
   int blocks_per_sm;
   int max_blocks_per_sm;
@@ -973,9 +982,6 @@ BatchParams params(const wb_batch* b) {
   p.dt_lag = b->dt_lag;
   p.seg_len = b->seg_len;
   p.budget = b->budget;
-  p.stage = -1;
-  p.stage_grp = 0;
-  p.stage_seq = 0;
   return p;
 }
 
@@ -986,6 +992,12 @@ const void* batch_kernel(const WbPhys& ph) {
   const bool ez = (ph.eps_zero & wbu::kEpsZeroLD) == wbu::kEpsZeroLD;
   if (ez && !ph.prot) return (const void*)k_batch<wbu::kEpsZeroLD, false>;
   return (const void*)k_batch<0, true>;
+}
+
+const void* bstage_sweep_kernel(const WbPhys& ph) {
+  const bool ez = (ph.eps_zero & wbu::kEpsZeroLD) == wbu::kEpsZeroLD;
+  if (ez && !ph.prot) return (const void*)k_bstage_sweep<wbu::kEpsZeroLD, false>;
+  return (const void*)k_bstage_sweep<0, true>;
 }
 
 const void* bstage_zone_kernel(int cls) {
@@ -1013,27 +1025,16 @@ cudaError_t enqueue_staged(wb_batch* b, int nsteps) {
         const void* fn;
         unsigned nt, nblocks;
         if (cls == SC_SWEEP) {
-          fn = batch_kernel(b->phys);
+          fn = bstage_sweep_kernel(b->phys);
           nt = kB;
-          nblocks = (unsigned)(b->blocks_per_sm * b->sms);
+          nblocks = (unsigned)(std::min(b->blocks_per_sm, b->sweep_blocks) * b->sms);
         } else {
           fn = bstage_zone_kernel(cls);
           nt = kNtZone;
           nblocks = (unsigned)((cls == SC_DT ? 1 : b->zone_blocks[cls]) * b->sms);
         }
-        if (cls == SC_SWEEP) {
-          // the sweeps run in k_batch itself (one stage, no barrier): the
-          // same compiled sweep as the persistent form
-          p.stage = s;
-          p.stage_grp = grp;
-          p.stage_seq = seq;
-          int one = 1;
-          void* args[] = {&p, &one};
-          e = cudaLaunchKernel(fn, dim3(nblocks), dim3(nt), args, 0, b->stream);
-        } else {
-          void* args[] = {&p, &grp, &s, &seq};
-          e = cudaLaunchKernel(fn, dim3(nblocks), dim3(nt), args, 0, b->stream);
-        }
+        void* args[] = {&p, &grp, &s, &seq};
+        e = cudaLaunchKernel(fn, dim3(nblocks), dim3(nt), args, 0, b->stream);
         if (e != cudaSuccess) return e;
       }
   return cudaSuccess;
@@ -1162,6 +1163,9 @@ int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel(b->phys), kB, 0);
   b->max_blocks_per_sm = nb > 0 ? nb : 1;
   b->blocks_per_sm = b->max_blocks_per_sm;
+  nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bstage_sweep_kernel(b->phys), kB, 0);
+  b->sweep_blocks = nb > 0 ? nb : 1;
   for (int c = 0; c < SC_COUNT; ++c) {
     nb = 0;
     if (c != SC_SWEEP) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bstage_zone_kernel(c), kNtZone, 0);
