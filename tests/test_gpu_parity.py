@@ -319,3 +319,44 @@ def test_reused_workspace_arrays(wb):
     with pytest.raises(wb.WombatError):
         lean.stage(0)
     assert np.array_equal(keep.stage(4), lean.stage(4))
+
+
+def test_ghost_poison_beyond_dependency_radius(wb):
+    """Halo indexing: on a box periodic on every axis (interior-only stages with
+    periodic images between them) a step reads the loaded ghost zones only to
+    depth 2.  NaN written into the state's ghost zones at depth 3 to 5 after
+    the load (every zone field and face field; the storage is padded by 5
+    zones per side, [field][z][y][x], state first in the workspace) must leave
+    the step's result bit-identical and every counter clean."""
+    import torch
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box
+    n = (20, 18, 16)
+    st = turbulence_box(n, seed=21)
+    clean = wb.Grid(n, length=st["length"])
+    clean.load_state(st)
+    clean.advance(1)
+    g = wb.Grid(n, length=st["length"])
+    g.load_state(st)
+    torch.cuda.synchronize()
+    NG = 5
+    pd = [x + 2 * NG for x in n]
+    V = pd[0] * pd[1] * pd[2]
+    mem = g.workspace.view(torch.float64)
+    idx = [torch.arange(p, device=mem.device) - NG for p in pd]
+    k, j, i = torch.meshgrid(idx[2], idx[1], idx[0], indexing="ij")
+
+    def depth(x, m):
+        return torch.clamp(torch.maximum(-x, x - (m - 1)), min=0)
+
+    d = torch.maximum(torch.maximum(depth(i, n[0]), depth(j, n[1])), depth(k, n[2]))
+    mask = (d >= 3).reshape(-1)
+    assert int(mask.sum()) > 0
+    for field in range(11):
+        view = mem[field * V:(field + 1) * V]
+        view[mask] = float("nan")
+    g.advance(1)
+    for a, b in zip(clean.read(), g.read()):
+        assert np.array_equal(a, b)
+    c = g.counters()
+    assert c["unphysical"] == 0 and c["floor_hits"] == 0
+    assert np.isfinite(g.totals()).all()
