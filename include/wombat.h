@@ -313,6 +313,18 @@ int wb_batch_steps_left(wb_batch* b, int* out);
  * Uses the grid's reduction words; synchronises the grid's stream. */
 int wb_selftest_math(wb_grid* g, int n, double worst[2]);
 
+/* Checked build (the library compiled with -DWB_CHECKED; a substitute for a
+ * device memory checker): every zone index a kernel forms, and the stencil
+ * neighbours of each stage, are tested against the padded storage of a
+ * patch; a bad index sets a check word and the access is redirected inside
+ * the array.  wb_check_flags synchronises the device, returns the check words
+ * of every translation unit OR-ed in *flags (0 = no bad index since the last
+ * call) and clears them; wb_check_selftest forms one out-of-range index in a
+ * probe kernel that accesses no memory and reports in *detected whether it
+ * was flagged.  In an unchecked build both return WB_ERR_INVALID with 0. */
+int wb_check_flags(unsigned* flags);
+int wb_check_selftest(int* detected);
+
 /* FP64 pipe probe: runs a dependent-free DFMA loop on every SM of the
  * current device and returns the achieved FP64 FLOP/s (FMA = 2 flops). */
 int wb_measure_fp64_peak(void* stream, double* flops);

@@ -33,18 +33,23 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Build the library; checked=True builds the index-checked variant
+    (-DWB_CHECKED) under _build/checked/."""
+    out = os.path.join(OUT, "checked") if checked else OUT
+    lib_path = os.path.join(out, "libwombat_gb300.so")
+    flags = FLAGS + (["-DWB_CHECKED"] if checked else [])
+    os.makedirs(out, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + \
         [os.path.join(os.path.dirname(HERE), "include", "wombat.h")]
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT, src.replace(".cu", ".o"))
+        o = os.path.join(out, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            jobs.append([nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([nvcc(), *ARCH, *flags, "-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]
@@ -54,14 +59,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     raise RuntimeError("nvcc failed: " + " ".join(j) + "\n" + r.stderr[-4000:])
                 if verbose and r.stderr:
                     print(r.stderr)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed: " + r.stderr[-4000:])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -30,7 +30,7 @@ EXPORTED = (
     "wb_batch_autotune", "wb_batch_config", "wb_batch_get_config", "wb_batch_last_error",
     "wb_pool_bytes", "wb_pool_create", "wb_pool_admit", "wb_pool_release", "wb_pool_free_bytes",
     "wb_batch_steps_left", "wb_batch_stage_timer", "wb_batch_stage_times", "wb_batch_set_form",
-    "wb_batch_get_form",
+    "wb_batch_get_form", "wb_check_flags", "wb_check_selftest",
 )
 
 BATCH_FORMS = {"persistent": 0, "staged": 1}
@@ -78,7 +78,12 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    return os.path.join(_build.OUT, "checked", "libwombat_gb300.so") if _checked() else _build.LIB
+
+
+def _checked() -> bool:
+    """WOMBAT_CHECKED=1 in the environment loads the index-checked build."""
+    return os.environ.get("WOMBAT_CHECKED", "") == "1"
 
 
 def lib(build: bool = True):
@@ -86,7 +91,7 @@ def lib(build: bool = True):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build() if build else _build.LIB
+            path = _build.build(checked=_checked()) if build else library_path()
             if not os.path.exists(path):
                 raise RuntimeError(f"libwombat_gb300.so not found at {path}")
             L = ctypes.CDLL(path)
@@ -130,6 +135,8 @@ def lib(build: bool = True):
             L.wb_batch_stage_times.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
             L.wb_batch_get_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]
+            L.wb_check_flags.argtypes = [ctypes.POINTER(ctypes.c_uint)]
+            L.wb_check_selftest.argtypes = [ctypes.POINTER(ctypes.c_int)]
             L.wb_batch_set_form.argtypes = [vp, ctypes.c_int]
             L.wb_batch_get_form.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
             L.wb_batch_last_error.argtypes = [vp]
@@ -509,6 +516,25 @@ def step_noalloc(desc: WbDesc, U, bx, by, bz, U_out, bx_out, by_out, bz_out, dt_
                                ctypes.c_void_p(s.cuda_stream))
     if rc:
         raise WombatError(rc, lib().wb_noalloc_last_error().decode())
+
+
+def check_flags() -> int:
+    """Check words of the index-checked build (0: no bad index since the last
+    call).  Raises in an unchecked build."""
+    out = ctypes.c_uint(0)
+    rc = lib().wb_check_flags(ctypes.byref(out))
+    if rc:
+        raise WombatError(rc, "not the checked build (set WOMBAT_CHECKED=1)")
+    return int(out.value)
+
+
+def check_selftest() -> bool:
+    """The checked build flags an out-of-range index formed by a probe kernel."""
+    out = ctypes.c_int(0)
+    rc = lib().wb_check_selftest(ctypes.byref(out))
+    if rc:
+        raise WombatError(rc, "not the checked build (set WOMBAT_CHECKED=1)")
+    return bool(out.value)
 
 
 def measure_fp64_peak(stream=None) -> float:

@@ -1619,3 +1619,5 @@ int wb_batch_autotune(wb_batch* b, int trial_steps, double* best_ms) {
 const char* wb_batch_last_error(const wb_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
 }  // extern "C"
+
+WB_CHECK_ACCESSOR(wb_check_take_batch)

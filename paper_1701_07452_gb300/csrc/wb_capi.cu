@@ -525,7 +525,6 @@ int wb_grid_create(const wb_desc* d, void* dev_mem, size_t bytes, void* stream, 
   for (int c = 0; c < 3; ++c) g->b[c] = st + (size_t)(8 + c) * V * L.npatch;
   double* w = reinterpret_cast<double*>(g->mem + L.state);
   size_t slab = V * (size_t)L.S;
-  size_t k = 0;
   carve_work(g, w, slab, d->keep_stages != 0);
   g->staging = reinterpret_cast<double*>(g->mem + L.state + L.work);
   g->scal = reinterpret_cast<WbScalars*>(g->mem + L.state + L.work + L.staging);
@@ -949,6 +948,56 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
   e = cudaGetLastError();
   if (e != cudaSuccess) return noalloc_fail(WB_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return WB_OK;
+}
+
+}  // extern "C"
+
+WB_CHECK_ACCESSOR(wb_check_take_capi)
+
+#ifdef WB_CHECKED
+namespace {
+// Positive control of the checked build: forms the index of a zone one past
+// the padded storage, which wb_at must flag; nothing is read or written at it.
+__global__ void k_check_probe(WbGeo g, long long* sink) {
+  const long long o = wb_at(g, g.pd[0] - WB_NG, 0, 0);
+  if (o == -1 && sink) *sink = o;  // never true: keeps the index computation
+}
+}  // namespace
+#endif
+
+extern "C" {
+
+int wb_check_flags(unsigned* flags) {
+  if (!flags) return WB_ERR_INVALID;
+  cudaDeviceSynchronize();
+  *flags = wb_check_take_sweep() | wb_check_take_stages() | wb_check_take_capi() | wb_check_take_batch();
+#ifdef WB_CHECKED
+  return WB_OK;
+#else
+  return WB_ERR_INVALID;
+#endif
+}
+
+int wb_check_selftest(int* detected) {
+  if (!detected) return WB_ERR_INVALID;
+  *detected = 0;
+#ifdef WB_CHECKED
+  WbGeo g{};
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = 4;
+    g.pd[a] = 4 + 2 * WB_NG;
+  }
+  g.sy = g.pd[0];
+  g.sz = (long long)g.pd[0] * g.pd[1];
+  g.V = g.sz * g.pd[2];
+  wb_check_take_capi();
+  k_check_probe<<<1, 32>>>(g, nullptr);
+  if (cudaDeviceSynchronize() != cudaSuccess) return WB_ERR_CUDA;
+  *detected = wb_check_take_capi() != 0;
+  return WB_OK;
+#else
+  return WB_ERR_INVALID;
+#endif
 }
 
 }  // extern "C"

@@ -31,7 +31,52 @@ struct WbGeo {
   double dx[3], idx[3];
 };
 
+// Zone (i, j, k) lies in the padded storage of a patch (a z index is free in
+// the one-plane storage of a 2D box, whose z stride is 0).
+__host__ __device__ __forceinline__ bool wb_zone_ok(const WbGeo& g, int i, int j, int k) {
+  return i >= -WB_NG && i < g.pd[0] - WB_NG && j >= -WB_NG && j < g.pd[1] - WB_NG &&
+         (g.sz == 0 || (k >= -WB_NG && k < g.pd[2] - WB_NG));
+}
+
+// The checked build (-DWB_CHECKED; a substitute for a memory checker, which
+// this GPU pool does not offer): every zone index a kernel forms is tested
+// against the padded storage; a bad one sets a bit in the translation unit's
+// check word (read through wb_check_flags) and wb_at redirects it to zone
+// (0, 0, 0), so the access stays inside the array.
+#ifdef WB_CHECKED
+static __device__ unsigned wb_check_word;
+#define WB_CHECK_ZONE(g, i, j, k)                                        \
+  do {                                                                   \
+    if (!wb_zone_ok((g), (i), (j), (k))) atomicOr(&wb_check_word, 1u);  \
+  } while (0)
+#else
+#define WB_CHECK_ZONE(g, i, j, k) \
+  do {                            \
+  } while (0)
+#endif
+
+// Host accessor of a translation unit's check word: returns it and clears it
+// (0 in an unchecked build).  Each .cu file defines one with WB_CHECK_ACCESSOR.
+#ifdef WB_CHECKED
+#define WB_CHECK_ACCESSOR(name)                                     \
+  unsigned name() {                                                 \
+    unsigned v = 0, z = 0;                                          \
+    cudaMemcpyFromSymbol(&v, wb_check_word, sizeof(v));             \
+    cudaMemcpyToSymbol(wb_check_word, &z, sizeof(z));               \
+    return v;                                                       \
+  }
+#else
+#define WB_CHECK_ACCESSOR(name) \
+  unsigned name() { return 0u; }
+#endif
+
 __host__ __device__ __forceinline__ long long wb_at(const WbGeo& g, int i, int j, int k) {
+#if defined(WB_CHECKED) && defined(__CUDA_ARCH__)
+  if (!wb_zone_ok(g, i, j, k)) {
+    atomicOr(&wb_check_word, 1u);
+    i = j = k = 0;
+  }
+#endif
   return (long long)(k + WB_NG) * g.sz + (long long)(j + WB_NG) * g.sy + (i + WB_NG);
 }
 

@@ -564,3 +564,5 @@ void wb_launch_copy_box(const double* src, long long slot, const WbGeo& geo, con
 void wb_launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {
   k_fp64_probe<<<blocks, 256, 0, s>>>(out, iters);
 }
+
+WB_CHECK_ACCESSOR(wb_check_take_stages)

@@ -223,3 +223,5 @@ __global__ void k_math_selftest(int n, unsigned long long seed, unsigned long lo
 void wb_launch_math_selftest(int n, unsigned long long* worst, cudaStream_t s) {
   k_math_selftest<<<(n + 255) / 256, 256, 0, s>>>(n, 0x1234567ULL, worst);
 }
+
+WB_CHECK_ACCESSOR(wb_check_take_sweep)

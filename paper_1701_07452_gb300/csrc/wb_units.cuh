@@ -421,6 +421,12 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
   pos[D] = fa - 2;
   const long long st = wb_stride<D>(g);
   const long long base = wb_at(g, pos[0], pos[1], pos[2]);
+  {
+    int last[3] = {pos[0], pos[1], pos[2]};
+    last[D] = fb + 1;  // the segment reads zones fa-2 .. fb+1
+    WB_CHECK_ZONE(g, last[0], last[1], last[2]);
+    (void)last;
+  }
   const long long off_in = qo + base;
   const long long off_out = wo + base;
   const double dtdx = WB_MUL(dt, g.idx[D]);
@@ -562,6 +568,7 @@ __device__ __forceinline__ void edge_load(const WbView& v, long long wo, bool co
   const long long o = wo + wb_at(g, i, j, k);
   const long long sa = a == 0 ? 1 : (a == 1 ? g.sy : g.sz);
   const long long sb = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
+  WB_CHECK_ZONE(g, i - (a == 0) - (b == 0), j - (a == 1) - (b == 1), k - (a == 2) - (b == 2));
   double* const* Fa = corr ? v.Fc[a] : v.Fp[a];
   double* const* Fb = corr ? v.Fc[b] : v.Fp[b];
   const double* Er = corr ? v.Erefh[C] : v.Eref[C];
@@ -613,6 +620,8 @@ __device__ __forceinline__ void ct_load(const WbView& v, long long qo, long long
   in.q = qo + wb_at(g, i, j, k);
   const long long sa = a == 0 ? 1 : (a == 1 ? g.sy : g.sz);
   const long long sb = b == 0 ? 1 : (b == 1 ? g.sy : g.sz);
+  WB_CHECK_ZONE(g, i + (a == 0), j + (a == 1), k + (a == 2));
+  WB_CHECK_ZONE(g, i + (b == 0), j + (b == 1), k + (b == 2));
   const double* Eb = fin ? v.Eedgeh[b] : v.Eedge[b];
   const double* Ea = fin ? v.Eedgeh[a] : v.Eedge[a];
   in.Eb0 = Eb[in.w];
@@ -711,6 +720,7 @@ __device__ __forceinline__ void transverse_set(const WbView& v, long long qo, lo
                                                int mask, int i, int j, int k) {
   const long long q = qo + wb_at(v.geo, i, j, k);
   const long long w = wo + wb_at(v.geo, i, j, k);
+  WB_CHECK_ZONE(v.geo, i + 1, j + 1, k + 1);  // the high neighbours of every axis
   // flux differences of every direction some state needs
   int need = 0;
 #pragma unroll
@@ -738,6 +748,7 @@ __device__ __forceinline__ void eref_half_load(const WbView& v, long long qo, lo
   const long long q = qo + wb_at(g, i, j, k);
   const long long w = wo + wb_at(g, i, j, k);
   const long long s[3] = {1, g.sy, g.sz};
+  WB_CHECK_ZONE(g, i + 1, j + 1, k + 1);
   in.w = w;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -911,6 +922,7 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
   const WbGeo& g = v.geo;
   const long long q = qo + wb_at(g, i, j, k);
   const long long wi = wo + wb_at(g, i, j, k);
+  WB_CHECK_ZONE(g, i + 1, j + 1, k + 1);
   const long long s[3] = {1, g.sy, g.sz};
   // explicit rounding: the same bits in every kernel this is inlined into
   const double cx = __dmul_rn(dt, g.idx[0]), cy = __dmul_rn(dt, g.idx[1]), cz = __dmul_rn(dt, g.idx[2]);
