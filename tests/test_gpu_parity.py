@@ -101,10 +101,10 @@ def test_patches_bit_exact(wb, n, patches, batch):
 
 def test_balanced_sweep_split(wb, oracle_mod):
     """Boxes large enough that every sweep launch hands each resident warp an
-    equal run of (slot, 32-pencil group, face) units (at least 64 units per
-    warp on a 152-SM GPU at 4 resident 64-thread blocks per SM), with a ragged
-    last group of pencils: one step against the oracle, and 2^3 resident
-    patches against the single grid bit for bit (the runs then span slots)."""
+    equal run of (slot, 32-pencil group, face) units (dozens of units per warp
+    on a 152-SM GPU at 4 resident 64-thread blocks per SM), with a ragged last
+    group of pencils: one step against the oracle, and 2^3 resident patches
+    against the single grid bit for bit (the runs then span slots)."""
     from paper_1701_07452_gb300.initial_conditions import turbulence_box
     n = (150, 136, 144)   # z sweep: 20400 pencils, the last group holds 16
     st = turbulence_box(n, seed=11)
