@@ -107,10 +107,22 @@ struct WbScalars {
 
 
 // magnitude comparison on the IEEE bit pattern (integer pipe): |a| < |b|
+// The sign bit is dropped by a left shift, not by a mask: the compiler turns
+// a masked sign bit into an FP64 absolute value, which costs an FP64-pipe
+// instruction on this GPU (measured), while the shift stays on the integer
+// pipe.
 __device__ __forceinline__ bool wb_abs_less(double a, double b) {
-  unsigned long long ua = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffULL;
-  unsigned long long ub = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffULL;
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a) << 1;
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b) << 1;
   return ua < ub;
+}
+
+// |x| on the integer pipe: the sign bit of the high word is cleared in PTX
+// (fabs, or a 64-bit mask, becomes an FP64-pipe instruction on this GPU).
+__device__ __forceinline__ double wb_fabs(double x) {
+  int hi = __double2hiint(x), h2;
+  asm("and.b32 %0, %1, 0x7fffffff;" : "=r"(h2) : "r"(hi));
+  return __hiloint2double(h2, __double2loint(x));
 }
 
 // minmod(a, b) on the integer pipe: the argument of smaller magnitude when the
@@ -157,7 +169,8 @@ __device__ __forceinline__ bool wb_pos(double x) {
 // x < 0 (false for -0.0 and NaN)
 __device__ __forceinline__ bool wb_neg(double x) {
   const long long b = __double_as_longlong(x);
-  return b < 0 && (b & 0x7fffffffffffffffLL) != 0 && (b & 0x7fffffffffffffffLL) <= 0x7ff0000000000000LL;
+  const unsigned long long m = (unsigned long long)b << 1;  // |x| bits, shifted (see wb_abs_less)
+  return b < 0 && m != 0 && m <= 0xffe0000000000000ULL;
 }
 // x is a positive normal finite double (>= 2^-1022; false for subnormals,
 // zero, negatives, inf and NaN)

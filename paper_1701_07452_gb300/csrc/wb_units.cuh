@@ -124,8 +124,8 @@ using Rec = RecT<kBlock>;
 // EZ have eps_k = 0, where Q is |nu|; the branch test runs on the integer pipe.
 template <int EZ>
 __device__ __forceinline__ double Qk_m_nu2(double nu, int k, const WbPhys& P) {
-  if (EZ & (1 << k)) return WB_FMA(-nu, nu, fabs(nu));
-  const double q = wb_abs_less(nu, P.two_eps[k]) ? WB_FMA(WB_MUL(nu, nu), P.inv4eps[k], P.eps[k]) : fabs(nu);
+  if (EZ & (1 << k)) return WB_FMA(-nu, nu, wb_fabs(nu));
+  const double q = wb_abs_less(nu, P.two_eps[k]) ? WB_FMA(WB_MUL(nu, nu), P.inv4eps[k], P.eps[k]) : wb_fabs(nu);
   return WB_FMA(-nu, nu, q);
 }
 
@@ -245,7 +245,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   const double icf = wb_rsqrt(cf2);
   const double ia = wb_rsqrt(a2);
   const double a = WB_MUL(a2, ia);
-  const double ca = WB_MUL(fabs(b), isrho);
+  const double ca = WB_MUL(wb_fabs(b), isrho);
   const double cf = WB_MUL(cf2, icf);
   const double cs = WB_MUL(WB_MUL(a, ca), icf);  // c_f c_s = a c_a
   double af, as;
