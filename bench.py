@@ -44,19 +44,20 @@ N_BOX = 256
 SEED = 2
 # FP64 flops (DFMA = 2, DMUL = DADD = 1) the MHDTVD sweep executes per interface
 # system it computes, from the ncu FP64 instruction counters of k_sweep on the
-# 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full.md): 492 M flops over
-# 9216 pencils x 4 segments x 26 interface systems.
-FLOPS_PER_FACE = 514.0
+# 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full.md): 470 M flops over
+# the 978,944 interface systems of that launch (884,736 interior faces plus the
+# two overlap faces of every warp's segments).
+FLOPS_PER_FACE = 480.0
 # DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the mean
 # of the six sweeps of a step from one ncu capture of this kernel
 # (profiles/k_sweep_256cube_dram.md); the algorithmic figure is 128 B per face.
-SWEEP_DRAM_BYTES_256 = 3.677e9
+SWEEP_DRAM_BYTES_256 = 3.683e9
 SWEEP_BYTES_PER_FACE = 128.0
-# FP64 flops of the other stages of a step per zone: 459 from the ncu counters
+# FP64 flops of the other stages of a step per zone: 448 from the ncu counters
 # of the corner EMFs, CT, transverse states, half-step EMF and update kernels
 # on the 96^3 box (profiles/stages_96cube_ncu_full.md), plus 18 for the
 # reference EMF (its source: one reciprocal, three products, three pairs).
-STAGE_FLOPS_PER_ZONE = 477.0
+STAGE_FLOPS_PER_ZONE = 466.0
 # algorithmic state bytes per cell-update: 5 conserved fields and 3 face fields
 # read and written once (the step's HBM roofline)
 STEP_BYTES_PER_CELL = 128.0
