@@ -821,7 +821,7 @@ __device__ __forceinline__ double signal_rate_core(double ir, const double vv[3]
     const double dd = __dsub_rn(a2, cn2[d]);
     const double disc = __fma_rn(dd, dd, __dmul_rn(ct2, __fma_rn(2.0, __dadd_rn(a2, cn2[d]), ct2)));
     const double cf = wb_sqrt_fast(wb_half(__dadd_rn(S, wb_sqrt_fast(disc))));
-    w = __fma_rn(__dadd_rn(fabs(vv[d]), cf), g.idx[d], w);
+    w = __fma_rn(__dadd_rn(wb_fabs(vv[d]), cf), g.idx[d], w);
   }
   return w;
 }
