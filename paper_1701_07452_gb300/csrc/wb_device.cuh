@@ -125,6 +125,15 @@ __device__ __forceinline__ double wb_fabs(double x) {
   return __hiloint2double(h2, __double2loint(x));
 }
 
+// -x on the integer pipe: the sign bit of the high word flipped in PTX.  A
+// negated double that feeds a select or an integer-pipe test, rather than an
+// FMA operand (where the negation is free), otherwise costs an FP64 DADD.
+__device__ __forceinline__ double wb_flip(double x) {
+  int hi = __double2hiint(x), h2;
+  asm("xor.b32 %0, %1, 0x80000000;" : "=r"(h2) : "r"(hi));
+  return __hiloint2double(h2, __double2loint(x));
+}
+
 // minmod(a, b) on the integer pipe: the argument of smaller magnitude when the
 // signs agree, else 0 (the SWEBY limiter with beta = 1, App. A).
 __device__ __forceinline__ double wb_minmod(double a, double b) {

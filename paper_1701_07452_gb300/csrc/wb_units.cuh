@@ -573,8 +573,8 @@ __device__ __forceinline__ void edge_load(const WbView& v, long long wo, bool co
   double* const* Fb = corr ? v.Fc[b] : v.Fp[b];
   const double* Er = corr ? v.Erefh[C] : v.Eref[C];
   in.o = o;
-  in.Ea_0 = -Fa[F_BX + b][o];
-  in.Ea_m = -Fa[F_BX + b][o - sb];
+  in.Ea_0 = wb_flip(Fa[F_BX + b][o]);
+  in.Ea_m = wb_flip(Fa[F_BX + b][o - sb]);
   in.Eb_0 = Fb[F_BX + a][o];
   in.Eb_m = Fb[F_BX + a][o - sa];
   in.ma_0 = Fa[F_RHO][o];
@@ -697,8 +697,8 @@ template <int D>
 __device__ __forceinline__ void trans_dir(const WbView& v, long long w, const TransZone& z) {
   constexpr int t1 = (D + 1) % 3, t2 = (D + 2) % 3;
   const long long sD = D == 0 ? 1 : (D == 1 ? v.geo.sy : v.geo.sz);
-  const double hm2 = wb_minmod(z.hdb[D], -z.hdb[t1]);  // for the t2 field component
-  const double hm1 = wb_minmod(z.hdb[D], -z.hdb[t2]);  // for the t1 field component
+  const double hm2 = wb_minmod(z.hdb[D], wb_flip(z.hdb[t1]));  // for the t2 field component
+  const double hm1 = wb_minmod(z.hdb[D], wb_flip(z.hdb[t2]));  // for the t1 field component
   const double hSe = __fma_rn(z.Bv[D], z.hdb[D], __fma_rn(z.Bv[t1], hm1, __dmul_rn(z.Bv[t2], hm2)));
   const double c1 = z.c[t1], c2 = z.c[t2];
   double u[8];
