@@ -53,11 +53,11 @@ FLOPS_PER_FACE = 480.0
 # (profiles/k_sweep_256cube_dram.md); the algorithmic figure is 128 B per face.
 SWEEP_DRAM_BYTES_256 = 3.683e9
 SWEEP_BYTES_PER_FACE = 128.0
-# FP64 flops of the other stages of a step per zone: 448 from the ncu counters
+# FP64 flops of the other stages of a step per zone: 428 from the ncu counters
 # of the corner EMFs, CT, transverse states, half-step EMF and update kernels
 # on the 96^3 box (profiles/stages_96cube_ncu_full.md), plus 18 for the
 # reference EMF (its source: one reciprocal, three products, three pairs).
-STAGE_FLOPS_PER_ZONE = 466.0
+STAGE_FLOPS_PER_ZONE = 446.0
 # algorithmic state bytes per cell-update: 5 conserved fields and 3 face fields
 # read and written once (the step's HBM roofline)
 STEP_BYTES_PER_CELL = 128.0
