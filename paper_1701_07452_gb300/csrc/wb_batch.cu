@@ -589,12 +589,12 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
 // persistent kernel every stage keeps the sweep's 4 blocks of 64 threads per
 // SM).  All stage arithmetic is written with explicit rounding, so both forms
 // compute the same bits.
-enum { SC_SWEEP = 0, SC_COPY, SC_PAIR, SC_TRANS, SC_EREF_H, SC_FINAL, SC_DT, SC_COUNT };
+enum { SC_SWEEP = 0, SC_COPY, SC_EMF, SC_TRANS, SC_EREF_H, SC_FINAL, SC_DT, SC_COUNT };
 
 __host__ __device__ inline int stage_class(int s) {
   if (stage_is_sweep(s)) return SC_SWEEP;
   if (s == BS_HALO || stage_is_wrap(s)) return SC_COPY;  // copies of up to 24 arrays
-  if (stage_pairs(s)) return SC_PAIR;                    // reference EMF, corner EMFs, CT (one item a thread)
+  if (stage_pairs(s)) return SC_EMF;                    // reference EMF, corner EMFs, CT (one item a thread)
   if (s == BS_TRANS) return SC_TRANS;
   if (s == BS_EREF_H) return SC_EREF_H;
   if (s == BS_FINAL) return SC_FINAL;
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(kNtZone, zone_min_blocks(CLS))
         unit_pair_copy(s, bi, it, it + NT < i1 ? it + NT : -1);
       return;
     }
-    if (CLS == SC_PAIR) {
+    if (CLS == SC_EMF) {
       for (long long it = i0 + threadIdx.x; it < i1; it += NT) unit_emf(s, d, bi, it, dt);
       return;
     }
@@ -1003,7 +1003,7 @@ const void* bstage_sweep_kernel(const WbPhys& ph) {
 const void* bstage_zone_kernel(int cls) {
   switch (cls) {
     case SC_COPY: return (const void*)k_bstage_zone<SC_COPY>;
-    case SC_PAIR: return (const void*)k_bstage_zone<SC_PAIR>;
+    case SC_EMF: return (const void*)k_bstage_zone<SC_EMF>;
     case SC_TRANS: return (const void*)k_bstage_zone<SC_TRANS>;
     case SC_EREF_H: return (const void*)k_bstage_zone<SC_EREF_H>;
     case SC_FINAL: return (const void*)k_bstage_zone<SC_FINAL>;
