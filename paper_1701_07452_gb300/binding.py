@@ -330,9 +330,10 @@ class Grid:
 
 
 class Batch:
-    """Many independent single-patch boxes advanced by one persistent kernel
-    (wb_batch_* of the C ABI).  boxes: list of dicts with keys n, length and
-    optional bc; physics keywords are shared by every box."""
+    """Many independent single-patch boxes advanced together, by one
+    persistent kernel or by one launch per stage (set_form), each with its own
+    dt (wb_batch_* of the C ABI).  boxes: list of dicts with keys n, length
+    and optional bc; physics keywords are shared by every box."""
 
     def __init__(self, boxes, work_budget=0, stream=None, **kw):
         import torch
