@@ -20,9 +20,10 @@
 //                             (Eqs. for u-bar of the HLL scheme, b+ and b-)
 // Readings where the paper is silent are tagged R1..R21 as in the design notes.
 //
-// Parity unpinned: the sign and size of the div B source term of Steps 5 and 7
-// (reading R13, after GS08, which is not available).  Tests pin only that it
-// vanishes for data varying along one axis and acts on oblique data.
+// Parity unpinned: the energy and induction parts of the div B source term of
+// Steps 5 and 7 (reading R13, after GS08, which is not available); tests pin
+// only that they vanish for data varying along one axis and act on oblique
+// data.  Its momentum part is pinned to the flux derivative it supplies.
 
 #include "mhd_oracle.h"
 

@@ -266,3 +266,50 @@ def test_div_b_source_is_multi_dimensional_only(oracle_mod):
         runs.append(g.read())
     diff = max(np.abs(a - b).max() for a, b in zip(*runs))
     assert diff > 1e-10
+
+
+def test_div_b_source_momentum_is_the_missing_flux_derivative(oracle_mod):
+    """The momentum part of the div B source of the transverse states (Steps
+    5, 7; reading R13) against the physics it must supply: a sweep along d
+    solves the 7-variable system with B_d held fixed (its energy variable
+    referred to the normal field, E - B_d^2/2: reading R4), so the term its
+    flux leaves out of dM/dt is -(dF_d[M]/dB_d) (db_d/dx_d), with dF_d/dB_d
+    the complex-step derivative of the paper's flux vector (Sec. 3, written
+    out in linear_waves._flux) at fixed (rho, M, E - B_d^2/2, B_t).  The
+    source is isolated as the difference of the oracle's q^{n+1/2}_d with the
+    source on and off (a test ablation), so a wrong sign or size of the
+    momentum source, or a difference taken along the wrong axis, fails here.
+    (The energy and induction parts follow GS08's minmod choices, which this
+    does not fix.)"""
+    n = (8, 8, 8)
+    st = random_box(n, seed=31)
+    g0 = oracle_mod.Grid(n, st["length"])
+    g0.load_state(st)
+    U, bx, by, bz, B = g0.read()
+    dt = g0.dt()
+    dumps = []
+    for s in (1.0, 0.0):
+        g = oracle_mod.Grid(n, st["length"])
+        g.load_state(st)
+        g.set_source_scale(s)
+        assert g.step(dt) == 0
+        dumps.append([g.stage(9 + d).reshape(8, n[2], n[1], n[0]) for d in range(3)])
+    dx = [st["length"][a] / n[a] for a in range(3)]
+    db = [np.diff(bx, axis=2) / dx[0], np.diff(by, axis=1) / dx[1], np.diff(bz, axis=0) / dx[2]]
+    rho, M, E = U[0], U[1:4], U[4]
+    worst = 0.0
+    for d in range(3):
+        t1, t2 = (d + 1) % 3, (d + 2) % 3
+        S = (dumps[0][d] - dumps[1][d]) / (0.5 * dt)
+        h = 1e-30
+        bn = B[d] + 1j * h
+        eref = E - 0.5 * B[d] ** 2                             # held fixed
+        u = [rho, M[d], M[t1], M[t2], B[t1], B[t2], eref + 0.5 * bn * bn]
+        dF = lw._flux(u, bn, lw.GAMMA).imag / h   # d F_d / d B_d, rows (rho, Md, Mt1, Mt2, ...)
+        for row, comp in ((1, d), (2, t1), (3, t2)):
+            want = -dF[row] * db[d]
+            got = S[1 + comp]
+            scale = np.abs(want).max()
+            assert scale > 1e-4
+            worst = max(worst, np.abs(got - want).max() / scale)
+    assert worst < 1e-8, worst
