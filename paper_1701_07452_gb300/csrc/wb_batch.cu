@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -1083,6 +1084,8 @@ bool phys_ok(const wb_desc& d) {
   for (int k = 0; k < 7; ++k)
     if (!(d.eps[k] >= 0.0) || !(d.eps[k] < 0.5)) return false;
   if (!(d.prot_rho >= 0.0) || !(d.prot_p >= 0.0)) return false;
+  if (!(d.rho_floor >= 0.0) || !(d.p_floor >= 0.0) || !std::isfinite(d.rho_floor) || !std::isfinite(d.p_floor))
+    return false;
   return d.sweby_beta >= 1.0 && d.sweby_beta <= 2.0;
 }
 

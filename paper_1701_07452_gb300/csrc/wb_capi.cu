@@ -92,6 +92,11 @@ bool valid_desc(const wb_desc* d, std::string* why) {
     *why = "protection floors must be >= 0";
     return false;
   }
+  if (!(d->rho_floor >= 0.0) || !(d->p_floor >= 0.0) || !std::isfinite(d->rho_floor) ||
+      !std::isfinite(d->p_floor)) {
+    *why = "floors must be finite and >= 0";
+    return false;
+  }
   return true;
 }
 

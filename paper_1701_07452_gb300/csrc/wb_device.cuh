@@ -181,6 +181,22 @@ __device__ __forceinline__ bool wb_neg(double x) {
   const unsigned long long m = (unsigned long long)b << 1;  // |x| bits, shifted (see wb_abs_less)
   return b < 0 && m != 0 && m <= 0xffe0000000000000ULL;
 }
+// x is finite (exponent field not all ones; tested on the high word)
+__device__ __forceinline__ bool wb_finite(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
+}
+// x < f for a floor f that is finite and >= +0: exact for every x, false
+// for NaN (the bit patterns of non-negative doubles order as their values;
+// an FP64 compare costs an FP64-pipe instruction on this GPU)
+__device__ __forceinline__ bool wb_below_floor(double x, double f) {
+  const long long bx = __double_as_longlong(x), bf = __double_as_longlong(f);
+  if (bx < 0) {
+    const unsigned long long m = (unsigned long long)bx << 1;
+    if (m > 0xffe0000000000000ULL) return false;  // NaN
+    return m != 0 || bf != 0;                      // x < 0 < ... ; -0 < f unless f = +0
+  }
+  return bx < bf;                                  // NaN (bx > inf >= bf) gives false
+}
 // x is a positive normal finite double (>= 2^-1022; false for subnormals,
 // zero, negatives, inf and NaN)
 __device__ __forceinline__ bool wb_normal_pos(double x) {

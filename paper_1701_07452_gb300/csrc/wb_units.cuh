@@ -941,20 +941,21 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
     B[e] = wb_half(__dadd_rn(v.b[e][q], v.b[e][q + s[e]]));
     v.q[F_BX + e][q] = B[e];
   }
-  if (u[0] < P.rho_floor) { u[0] = P.rho_floor; ++*hits; }
+  // the tests below run on the integer pipe (FP64 compares take FP64 issue)
+  if (wb_below_floor(u[0], P.rho_floor)) { u[0] = P.rho_floor; ++*hits; }
   const double ir = wb_rcp(u[0]);
   const double m[3] = {u[1], u[2], u[3]};
   const double vv[3] = {__dmul_rn(u[1], ir), __dmul_rn(u[2], ir), __dmul_rn(u[3], ir)};
   const double ke = kinetic(m, vv);
   const double me = wb_half(__fma_rn(B[2], B[2], __fma_rn(B[1], B[1], __dmul_rn(B[0], B[0]))));
   double p = __dmul_rn(P.gm1, __dsub_rn(__dsub_rn(u[4], ke), me));
-  if (p < P.p_floor) {
+  if (wb_below_floor(p, P.p_floor)) {
     u[4] = __dadd_rn(__fma_rn(P.p_floor, P.inv_gm1, ke), me);
     p = __dmul_rn(P.gm1, __dsub_rn(__dsub_rn(u[4], ke), me));
     ++*hits;
   }
-  const bool fin = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]) &&
-                   isfinite(u[4]) && u[0] > 0.0 && isfinite(p);
+  const bool fin = wb_pos(u[0]) && wb_finite(u[1]) && wb_finite(u[2]) && wb_finite(u[3]) &&
+                   wb_finite(u[4]) && wb_finite(p);
 #pragma unroll
   for (int c = 0; c < 5; ++c) v.q[c][q] = u[c];
   if (!fin) {

@@ -85,6 +85,8 @@ def test_descriptor_edge_cases_rejected_without_gpu():
         dict(n=(8, 8, 8), bc=(0, 2, 0)),
         dict(n=(8, 8, 8), batch_patches=-1),
         dict(n=(8, 8, 8), prot_rho=-1.0),
+        dict(n=(8, 8, 8), rho_floor=-1.0),
+        dict(n=(8, 8, 8), p_floor=float("nan")),
         dict(n=(20000, 20000, 20000)),            # beyond any device: refused, no overflow
     ]
     for kw in bad:
