@@ -14,10 +14,19 @@ e2e        the same metric through the C ABI with host buffers: every step
            loads the state from pinned host memory, advances one step and
            reads the state back (copies inside the timed region).
 roofline   the MHDTVD sweep kernel against the FP64 pipe (the step is FP64
-           bound): algorithmic flops per face x faces per launch / measured
-           launch time, peak = FP64 DFMA probe run in this process.
+           bound): algorithmic flops per face (the oracle's instrumented
+           count, oracle/count_flops.py) x faces per launch / measured launch
+           time; peak = SMs x 4 FP64 flops per clock x the SM clock sampled
+           under load.  The kernel's own executed flops (ncu FP64 counters)
+           are reported beside it as "executed".
 cpu_baseline  the plain FP64 oracle timed on the host cores on a bounded
-           sample of the same workload.
+           sample of the same workload (all cores, and one core).
+batch      the ensemble workload: a seeded subset of the 1000 boxes of edges
+           {16..128}, 100 steps each, advanced in shared launches, against the
+           same boxes one at a time through the single-box path.
+serve      the serving workload: Poisson arrivals (50/s) of turbulence runs of
+           edge log-uniform 32..192 and U{50..500} steps under a 150 GB state
+           budget; p50/p99 time to completion.
 
 --impl reference times the oracle (the slow CPU reading of the paper) as the
 reference arm.  --gpus N > 1 runs N independent replicas of the box, one per
@@ -26,6 +35,7 @@ rank (the path has no data exchange between GPUs).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -42,28 +52,65 @@ METRIC = "FP64 cell-updates/s"
 UNIT = "cell-updates/s"
 N_BOX = 256
 SEED = 2
-# FP64 flops (DFMA = 2, DMUL = DADD = 1) the MHDTVD sweep executes per interface
-# system it computes, from the ncu FP64 instruction counters of k_sweep on the
-# 96^3 corrector x-sweep (profiles/k_sweep_96cube_ncu_full.md): 470 M flops over
-# the 978,944 interface systems of that launch (884,736 interior faces plus the
-# two overlap faces of every warp's segments).
-FLOPS_PER_FACE = 480.0
-# DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the mean
-# of the six sweeps of a step from one ncu capture of this kernel
-# (profiles/k_sweep_256cube_dram.md); the algorithmic figure is 128 B per face.
-SWEEP_DRAM_BYTES_256 = 3.683e9
+# Algorithmic FP64 operations of the method: the oracle's instrumented count
+# (oracle/count_flops.py 64 2 2: the turbulence data at 64^3, steps 2-3;
+# add/sub/mul/div/sqrt = 1, identity operations of its dense 7x7 matrices not
+# counted), per sweep face (zone state and flux, Roe state and eigen-system,
+# alpha_k, g-tilde, limiter, emitted flux) and per cell-update (six sweep
+# faces plus every other stage of the step); profiles/oracle_flop_count.md.
+ALG_FLOPS_PER_FACE = 879.0
+ALG_FLOPS_PER_CELL_UPDATE = 5871.0
+# FP64 flops (DFMA = 2, DMUL = DADD = 1) the kernels execute, from ncu FP64
+# instruction counters: per interface system of k_sweep, and per zone of the
+# other stage kernels together (profiles/k_sweep_96cube_ncu_full.md,
+# profiles/stages_96cube_ncu_full.md).
+EXEC_FLOPS_PER_FACE = 480.0
+EXEC_STAGE_FLOPS_PER_ZONE = 446.0
+# DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the
+# mean of the six sweeps of a step from one ncu capture
+# (profiles/k_sweep_256cube_dram.md), valid only for the kernel sources it was
+# taken on (their SHA-256 over csrc/wb_sweep.cu, wb_units.cuh, wb_device.cuh);
+# the algorithmic figure is 128 B per face.
+SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.683e9, "src_sha256": ""}
 SWEEP_BYTES_PER_FACE = 128.0
-# FP64 flops of the other stages of a step per zone: 428 from the ncu counters
-# of the corner EMFs, CT, transverse states, half-step EMF and update kernels
-# on the 96^3 box (profiles/stages_96cube_ncu_full.md), plus 18 for the
-# reference EMF (its source: one reciprocal, three products, three pairs).
-STAGE_FLOPS_PER_ZONE = 446.0
 # algorithmic state bytes per cell-update: 5 conserved fields and 3 face fields
 # read and written once (the step's HBM roofline)
 STEP_BYTES_PER_CELL = 128.0
 # FP64 issue rate of one GB300 SM: 2 DFMA per clock (measured with the DFMA
 # probe: 1196 GFLOP/s at 1995 MHz on 152 SMs), i.e. 4 flops per clock per SM.
 FP64_FLOPS_PER_CLK_PER_SM = 4.0
+
+
+def sweep_src_sha256():
+    """SHA-256 over the sweep kernel's sources (the DRAM capture's stamp)."""
+    h = hashlib.sha256()
+    for name in ("wb_sweep.cu", "wb_units.cuh", "wb_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1701_07452_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def sweep_traffic(n):
+    """Measured DRAM bytes per sweep launch, or None when no capture of the
+    current kernel at this size exists."""
+    cap = SWEEP_DRAM_CAPTURE
+    if cap["n"] == n and cap["src_sha256"] == sweep_src_sha256():
+        return cap["bytes"]
+    return None
+
+
+def cpu_model():
+    """Host CPU model name (lscpu), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except Exception:
+        pass
+    return None
 
 
 def step_launches(desc):
@@ -95,21 +142,29 @@ def l2_note(n):
 def step_roofline(value, fp64_peak_tflops):
     """The whole step against the slower of its two ceilings: FP64 flops per
     cell-update at the FP64 peak, and its state bytes at the measured HBM
-    copy bandwidth."""
+    copy bandwidth.  The FP64 ceiling is taken with the algorithmic count
+    (the oracle's operations) and, as "executed", with the kernels' own."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             hbm = float(json.load(f)["hbm_gbs"])
         src = "MEASURED_PEAKS.json (measured copy)"
     except (OSError, KeyError, ValueError):
         hbm, src = 6800.0, "fallback 6.8 TB/s"
-    flops = 6 * FLOPS_PER_FACE + STAGE_FLOPS_PER_ZONE
-    fp64_rate = fp64_peak_tflops * 1e12 / flops
     hbm_rate = hbm * 1e9 / STEP_BYTES_PER_CELL
-    bound = min(fp64_rate, hbm_rate)
-    return {"bound": "fp64" if fp64_rate <= hbm_rate else "hbm", "unit": UNIT,
-            "fp64_rate": fp64_rate, "hbm_rate": hbm_rate, "frac": value / bound,
-            "flops_per_cell_update": flops, "bytes_per_cell_update": STEP_BYTES_PER_CELL,
-            "hbm_gbs": hbm, "hbm_source": src, "hbm_frac": value * STEP_BYTES_PER_CELL / (hbm * 1e9)}
+
+    def ceiling(flops):
+        fp64_rate = fp64_peak_tflops * 1e12 / flops
+        bound = min(fp64_rate, hbm_rate)
+        return {"bound": "fp64" if fp64_rate <= hbm_rate else "hbm", "fp64_rate": fp64_rate,
+                "frac": value / bound, "flops_per_cell_update": flops}
+
+    exec_flops = 6 * EXEC_FLOPS_PER_FACE + EXEC_STAGE_FLOPS_PER_ZONE
+    out = ceiling(ALG_FLOPS_PER_CELL_UPDATE)
+    out.update({"flops_kind": "algorithmic (oracle count)", "unit": UNIT, "hbm_rate": hbm_rate,
+                "bytes_per_cell_update": STEP_BYTES_PER_CELL, "hbm_gbs": hbm, "hbm_source": src,
+                "hbm_frac": value * STEP_BYTES_PER_CELL / (hbm * 1e9),
+                "executed": ceiling(exec_flops)})
+    return out
 
 
 def sweep_faces_per_step(n):
@@ -243,144 +298,194 @@ def run_reference(args, world, rank):
     return 0
 
 
-def run_mode(args):
-    """Secondary workloads, one JSON line each (not the headline line)."""
+def ensemble_boxes(nbox):
+    """The first nbox boxes of the seeded 1000-box ensemble: edges drawn from
+    {16, 24, 32, 48, 64, 96, 128} (seed 4), random data of seed 4000 + b."""
     import numpy as np
+    from paper_1701_07452_gb300.initial_conditions import random_box
+    rng = np.random.default_rng(4)
+    edges = rng.choice([16, 24, 32, 48, 64, 96, 128], size=1000)[:nbox]
+    states = [random_box(int(e), seed=4000 + b) for b, e in enumerate(edges)]
+    boxes = [{"n": (int(e),) * 3, "length": st["length"]} for e, st in zip(edges, states)]
+    return edges, boxes, states
+
+
+def batch_figures(nbox, steps, form="auto", other_form=True, oracle_boxes=0):
+    """Batched vs one-box-at-a-time solves/s on the ensemble subset (CUDA
+    events; a solve is one box advanced `steps` steps).  oracle_boxes > 0
+    also checks that many of the smallest boxes against the FP64 oracle."""
     import torch
 
     from paper_1701_07452_gb300 import binding as wb
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import state_err
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    edges, boxes, states = ensemble_boxes(nbox)
+    if form == "auto":
+        tune = wb.Batch(boxes)
+        for i, st in enumerate(states):
+            tune.load_state(i, st)
+        tune.set_steps(-1, 1000)
+        tune.autotune(trial_steps=1)
+        cfg = tune.get_config()
+        del tune
+    bt = wb.Batch(boxes)
+    if form != "auto":
+        bt.set_form(form)
+    else:
+        bt.config(seg_len=cfg["seg_len"], blocks_per_sm=cfg["blocks_per_sm"])
+        bt.set_form(cfg["form"])
+    cfg = bt.get_config()
+    for i, st in enumerate(states):
+        bt.load_state(i, st)
+    bt.set_steps(-1, 1)
+    bt.advance(1, use_graph=True)       # graph capture + warm-up step
+    for i, st in enumerate(states):
+        bt.load_state(i, st)
+    bt.set_steps(-1, steps)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    bt.advance(steps, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    assert all(bt.counters(i)["steps"] == steps for i in range(nbox))
+    out = {}
+    if oracle_boxes:
+        import oracle
+        oracle.set_threads(os.cpu_count() or 1)
+        order = sorted(range(nbox), key=lambda i: int(edges[i]))[:oracle_boxes]
+        worst = 0.0
+        for i in order:
+            o = oracle.Grid(boxes[i]["n"], boxes[i]["length"])
+            o.load_state(states[i])
+            o.advance(steps)
+            worst = max(worst, state_err(bt.read(i), o.read()))
+        out["oracle_check"] = {"boxes": [int(edges[i]) for i in order], "steps": steps,
+                               "max_rel_err": worst, "tolerance": 1e-8}
+    if other_form:
+        other = "staged" if cfg["form"] == "persistent" else "persistent"
+        bt.set_form(other)
+        for i, st in enumerate(states):
+            bt.load_state(i, st)
+        bt.set_steps(-1, 1)
+        bt.advance(1, use_graph=True)
+        for i, st in enumerate(states):
+            bt.load_state(i, st)
+        bt.set_steps(-1, steps)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bt.advance(steps, use_graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["other_form"] = {"form": other, "solves_per_s": nbox / (e0.elapsed_time(e1) * 1e-3)}
+        bt.set_form(cfg["form"])
+        # per-stage breakdown of the chosen form (stage timer, no graph), one
+        # more step of every box, outside the timed region
+        bt.set_steps(-1, 1)
+        bt.stage_timer(True)
+        bt.advance(1, use_graph=False)
+        out["stage_ms_one_step"] = {k: round(v, 3) for k, v in bt.stage_times().items()}
+        bt.stage_timer(False)
+    del bt
+    # the plain path: one box at a time through the single-box API, each
+    # after one untimed warm-up step
+    t_plain = 0.0
+    for b, st in zip(boxes, states):
+        g = wb.Grid(b["n"], length=b["length"])
+        g.load_state(st)
+        g.advance(1)
+        g.load_state(st)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.advance(steps, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_plain += e0.elapsed_time(e1) * 1e-3
+        del g
+    torch.cuda.empty_cache()
+    cells = float(sum(int(e) ** 3 for e in edges)) * steps
+    res = {"solves_per_s": nbox / t_batch, "plain_solves_per_s": nbox / t_plain,
+           "speedup": t_plain / t_batch, "batched_cell_updates_per_s": cells / t_batch,
+           "plain_cell_updates_per_s": cells / t_plain, "steps": steps, "boxes": nbox,
+           "form": cfg, "workload": f"the first {nbox} of the 1000 ensemble boxes (edges from "
+                                    f"{{16..128}}, seed 4; random data seed 4000+b), {steps} steps "
+                                    "each; a solve = one box x all its steps"}
+    res.update(out)
+    return res
+
+
+def serve_figures(requests, steps_scale=1.0, policies=("srpt",)):
+    """Serving run of the request stream: p50/p99 time from arrival to
+    completion and cell-updates/s, per tick policy (the first is the line's)."""
+    import numpy as np
+    import torch
+
     from paper_1701_07452_gb300 import serve as sv
-    from paper_1701_07452_gb300.initial_conditions import (random_box, turbulence_box,
-                                                           turbulence_box_device)
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box_device
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rng = np.random.default_rng(5)
+    gaps = rng.exponential(1.0 / 50.0, size=requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    ns = np.rint(np.exp(rng.uniform(np.log(32), np.log(192), size=requests))).astype(int)
+    nsteps = np.maximum(1, np.rint(rng.integers(50, 501, size=requests) * steps_scale)).astype(int)
+    reqs = []
+    for r in range(requests):
+        st = turbulence_box_device(int(ns[r]), 5000 + r, dev)
+        st = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in st.items()}
+        reqs.append(sv.Request(r, float(arrivals[r]), (int(ns[r]),) * 3, int(nsteps[r]), st))
+    runs = {}
+    for policy in policies:
+        srv = sv.Server(state_bytes=150 << 30, work_bytes=40 << 30, max_boxes=requests,
+                        max_n=int(ns.max()), tick_steps=5, policy=policy, tick_cells=1.5e8)
+        recs = srv.run(reqs)
+        runs[policy] = (sv.summarize(recs), srv.ticks)
+        del srv
+        torch.cuda.empty_cache()
+    summ, ticks = runs[policies[0]]
+    res = {"cell_updates_per_s": summ["cell_updates_per_s"], "p50_s": summ["p50_s"],
+           "p99_s": summ["p99_s"], "solves_per_s": summ["solves_per_s"],
+           "completed": summ["completed"], "failed": summ["failed"], "wall_s": summ["wall_s"],
+           "ticks": ticks, "policy": policies[0],
+           "workload": f"{requests} requests, Poisson 50/s (seed 5), edge log-uniform 32..192, "
+                       f"steps U{{50..500}}" + (f" x {steps_scale}" if steps_scale != 1.0 else "") +
+                       ", turbulence data seed 5000+r, 150 GB state budget, 5 steps per tick "
+                       "(srpt: least remaining work first, up to 1.5e8 cell-updates per tick)"}
+    for policy in policies[1:]:
+        o = runs[policy][0]
+        res[policy] = {"cell_updates_per_s": o["cell_updates_per_s"], "p50_s": o["p50_s"],
+                       "p99_s": o["p99_s"]}
+    return res
+
+
+def run_mode(args):
+    """Secondary workloads, one JSON line each (not the headline line)."""
+    import torch
+
+    from paper_1701_07452_gb300 import binding as wb
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box_device
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
     if args.mode == "batch":
-        # ensemble: boxes of edge drawn from {16,...,128} (seed 4), data seed 4000+b
-        rng = np.random.default_rng(4)
-        edges = rng.choice([16, 24, 32, 48, 64, 96, 128], size=args.nbox)
-        states = [random_box(int(e), seed=4000 + b) for b, e in enumerate(edges)]
-        boxes = [{"n": (int(e),) * 3, "length": st["length"]} for e, st in zip(edges, states)]
-        steps = args.steps
-        if args.form == "auto":
-            tune = wb.Batch(boxes)
-            for i, st in enumerate(states):
-                tune.load_state(i, st)
-            tune.set_steps(-1, 1000)
-            tune.autotune(trial_steps=1)
-            cfg = tune.get_config()
-            del tune
-        bt = wb.Batch(boxes)
-        if args.form != "auto":
-            # a given form with the default segment length and block count
-            bt.set_form(args.form)
-            cfg = bt.get_config()
-        for i, st in enumerate(states):
-            bt.load_state(i, st)
-        bt.set_steps(-1, steps)
-        bt.advance(1, use_graph=True)       # capture + warm-up step
-        bt.set_steps(-1, steps)
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        bt.advance(steps, use_graph=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_batch = e0.elapsed_time(e1) * 1e-3
-        # the other form (persistent kernel / one launch per stage) with the
-        # same segment length and block count, for comparison
-        other = "staged" if cfg["form"] == "persistent" else "persistent"
-        bt.set_form(other)
-        bt.set_steps(-1, 1)
-        bt.advance(1, use_graph=True)
-        bt.set_steps(-1, steps)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        bt.advance(steps, use_graph=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_other = e0.elapsed_time(e1) * 1e-3
-        bt.set_form(cfg["form"])
-        # per-stage breakdown of the tuned form (stage timer, no graph), one
-        # more step of every box, outside the timed region
-        bt.set_steps(-1, 1)
-        bt.stage_timer(True)
-        bt.advance(1, use_graph=False)
-        stage_ms = {k: round(v, 3) for k, v in bt.stage_times().items()}
-        bt.stage_timer(False)
-        # the plain path: one box at a time through the single-grid API
-        t_plain = 0.0
-        worst = 0.0
-        sys.path.insert(0, os.path.join(ROOT, "tests"))
-        from parity import state_err
-        for i, (b, st) in enumerate(zip(boxes, states)):
-            g = wb.Grid(b["n"], length=b["length"])
-            g.load_state(st)
-            g.advance(1)
-            g.load_state(st)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            g.advance(steps + 1, sync=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_plain += e0.elapsed_time(e1) * 1e-3 * steps / (steps + 1)
-            if i < 8:
-                ref = wb.Batch([b])
-                ref.load_state(0, st)
-                ref.set_steps(0, steps + 1)
-                ref.advance(steps + 1)
-                worst = max(worst, state_err(ref.read(0), g.read()))
-            del g
-        cells = float(sum(int(e) ** 3 for e in edges)) * steps
+        r = batch_figures(args.nbox, args.batch_steps, form=args.form, other_form=True,
+                          oracle_boxes=4)
         line = {"metric": "solves/s (batched vs one box at a time)", "mode": "batch",
-                "value": args.nbox / t_batch, "unit": "solves/s", "higher_is_better": True,
-                "plain_solves_per_s": args.nbox / t_plain, "speedup": t_plain / t_batch,
-                "batched_cell_updates_per_s": cells / t_batch, "plain_cell_updates_per_s": cells / t_plain,
-                "steps": steps, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"{args.nbox} periodic boxes, edges from {{16..128}} (seed 4), "
-                                       f"random data seed 4000+b, {steps} steps each (solve = one box x "
-                                       f"{steps} steps)", "autotuned" if args.form == "auto" else "given": cfg},
-                "other_form": {"form": other, "solves_per_s": args.nbox / t_other},
-                "batch_vs_grid_max_rel_err": worst,
-                "stage_ms_one_step": stage_ms}
+                "value": r.pop("solves_per_s"), "unit": "solves/s", "higher_is_better": True,
+                "dtype": "f64", "data": "synthetic", "config": {"workload": r.pop("workload")}}
+        line.update(r)
         print(json.dumps(line), flush=True)
         return 0
     if args.mode == "serve":
-        rng = np.random.default_rng(5)
-        gaps = rng.exponential(1.0 / 50.0, size=args.requests)
-        arrivals = np.cumsum(gaps) - gaps[0]
-        ns = np.rint(np.exp(rng.uniform(np.log(32), np.log(192), size=args.requests))).astype(int)
-        nsteps = np.maximum(1, np.rint(rng.integers(50, 501, size=args.requests) * args.steps_scale)).astype(int)
-        reqs = []
-        for r in range(args.requests):
-            st = turbulence_box_device(int(ns[r]), 5000 + r, dev)
-            st = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in st.items()}
-            reqs.append(sv.Request(r, float(arrivals[r]), (int(ns[r]),) * 3, int(nsteps[r]), st))
-        # least-remaining-work ticks (srpt) as the served form; processor
-        # sharing (fair) on the same stream for comparison
-        runs = {}
-        for policy in ("srpt", "fair"):
-            srv = sv.Server(state_bytes=150 << 30, work_bytes=40 << 30, max_boxes=args.requests,
-                            max_n=int(ns.max()), tick_steps=5, policy=policy, tick_cells=1.5e8)
-            recs = srv.run(reqs)
-            runs[policy] = (sv.summarize(recs), srv.ticks)
-            del srv
-            torch.cuda.empty_cache()
-        summ, ticks = runs["srpt"]
-        fair = runs["fair"][0]
+        r = serve_figures(args.requests, args.steps_scale, policies=("srpt", "fair"))
         line = {"metric": "serving p50/p99 completion latency and cell-updates/s", "mode": "serve",
-                "value": summ["cell_updates_per_s"], "unit": "cell-updates/s", "higher_is_better": True,
-                "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "solves_per_s": summ["solves_per_s"],
-                "completed": summ["completed"], "failed": summ["failed"],
-                "wall_s": summ["wall_s"], "ticks": ticks, "dtype": "f64", "data": "synthetic",
-                "policy": "srpt: each tick grants up to 5 steps to the runs with the least remaining "
-                          "work until 1.5e8 cell-updates",
-                "fair": {"value": fair["cell_updates_per_s"], "p50_s": fair["p50_s"], "p99_s": fair["p99_s"],
-                         "policy": "every resident run advances 5 steps per tick"},
-                "config": {"workload": f"{args.requests} requests, Poisson 50/s (seed 5), edge "
-                                       f"log-uniform 32..192, steps U{{50..500}} x {args.steps_scale}, "
-                                       "turbulence data seed 5000+r, 150 GB state budget, 5 steps per tick"}}
+                "value": r.pop("cell_updates_per_s"), "unit": "cell-updates/s",
+                "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": r.pop("workload")}}
+        line.update(r)
         print(json.dumps(line), flush=True)
         return 0
     if args.mode in ("patches", "big"):
@@ -455,13 +560,17 @@ def main():
                     help="box: the 256^3 box (default line); batch: ensemble of boxes, batched vs "
                          "one at a time; serve: request stream; patches: 512^3 in 64^3 patches vs "
                          "the single grid; big: 768^3 in 12^3 patches")
-    ap.add_argument("--nbox", type=int, default=64)
+    ap.add_argument("--nbox", type=int, default=48,
+                    help="batch: boxes of the ensemble (the first nbox of the seeded 1000)")
+    ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without the batch and serving figures")
     ap.add_argument("--form", default="auto", choices=["auto", "persistent", "staged"],
                     help="batch mode: the autotuned form, or a given one without autotuning")
     ap.add_argument("--ref-sample", type=int, default=128,
                     help="reference arm: edge of the box the oracle steps per bench step")
-    ap.add_argument("--requests", type=int, default=40)
-    ap.add_argument("--steps-scale", type=float, default=0.1)
+    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--steps-scale", type=float, default=1.0)
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -531,16 +640,31 @@ def main():
     # ---- CPU baseline: oracle on a bounded sample -------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the workload itself, two steps (10-20 s on the host cores)
+        # the workload itself, two steps (10-20 s on the host cores), and one
+        # step of a 64^3 box of the same data on one core (a few seconds)
         steps_s = 2
         v, wall, used = cpu_sample(n, steps_s, st=st)
+        v1, wall1, _ = cpu_sample(64, 1, threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
-               "sample": f"{steps_s} steps of the {n}^3 box itself ({wall:.1f} s)"}
+               "sample": f"{steps_s} steps of the {n}^3 box itself ({wall:.1f} s)",
+               "one_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"1 step of a 64^3 box of the same data ({wall1:.1f} s)"},
+               "cpu_model": cpu_model()}
+        import oracle
+        oracle.set_threads(os.cpu_count() or 1)
+
+    # ---- batched and served workloads (rank 0 of a 1-GPU run) -------------
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras["batch"] = batch_figures(args.nbox, args.batch_steps, other_form=False,
+                                        oracle_boxes=3)
+        extras["serve"] = serve_figures(args.requests, args.steps_scale)
 
     if rank == 0:
         per_launch_ms = sweep_ms / max(sweep_launches, 1)
         faces_per_launch = sweep_faces_per_step(n) / 6.0
-        achieved = FLOPS_PER_FACE * faces_per_launch / (per_launch_ms * 1e-3) / 1e12
+        achieved = ALG_FLOPS_PER_FACE * faces_per_launch / (per_launch_ms * 1e-3) / 1e12
+        achieved_exec = EXEC_FLOPS_PER_FACE * faces_per_launch / (per_launch_ms * 1e-3) / 1e12
         clk_summary = clk.summary()
         sm_mhz = clk_summary["sm_mhz"] or 2070.0
         props = torch.cuda.get_device_properties(dev)
@@ -558,11 +682,17 @@ def main():
                     "steps": args.e2e_steps},
             "roofline": {"bound": "alu", "kernel": "k_sweep (MHDTVD flux)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": SWEEP_DRAM_BYTES_256 if n == 256 else None,
+                         "traffic": sweep_traffic(n),
                          "algorithmic_bytes": SWEEP_BYTES_PER_FACE * faces_per_launch,
-                         "flops_per_face": FLOPS_PER_FACE,
-                         "peak_source": "SMs x 2 DFMA/clk x 2 flops x median SM clock under load; "
-                                        "DFMA probe in this process: %.3f TFLOP/s" % (fp64_peak / 1e12),
+                         "flops_per_face": ALG_FLOPS_PER_FACE,
+                         "flops_kind": "algorithmic: the oracle's FP64 operations per face "
+                                       "(instrumented scalar, oracle/count_flops.py)",
+                         "executed": {"flops_per_face": EXEC_FLOPS_PER_FACE, "achieved": achieved_exec,
+                                      "frac": achieved_exec / peak,
+                                      "source": "ncu FP64 instruction counters of k_sweep, DFMA = 2"},
+                         "peak_source": "nominal: SMs x 2 DFMA/clk x 2 flops x median SM clock "
+                                        "under load; DFMA probe in this process: %.3f TFLOP/s"
+                                        % (fp64_peak / 1e12),
                          "sweep_ms_per_launch": per_launch_ms,
                          "sweep_share_of_step": sweep_ms / ms},
             "step_roofline": step_roofline(value, peak),
@@ -570,6 +700,7 @@ def main():
             "clocks": clk_summary,
             "gpu_launches": launches_per_step * args.steps,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -21,31 +21,37 @@ _SRC = os.path.join(_HERE, "mhd_oracle.cpp")
 _HDR = os.path.join(_HERE, "mhd_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libmhd_oracle.so")
+_LIB_COUNT = os.path.join(_BUILD, "libmhd_oracle_count.so")
+_CNT_HDR = os.path.join(_HERE, "flop_count.h")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 DEFAULT_EPS = (0.1, 0.0, 0.1, 0.0, 0.1, 0.0, 0.1)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (-O2 -ffp-contract=off -fopenmp)."""
+def build(force: bool = False, count: bool = False) -> str:
+    """Compile the oracle with g++ (-O2 -ffp-contract=off -fopenmp).  With
+    count=True, the single-threaded operation-counting build
+    (-DORACLE_COUNT_FLOPS, flop_count.h): the same results, plus per-section
+    FP64 operation counts."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
-           "-shared", "-std=c++17", "-o", tmp, _SRC]
+    target = _LIB_COUNT if count else _LIB
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR), os.path.getmtime(_CNT_HDR))
+    if not force and os.path.exists(target) and os.path.getmtime(target) >= newest:
+        return target
+    tmp = target + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c++17"]
+    cmd += ["-DORACLE_COUNT_FLOPS", "-Wno-unknown-pragmas"] if count else ["-fopenmp"]
+    cmd += ["-o", tmp, _SRC]
     subprocess.check_call(cmd)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, target)
+    return target
 
 
-def lib():
-    global _lib
+def lib(count: bool = False):
     with _lock:
-        if _lib is None:
-            path = build()
+        if count not in _libs:
+            path = build(count=count)
             L = ctypes.CDLL(path)
             dp = ctypes.POINTER(ctypes.c_double)
             ip = ctypes.POINTER(ctypes.c_int)
@@ -75,8 +81,32 @@ def lib():
             L.or_step_1d.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, dp, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int]
-            _lib = L
-    return _lib
+            llp = ctypes.POINTER(ctypes.c_longlong)
+            L.or_flop_report.argtypes = [llp, llp, ctypes.c_int]
+            L.or_flop_reset.argtypes = []
+            _libs[count] = L
+    return _libs[count]
+
+
+# sections of the counting build, in the order of flop_count.h
+FLOP_SECTIONS = ("none", "cell", "face", "hll", "limit", "emit", "eref", "edge", "ct", "trans",
+                 "erefh", "update", "final", "dt")
+
+
+def flop_report():
+    """{section: (operations, units)} of the counting build since the last
+    flop_reset()."""
+    L = lib(count=True)
+    n = len(FLOP_SECTIONS)
+    f = (ctypes.c_longlong * n)()
+    u = (ctypes.c_longlong * n)()
+    got = L.or_flop_report(f, u, n)
+    assert got == n, got
+    return {name: (int(f[i]), int(u[i])) for i, name in enumerate(FLOP_SECTIONS)}
+
+
+def flop_reset():
+    lib(count=True).or_flop_reset()
 
 
 def _p(a):
@@ -91,7 +121,9 @@ class Grid:
     """One periodic/outflow box evolved by the oracle (single grid, 5 ghosts)."""
 
     def __init__(self, n, length, gamma=5.0 / 3.0, cfl=0.8, bc=(0, 0, 0), eps=DEFAULT_EPS,
-                 sweby=1.0, rho_floor=1e-20, p_floor=1e-20, dt_lag=False):
+                 sweby=1.0, rho_floor=1e-20, p_floor=1e-20, dt_lag=False, counting=False):
+        """counting=True runs the grid in the operation-counting build."""
+        self._L = lib(count=counting)
         self.dt_lag = bool(dt_lag)
         self._lag_dt = None   # lagged dt: CFL dt of the previous step's start state
         self.n = tuple(int(x) for x in n)
@@ -99,7 +131,7 @@ class Grid:
         self.gamma = float(gamma)
         bcs = (ctypes.c_int * 3)(*[int(b) for b in bc])
         epsa = np.ascontiguousarray(eps, dtype=np.float64)
-        self._h = lib().or_create(*self.n, *self.length, self.gamma, float(cfl), bcs, _p(epsa),
+        self._h = self._L.or_create(*self.n, *self.length, self.gamma, float(cfl), bcs, _p(epsa),
                                   float(sweby), float(rho_floor), float(p_floor))
         if not self._h:
             raise ValueError("oracle: invalid grid description")
@@ -107,7 +139,7 @@ class Grid:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().or_destroy(h)
+            self._L.or_destroy(h)
             self._h = None
 
     def load(self, U, bx, by, bz):
@@ -119,7 +151,7 @@ class Grid:
         assert U.shape == (5, nz, ny, nx)
         assert bx.shape == (nz, ny, nx + 1) and by.shape == (nz, ny + 1, nx)
         assert bz.shape == (nz + 1, ny, nx)
-        rc = lib().or_load(self._h, _p(U), _p(bx), _p(by), _p(bz))
+        rc = self._L.or_load(self._h, _p(U), _p(bx), _p(by), _p(bz))
         if rc:
             raise RuntimeError(f"oracle load failed rc={rc}")
         self._lag_dt = None
@@ -131,7 +163,7 @@ class Grid:
         bx = np.ascontiguousarray(bx, dtype=np.float64)
         by = np.ascontiguousarray(by, dtype=np.float64)
         bz = np.ascontiguousarray(bz, dtype=np.float64)
-        rc = lib().or_load_primitive(self._h, _p(W), _p(bx), _p(by), _p(bz))
+        rc = self._L.or_load_primitive(self._h, _p(W), _p(bx), _p(by), _p(bz))
         if rc:
             raise RuntimeError(f"oracle load failed rc={rc}")
         self._lag_dt = None
@@ -146,14 +178,14 @@ class Grid:
         by = np.empty((nz, ny + 1, nx))
         bz = np.empty((nz + 1, ny, nx))
         B = np.empty((3, nz, ny, nx))
-        lib().or_read(self._h, _p(U), _p(bx), _p(by), _p(bz), _p(B))
+        self._L.or_read(self._h, _p(U), _p(bx), _p(by), _p(bz), _p(B))
         return U, bx, by, bz, B
 
     def dt(self) -> float:
-        return lib().or_compute_dt(self._h)
+        return self._L.or_compute_dt(self._h)
 
     def step(self, dt: float) -> int:
-        return lib().or_step(self._h, float(dt))
+        return self._L.or_step(self._h, float(dt))
 
     def advance(self, nsteps: int, t_end: float | None = None, dt: float | None = None):
         """nsteps CFL (or fixed-dt) steps; stops at t_end (measured from this
@@ -189,33 +221,33 @@ class Grid:
 
     def totals(self):
         out = np.zeros(8)
-        lib().or_totals(self._h, _p(out))
+        self._L.or_totals(self._h, _p(out))
         return out
 
     def divb_max(self) -> float:
-        return lib().or_divb_max(self._h)
+        return self._L.or_divb_max(self._h)
 
     def counters(self):
         """(floor hits, unphysical zones, HLL faces) over all steps."""
         out = (ctypes.c_longlong * 3)()
-        lib().or_counters(self._h, out)
+        self._L.or_counters(self._h, out)
         return int(out[0]), int(out[1]), int(out[2])
 
     def set_protection(self, prot_rho: float = 0.0, prot_p: float = 0.0):
         """Protection floors of App. A (faces next to a zone below them use HLL)."""
-        if lib().or_set_protection(self._h, float(prot_rho), float(prot_p)):
+        if self._L.or_set_protection(self._h, float(prot_rho), float(prot_p)):
             raise ValueError("oracle: invalid protection floors")
 
     def set_source_scale(self, s: float):
         """Test ablation: multiply the div B source of Steps 5 and 7 by s."""
-        if lib().or_set_source_scale(self._h, float(s)):
+        if self._L.or_set_source_scale(self._h, float(s)):
             raise ValueError("oracle: invalid source scale")
 
     def stage(self, which: int):
         nx, ny, nz = self.n
         cap = 8 * (nx + 1) * (ny + 1) * (nz + 1)
         out = np.empty(cap)
-        w = lib().or_stage(self._h, int(which), _p(out), cap)
+        w = self._L.or_stage(self._h, int(which), _p(out), cap)
         return out[:w]
 
 

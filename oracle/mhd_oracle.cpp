@@ -20,10 +20,12 @@
 //                             (Eqs. for u-bar of the HLL scheme, b+ and b-)
 // Readings where the paper is silent are tagged R1..R21 as in the design notes.
 //
-// Parity unpinned: the energy and induction parts of the div B source term of
-// Steps 5 and 7 (reading R13, after GS08, which is not available); tests pin
-// only that they vanish for data varying along one axis and act on oblique
-// data.  Its momentum part is pinned to the flux derivative it supplies.
+// The div B source of Steps 5 and 7 (reading R13, after GS08, which is not
+// available) is pinned to the flux derivative it supplies in every row
+// (momentum, energy, induction) where its limiter is inactive, and its minmod
+// pairing to the planar problem.  Parity unpinned: the limiter itself (GS08's
+// choice to limit the induction and energy rows by minmod) where it is active,
+// and the free constants eps_k and beta_s (readings R7, R8).
 
 #include "mhd_oracle.h"
 
@@ -34,6 +36,38 @@
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
+#endif
+
+// The arithmetic type: plain double, or, in the separate operation-counting
+// build (-DORACLE_COUNT_FLOPS, single-threaded), an instrumented scalar with
+// the same IEEE results (flop_count.h).  Parameters (gamma, eps_k, dt, dx)
+// stay plain double.
+#ifdef ORACLE_COUNT_FLOPS
+#include "flop_count.h"
+using flopcount::real;
+using flopcount::r_sqrt;
+using flopcount::r_fabs;
+using flopcount::r_fmin;
+using flopcount::r_fmax;
+using flopcount::r_isfinite;
+using flopcount::to_d;
+namespace flopcount {
+long long flops[SEC_COUNT];
+long long units[SEC_COUNT];
+int section = SEC_NONE;
+}  // namespace flopcount
+#define FLOP_SECTION(s) flopcount::enter(flopcount::s)
+#define FLOP_UNIT(s) flopcount::unit(flopcount::s)
+#else
+typedef double real;
+inline double r_sqrt(double x) { return std::sqrt(x); }
+inline double r_fabs(double x) { return std::fabs(x); }
+inline double r_fmin(double a, double b) { return std::fmin(a, b); }
+inline double r_fmax(double a, double b) { return std::fmax(a, b); }
+inline bool r_isfinite(double x) { return std::isfinite(x); }
+inline double to_d(double x) { return x; }
+#define FLOP_SECTION(s) ((void)0)
+#define FLOP_UNIT(s) ((void)0)
 #endif
 
 namespace {
@@ -50,16 +84,16 @@ struct Params {
 // 3D array over the padded box [-NG, n+NG) per dimension, x fastest.
 struct Arr {
   int nx = 0, ny = 0, nz = 0, px = 0, py = 0;
-  std::vector<double> d;
+  std::vector<real> d;
   void init(int nx_, int ny_, int nz_) {
     nx = nx_; ny = ny_; nz = nz_;
     px = nx + 2 * NG; py = ny + 2 * NG;
     d.assign((size_t)px * py * (nz + 2 * NG), NaN);
   }
-  double& operator()(int i, int j, int k) {
+  real& operator()(int i, int j, int k) {
     return d[((size_t)(k + NG) * py + (j + NG)) * px + (i + NG)];
   }
-  double operator()(int i, int j, int k) const {
+  real operator()(int i, int j, int k) const {
     return d[((size_t)(k + NG) * py + (j + NG)) * px + (i + NG)];
   }
 };
@@ -70,10 +104,10 @@ enum { RHO = 0, MX = 1, MY = 2, MZ = 3, EN = 4, BX = 5, BY = 6, BZ = 7 };
 // Single-cell quantities in a sweep frame (n = sweep normal, t1, t2 cyclic).
 // ---------------------------------------------------------------------------
 struct Cell {  // conserved, zone-centred B
-  double rho, mn, mt1, mt2, e, bn, bt1, bt2;
+  real rho, mn, mt1, mt2, e, bn, bt1, bt2;
 };
 struct Prim {
-  double rho, vn, vt1, vt2, p, bn, bt1, bt2;
+  real rho, vn, vt1, vt2, p, bn, bt1, bt2;
 };
 
 // Sec. 3, Eqs. totpressure / totenergy solved for P.
@@ -84,17 +118,17 @@ inline Prim cell_prim(const Cell& c, double gamma) {
   p.vt1 = c.mt1 / c.rho;
   p.vt2 = c.mt2 / c.rho;
   p.bn = c.bn; p.bt1 = c.bt1; p.bt2 = c.bt2;
-  double ke = 0.5 * c.rho * (p.vn * p.vn + p.vt1 * p.vt1 + p.vt2 * p.vt2);
-  double me = 0.5 * (c.bn * c.bn + c.bt1 * c.bt1 + c.bt2 * c.bt2);
+  real ke = 0.5 * c.rho * (p.vn * p.vn + p.vt1 * p.vt1 + p.vt2 * p.vt2);
+  real me = 0.5 * (c.bn * c.bn + c.bt1 * c.bt1 + c.bt2 * c.bt2);
   p.p = (gamma - 1.0) * (c.e - ke - me);
   return p;
 }
 
 // Sec. 3, flux vector F of the 1D conservative form (7 non-trivial
 // components, ordered rho, Mn, Mt1, Mt2, Bt1, Bt2, E; F[Bn] = 0).
-inline void cell_flux(const Cell& c, const Prim& p, double F[7]) {
-  double me = 0.5 * (c.bn * c.bn + c.bt1 * c.bt1 + c.bt2 * c.bt2);
-  double pstar = p.p + me;
+inline void cell_flux(const Cell& c, const Prim& p, real F[7]) {
+  real me = 0.5 * (c.bn * c.bn + c.bt1 * c.bt1 + c.bt2 * c.bt2);
+  real pstar = p.p + me;
   F[0] = c.mn;
   F[1] = c.mn * p.vn + pstar - c.bn * c.bn;
   F[2] = c.mn * p.vt1 - c.bn * c.bt1;
@@ -121,84 +155,84 @@ inline void cell_flux(const Cell& c, const Prim& p, double F[7]) {
 // ---------------------------------------------------------------------------
 struct Eigen {
   // Roe state
-  double rho, srho, vn, vt1, vt2, b, bt1, bt2, X;
-  double a2, a, ca2, ct2, cf2, cs2, cf, cs, ca, af, as, beta1, beta2, S;
-  double lam[7];
-  double R[7][7];  // R[m][k]: conserved component m of right eigenvector k
-  double L[7][7];  // L[k][m]: left eigenvector k
-  double rrho[7], rp[7];  // density and pressure rows of the primitive r_k
+  real rho, srho, vn, vt1, vt2, b, bt1, bt2, X;
+  real a2, a, ca2, ct2, cf2, cs2, cf, cs, ca, af, as, beta1, beta2, S;
+  real lam[7];
+  real R[7][7];  // R[m][k]: conserved component m of right eigenvector k
+  real L[7][7];  // L[k][m]: left eigenvector k
+  real rrho[7], rp[7];  // density and pressure rows of the primitive r_k
   bool bad;
 };
 
-inline double sgn_pos(double x) { return x >= 0.0 ? 1.0 : -1.0; }
+inline real sgn_pos(real x) { return x >= 0.0 ? 1.0 : -1.0; }
 
 // Roe state + eigenvalues + eigenvectors for one interface.
 // L, R in the sweep frame with zone-centred B; b = face normal field.
-void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e) {
+void roe_state(const Prim& pL, const Prim& pR, real b, double gamma, Eigen* e) {
   e->bad = false;
-  double sL = std::sqrt(pL.rho), sR = std::sqrt(pR.rho);
-  double D = sL + sR;
+  real sL = r_sqrt(pL.rho), sR = r_sqrt(pR.rho);
+  real D = sL + sR;
   e->rho = sL * sR;
   e->vn = (sL * pL.vn + sR * pR.vn) / D;
   e->vt1 = (sL * pL.vt1 + sR * pR.vt1) / D;
   e->vt2 = (sL * pL.vt2 + sR * pR.vt2) / D;
   // enthalpy with the face normal field: H = (gamma/(gamma-1) P + rho v^2/2 + b^2 + Bt^2)/rho
-  double keL = 0.5 * pL.rho * (pL.vn * pL.vn + pL.vt1 * pL.vt1 + pL.vt2 * pL.vt2);
-  double keR = 0.5 * pR.rho * (pR.vn * pR.vn + pR.vt1 * pR.vt1 + pR.vt2 * pR.vt2);
-  double HL = (gamma / (gamma - 1.0) * pL.p + keL + b * b + pL.bt1 * pL.bt1 + pL.bt2 * pL.bt2) / pL.rho;
-  double HR = (gamma / (gamma - 1.0) * pR.p + keR + b * b + pR.bt1 * pR.bt1 + pR.bt2 * pR.bt2) / pR.rho;
-  double H = (sL * HL + sR * HR) / D;
+  real keL = 0.5 * pL.rho * (pL.vn * pL.vn + pL.vt1 * pL.vt1 + pL.vt2 * pL.vt2);
+  real keR = 0.5 * pR.rho * (pR.vn * pR.vn + pR.vt1 * pR.vt1 + pR.vt2 * pR.vt2);
+  real HL = (gamma / (gamma - 1.0) * pL.p + keL + b * b + pL.bt1 * pL.bt1 + pL.bt2 * pL.bt2) / pL.rho;
+  real HR = (gamma / (gamma - 1.0) * pR.p + keR + b * b + pR.bt1 * pR.bt1 + pR.bt2 * pR.bt2) / pR.rho;
+  real H = (sL * HL + sR * HR) / D;
   e->b = b;
   e->bt1 = (sR * pL.bt1 + sL * pR.bt1) / D;
   e->bt2 = (sR * pL.bt2 + sL * pR.bt2) / D;
-  double dbt1 = pR.bt1 - pL.bt1, dbt2 = pR.bt2 - pL.bt2;
+  real dbt1 = pR.bt1 - pL.bt1, dbt2 = pR.bt2 - pL.bt2;
   e->X = 0.5 * (dbt1 * dbt1 + dbt2 * dbt2) / (D * D);
-  double v2 = e->vn * e->vn + e->vt1 * e->vt1 + e->vt2 * e->vt2;
-  double bt2sum = e->bt1 * e->bt1 + e->bt2 * e->bt2;
+  real v2 = e->vn * e->vn + e->vt1 * e->vt1 + e->vt2 * e->vt2;
+  real bt2sum = e->bt1 * e->bt1 + e->bt2 * e->bt2;
   e->a2 = (gamma - 1.0) * (H - 0.5 * v2 - (b * b + bt2sum) / e->rho) - (gamma - 2.0) * e->X;
   if (!(e->a2 >= std::numeric_limits<double>::min())) {  // no real sound speed
     e->bad = true;
     return;
   }
-  e->srho = std::sqrt(e->rho);
+  e->srho = r_sqrt(e->rho);
   // characteristic speeds (Sec. 3) at the Roe state; the discriminant is
   // written as a sum of non-negative terms (reading R2).
-  double a2 = e->a2;
+  real a2 = e->a2;
   e->ca2 = b * b / e->rho;
   e->ct2 = bt2sum / e->rho;
-  double ca2 = e->ca2, ct2 = e->ct2;
-  double disc = (a2 - ca2) * (a2 - ca2) + ct2 * (ct2 + 2.0 * a2 + 2.0 * ca2);
-  double sd = std::sqrt(disc);  // = cf^2 - cs^2
+  real ca2 = e->ca2, ct2 = e->ct2;
+  real disc = (a2 - ca2) * (a2 - ca2) + ct2 * (ct2 + 2.0 * a2 + 2.0 * ca2);
+  real sd = r_sqrt(disc);  // = cf^2 - cs^2
   e->cf2 = 0.5 * (a2 + ca2 + ct2 + sd);
   e->cs2 = a2 * ca2 / e->cf2;   // cf^2 cs^2 = a^2 ca^2 (product of the two roots)
-  e->cf = std::sqrt(e->cf2);
-  e->cs = std::sqrt(e->cs2);
-  e->ca = std::sqrt(ca2);
-  e->a = std::sqrt(a2);
+  e->cf = r_sqrt(e->cf2);
+  e->cs = r_sqrt(e->cs2);
+  e->ca = r_sqrt(ca2);
+  e->a = r_sqrt(a2);
   // normalisation factors alpha_f, alpha_s (reading R6 for degeneracies)
   if (sd <= 1e-12 * (a2 + ca2 + ct2)) {
     if (a2 >= ca2) { e->af = 1.0; e->as = 0.0; }
     else { e->af = 0.0; e->as = 1.0; }
   } else {
     // cf^2 - a^2 and a^2 - cs^2 without cancellation
-    double t1 = ca2 + ct2 - a2;
-    double cf2_a2 = (t1 >= 0.0) ? 0.5 * (t1 + sd) : 2.0 * a2 * ct2 / (sd - t1);
-    double t2 = a2 - ca2 + ct2;
-    double cf2_ca2 = (t2 >= 0.0) ? 0.5 * (t2 + sd) : 2.0 * ca2 * ct2 / (sd - t2);
-    double a2_cs2 = a2 * cf2_ca2 / e->cf2;
-    double af2 = a2_cs2 / sd, as2 = cf2_a2 / sd;
+    real t1 = ca2 + ct2 - a2;
+    real cf2_a2 = (t1 >= 0.0) ? 0.5 * (t1 + sd) : 2.0 * a2 * ct2 / (sd - t1);
+    real t2 = a2 - ca2 + ct2;
+    real cf2_ca2 = (t2 >= 0.0) ? 0.5 * (t2 + sd) : 2.0 * ca2 * ct2 / (sd - t2);
+    real a2_cs2 = a2 * cf2_ca2 / e->cf2;
+    real af2 = a2_cs2 / sd, as2 = cf2_a2 / sd;
     if (af2 > 1.0) af2 = 1.0;
     if (af2 < 0.0) af2 = 0.0;
     if (as2 > 1.0) as2 = 1.0;
     if (as2 < 0.0) as2 = 0.0;
-    e->af = std::sqrt(af2);
-    e->as = std::sqrt(as2);
+    e->af = r_sqrt(af2);
+    e->as = r_sqrt(as2);
   }
-  double btm2 = bt2sum;
+  real btm2 = bt2sum;
   if (btm2 <= 1e-24 * (e->rho * a2 + b * b + bt2sum)) {
     e->beta1 = e->beta2 = 1.0 / std::sqrt(2.0);
   } else {
-    double btm = std::sqrt(btm2);
+    real btm = r_sqrt(btm2);
     e->beta1 = e->bt1 / btm;
     e->beta2 = e->bt2 / btm;
   }
@@ -214,15 +248,15 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
 
   // primitive right (columns r[.][k]) and left (rows l[k][.]) eigenvectors in
   // w = (rho, vn, vt1, vt2, Bt1, Bt2, p)
-  double r[7][7], l[7][7];
+  real r[7][7], l[7][7];
   for (int m = 0; m < 7; ++m)
     for (int k = 0; k < 7; ++k) { r[m][k] = 0.0; l[k][m] = 0.0; }
-  double af = e->af, as = e->as, cf = e->cf, cs = e->cs, S = e->S;
-  double b1 = e->beta1, b2 = e->beta2, rho = e->rho, sr = e->srho, a = e->a;
+  real af = e->af, as = e->as, cf = e->cf, cs = e->cs, S = e->S;
+  real b1 = e->beta1, b2 = e->beta2, rho = e->rho, sr = e->srho, a = e->a;
   // fast k=0 (v-cf) and k=6 (v+cf)
   for (int s = 0; s < 2; ++s) {
     int k = s == 0 ? 0 : 6;
-    double sg = s == 0 ? -1.0 : 1.0;  // sign of u = lambda - vn
+    real sg = s == 0 ? -1.0 : 1.0;  // sign of u = lambda - vn
     r[0][k] = rho * af;
     r[1][k] = sg * af * cf;
     r[2][k] = -sg * as * cs * S * b1;
@@ -240,7 +274,7 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
   // slow k=2 (v-cs) and k=4 (v+cs)
   for (int s = 0; s < 2; ++s) {
     int k = s == 0 ? 2 : 4;
-    double sg = s == 0 ? -1.0 : 1.0;
+    real sg = s == 0 ? -1.0 : 1.0;
     r[0][k] = rho * as;
     r[1][k] = sg * as * cs;
     r[2][k] = sg * af * cf * S * b1;
@@ -258,7 +292,7 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
   // Alfven k=1 (v-ca) and k=5 (v+ca)
   for (int s = 0; s < 2; ++s) {
     int k = s == 0 ? 1 : 5;
-    double sg = s == 0 ? 1.0 : -1.0;
+    real sg = s == 0 ? 1.0 : -1.0;
     r[2][k] = -b2;
     r[3][k] = b1;
     r[4][k] = -sg * S * sr * b2;
@@ -278,7 +312,7 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
     e->rp[k] = r[6][k];
   }
   // W: conserved (rho, Mn, Mt1, Mt2, Bt1, Bt2, E) -> w
-  double W[7][7];
+  real W[7][7];
   for (int m = 0; m < 7; ++m)
     for (int n = 0; n < 7; ++n) W[m][n] = 0.0;
   W[0][0] = 1.0;
@@ -295,7 +329,7 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
   W[6][5] = -(gamma - 1.0) * e->bt2;
   W[6][6] = gamma - 1.0;
   // T = W^-1: w -> conserved
-  double T[7][7];
+  real T[7][7];
   for (int m = 0; m < 7; ++m)
     for (int n = 0; n < 7; ++n) T[m][n] = 0.0;
   T[0][0] = 1.0;
@@ -314,13 +348,13 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
   // R = T r, L = l W
   for (int m = 0; m < 7; ++m)
     for (int k = 0; k < 7; ++k) {
-      double s = 0.0;
+      real s = 0.0;
       for (int n = 0; n < 7; ++n) s += T[m][n] * r[n][k];
       e->R[m][k] = s;
     }
   for (int k = 0; k < 7; ++k)
     for (int m = 0; m < 7; ++m) {
-      double s = 0.0;
+      real s = 0.0;
       for (int n = 0; n < 7; ++n) s += l[k][n] * W[n][m];
       e->L[k][m] = s;
     }
@@ -330,7 +364,7 @@ void roe_state(const Prim& pL, const Prim& pR, double b, double gamma, Eigen* e)
 // (rho, Mn, Mt1, Mt2, Bt1, Bt2, E); the energy of each cell is referred to the
 // face normal field (the 7-variable system treats Bn as a parameter; its
 // zone-centred value differs from b between the two cells), reading R4.
-inline void cons_diff(const Cell& L, const Cell& R, double dq[7]) {
+inline void cons_diff(const Cell& L, const Cell& R, real dq[7]) {
   dq[0] = R.rho - L.rho;
   dq[1] = R.mn - L.mn;
   dq[2] = R.mt1 - L.mt1;
@@ -341,32 +375,32 @@ inline void cons_diff(const Cell& L, const Cell& R, double dq[7]) {
 }
 
 // App. A: Q_k(chi)
-inline double Qk(double chi, double eps) {
-  double ac = std::fabs(chi);
+inline real Qk(real chi, double eps) {
+  real ac = r_fabs(chi);
   if (ac < 2.0 * eps) return chi * chi / (4.0 * eps) + eps;
   return ac;
 }
 
 // App. A: g_{k,i} = SIGN(gt_{i+1/2}) SWEBY(gt_{i+1/2}, gt_{i-1/2}) (reading R8)
-inline double sweby(double gp, double gm, double beta) {
-  double s = gp >= 0.0 ? 1.0 : -1.0;
-  double ap = std::fabs(gp);
-  double m1 = std::fmin(beta * ap, s * gm);
-  double m2 = std::fmin(ap, beta * s * gm);
-  double m = std::fmax(0.0, std::fmax(m1, m2));
+inline real sweby(real gp, real gm, double beta) {
+  real s = gp >= 0.0 ? 1.0 : -1.0;
+  real ap = r_fabs(gp);
+  real m1 = r_fmin(beta * ap, s * gm);
+  real m2 = r_fmin(ap, beta * s * gm);
+  real m = r_fmax(0.0, r_fmax(m1, m2));
   return s * m;
 }
 
 // Fast magnetosonic speed of one zone along the sweep normal (Sec. 3):
 // c_f^2 = [a^2 + B^2/rho + sqrt((a^2 + B^2/rho)^2 - 4 a^2 Bn^2/rho)] / 2,
 // a^2 = gamma P / rho, zone-centred B.
-inline double fast_speed(const Prim& p, double gamma) {
-  double a2 = gamma * p.p / p.rho;
-  double b2 = (p.bn * p.bn + p.bt1 * p.bt1 + p.bt2 * p.bt2) / p.rho;
-  double s = a2 + b2;
-  double disc = s * s - 4.0 * a2 * p.bn * p.bn / p.rho;
+inline real fast_speed(const Prim& p, double gamma) {
+  real a2 = gamma * p.p / p.rho;
+  real b2 = (p.bn * p.bn + p.bt1 * p.bt1 + p.bt2 * p.bt2) / p.rho;
+  real s = a2 + b2;
+  real disc = s * s - 4.0 * a2 * p.bn * p.bn / p.rho;
   if (disc < 0.0) disc = 0.0;  // reading R2
-  return std::sqrt(0.5 * (s + std::sqrt(disc)));
+  return r_sqrt(0.5 * (s + r_sqrt(disc)));
 }
 
 // Protection floor (App. A, reading R22): active when a floor is > 0.  A face
@@ -377,11 +411,11 @@ inline double fast_speed(const Prim& p, double gamma) {
 // these states are unphysical).
 inline bool protection_active(const Params& P) { return P.prot_rho > 0.0 || P.prot_p > 0.0; }
 
-bool protection_hit(const Prim& pL, const Prim& pR, const Eigen& e, const double alpha[7],
+bool protection_hit(const Prim& pL, const Prim& pR, const Eigen& e, const real alpha[7],
                     const Params& P) {
   if (pL.rho < P.prot_rho || pL.p < P.prot_p) return true;
   if (pR.rho < P.prot_rho || pR.p < P.prot_p) return true;
-  double rho = pL.rho, p = pL.p;
+  real rho = pL.rho, p = pL.p;
   for (int k = 0; k < 6; ++k) {
     rho += alpha[k] * e.rrho[k];
     p += alpha[k] * e.rp[k];
@@ -398,21 +432,21 @@ bool protection_hit(const Prim& pL, const Prim& pR, const Eigen& e, const double
 // which is not consistent (u != F for q_L = q_R); the Einfeldt form used here
 // is.  If both speeds vanish (no Roe state and both zones moving
 // supersonically into the face) the bounds are +-max(|v| + c_f).
-void hll_flux(const Cell& L, const Cell& R, const Prim& pL, const Prim& pR, const double FL[7],
-              const double FR[7], const Eigen* roe, double gamma, double out[7]) {
-  double cfL = fast_speed(pL, gamma), cfR = fast_speed(pR, gamma);
-  double bp = std::fmax(pR.vn + cfR, 0.0);
-  double bm = std::fmin(pL.vn - cfL, 0.0);
+void hll_flux(const Cell& L, const Cell& R, const Prim& pL, const Prim& pR, const real FL[7],
+              const real FR[7], const Eigen* roe, double gamma, real out[7]) {
+  real cfL = fast_speed(pL, gamma), cfR = fast_speed(pR, gamma);
+  real bp = r_fmax(pR.vn + cfR, 0.0);
+  real bm = r_fmin(pL.vn - cfL, 0.0);
   if (roe) {
-    bp = std::fmax(bp, roe->lam[6]);
-    bm = std::fmin(bm, roe->lam[0]);
+    bp = r_fmax(bp, roe->lam[6]);
+    bm = r_fmin(bm, roe->lam[0]);
   }
   if (!(bp - bm > 0.0)) {
-    double s = std::fmax(std::fabs(pL.vn) + cfL, std::fabs(pR.vn) + cfR);
+    real s = r_fmax(r_fabs(pL.vn) + cfL, r_fabs(pR.vn) + cfR);
     bp = s;
     bm = -s;
   }
-  double dq[7];
+  real dq[7];
   cons_diff(L, R, dq);
   for (int m = 0; m < 7; ++m)
     out[m] = (bp * FL[m] - bm * FR[m] + bp * bm * dq[m]) / (bp - bm);
@@ -420,9 +454,9 @@ void hll_flux(const Cell& L, const Cell& R, const Prim& pL, const Prim& pR, cons
 
 struct Face {
   Eigen e;
-  double alpha[7], nu[7], gt[7], Favg[7];
+  real alpha[7], nu[7], gt[7], Favg[7];
   bool hll;
-  double Fhll[7];
+  real Fhll[7];
 };
 
 // MHDTVD flux on one pencil.  cells[c] for c in [0, ncell), face f between
@@ -433,15 +467,17 @@ struct Face {
 // contributes g-tilde = 0 to the limiter of its neighbours (reading R22).
 // Returns the number of output faces that took the HLL flux; if hll_flag is
 // given, hll_flag[f] = 1 marks those faces (0 elsewhere).
-int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
-                double dx_2dt, const Params& P, double (*out)[7],
+int pencil_flux(int ncell, const Cell* cells, const real* bface, double dtdx,
+                double dx_2dt, const Params& P, real (*out)[7],
                 unsigned char* hll_flag = nullptr) {
   if (hll_flag)
     for (int f = 0; f <= ncell; ++f) hll_flag[f] = 0;
   int nhll = 0;
   std::vector<Prim> prim(ncell);
-  std::vector<double> Fc((size_t)ncell * 7);
+  std::vector<real> Fc((size_t)ncell * 7);
+  FLOP_SECTION(SEC_CELL);
   for (int c = 0; c < ncell; ++c) {
+    FLOP_UNIT(SEC_CELL);
     prim[c] = cell_prim(cells[c], P.gamma);
     cell_flux(cells[c], prim[c], &Fc[(size_t)c * 7]);
   }
@@ -450,13 +486,15 @@ int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
     Face& F = face[f];
     const Cell& L = cells[f - 1];
     const Cell& R = cells[f];
+    FLOP_SECTION(SEC_FACE);
+    FLOP_UNIT(SEC_FACE);
     roe_state(prim[f - 1], prim[f], bface[f], P.gamma, &F.e);
     F.hll = F.e.bad;
     if (!F.hll) {
-      double dq[7];
+      real dq[7];
       cons_diff(L, R, dq);
       for (int k = 0; k < 7; ++k) {
-        double s = 0.0;
+        real s = 0.0;
         for (int m = 0; m < 7; ++m) s += F.e.L[k][m] * dq[m];
         F.alpha[k] = s;                       // alpha_k = L_k . (q_{i+1} - q_i)
       }
@@ -467,6 +505,8 @@ int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
         F.alpha[k] = F.nu[k] = NaN;
         F.gt[k] = 0.0;
       }
+      FLOP_SECTION(SEC_HLL);
+      FLOP_UNIT(SEC_HLL);
       hll_flux(L, R, prim[f - 1], prim[f], &Fc[(size_t)(f - 1) * 7], &Fc[(size_t)f * 7],
                F.e.bad ? nullptr : &F.e, P.gamma, F.Fhll);
       continue;
@@ -479,28 +519,34 @@ int pencil_flux(int ncell, const Cell* cells, const double* bface, double dtdx,
       F.Favg[m] = 0.5 * (Fc[(size_t)(f - 1) * 7 + m] + Fc[(size_t)f * 7 + m]);
   }
   // g_{k,c} for cells c in [1, ncell-2]: faces c (i-1/2) and c+1 (i+1/2)
-  std::vector<double> g((size_t)ncell * 7, NaN);
-  for (int c = 1; c <= ncell - 2; ++c)
+  std::vector<real> g((size_t)ncell * 7, NaN);
+  FLOP_SECTION(SEC_LIMIT);
+  for (int c = 1; c <= ncell - 2; ++c) {
+    FLOP_UNIT(SEC_LIMIT);
     for (int k = 0; k < 7; ++k)
       g[(size_t)c * 7 + k] = sweby(face[c + 1].gt[k], face[c].gt[k], P.sweby);
+  }
+  FLOP_SECTION(SEC_EMIT);
   for (int f = 2; f <= ncell - 2; ++f) {
     const Face& F = face[f];
+    FLOP_UNIT(SEC_EMIT);
     if (F.hll) {
       ++nhll;
       if (hll_flag) hll_flag[f] = 1;
       for (int m = 0; m < 7; ++m) out[f][m] = F.Fhll[m];
       continue;
     }
-    double fsum[7] = {0, 0, 0, 0, 0, 0, 0};
+    real fsum[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < 7; ++k) {
-      double gi = g[(size_t)(f - 1) * 7 + k];   // g_{k,i}, i = left cell
-      double gi1 = g[(size_t)f * 7 + k];        // g_{k,i+1}
-      double gam = (F.alpha[k] != 0.0) ? (gi1 - gi) / F.alpha[k] : 0.0;
-      double beta = Qk(F.nu[k] + gam, P.eps[k]) * F.alpha[k] - (gi + gi1);
+      real gi = g[(size_t)(f - 1) * 7 + k];   // g_{k,i}, i = left cell
+      real gi1 = g[(size_t)f * 7 + k];        // g_{k,i+1}
+      real gam = (F.alpha[k] != 0.0) ? (gi1 - gi) / F.alpha[k] : 0.0;
+      real beta = Qk(F.nu[k] + gam, P.eps[k]) * F.alpha[k] - (gi + gi1);
       for (int m = 0; m < 7; ++m) fsum[m] += beta * F.e.R[m][k];
     }
     for (int m = 0; m < 7; ++m) out[f][m] = F.Favg[m] - dx_2dt * fsum[m];
   }
+  FLOP_SECTION(SEC_NONE);
   return nhll;
 }
 
@@ -599,8 +645,8 @@ int sweep(or_grid* g, int d, const Arr* qin, const Arr& bn, double dt, const Ran
     for (int ia = 0; ia < na; ++ia) {
       int a = r.lo[t1] + ia, bb = r.lo[t2] + ib;
       std::vector<Cell> cells(ncell);
-      std::vector<double> bface(ncell + 1);
-      std::vector<double> flux((size_t)(ncell + 1) * 7, NaN);
+      std::vector<real> bface(ncell + 1);
+      std::vector<real> flux((size_t)(ncell + 1) * 7, NaN);
       std::vector<unsigned char> hflag(ncell + 1);
       for (int c = 0; c < ncell; ++c) {
         int idx[3];
@@ -614,14 +660,14 @@ int sweep(or_grid* g, int d, const Arr* qin, const Arr& bn, double dt, const Ran
       }
       bface[0] = NaN;
       pencil_flux(ncell, cells.data(), bface.data(), dtdx, dx_2dt, g->P,
-                  reinterpret_cast<double(*)[7]>(flux.data()), hflag.data());
+                  reinterpret_cast<real(*)[7]>(flux.data()), hflag.data());
       const bool across = a >= 0 && a < g->n[t1] && bb >= 0 && bb < g->n[t2];
       for (int f = 2; f <= ncell - 2; ++f)
         if (hflag[f] && across && c0 + f >= 0 && c0 + f < g->n[d]) ++bad;
       for (int f = 2; f <= ncell - 2; ++f) {
         int idx[3];
         idx[d] = c0 + f; idx[t1] = a; idx[t2] = bb;
-        const double* F = &flux[(size_t)f * 7];
+        const real* F = &flux[(size_t)f * 7];
         int i = idx[0], j = idx[1], k = idx[2];
         out[RHO](i, j, k) = F[0];
         out[MX + d](i, j, k) = F[1];
@@ -638,14 +684,16 @@ int sweep(or_grid* g, int d, const Arr* qin, const Arr& bn, double dt, const Ran
 
 // Steps 2 and 8: zone-centred reference EMF E = -v x B.
 void reference_emf(const Arr* rho, const Arr* m, const Arr* B, Arr* E, const Range& r) {
+  FLOP_SECTION(SEC_EREF);
 #pragma omp parallel for schedule(static)
   for (int k = r.lo[2]; k <= r.hi[2]; ++k)
     for (int j = r.lo[1]; j <= r.hi[1]; ++j)
       for (int i = r.lo[0]; i <= r.hi[0]; ++i) {
-        double vx = m[0](i, j, k) / rho[0](i, j, k);
-        double vy = m[1](i, j, k) / rho[0](i, j, k);
-        double vz = m[2](i, j, k) / rho[0](i, j, k);
-        double bx = B[0](i, j, k), by = B[1](i, j, k), bz = B[2](i, j, k);
+        FLOP_UNIT(SEC_EREF);
+        real vx = m[0](i, j, k) / rho[0](i, j, k);
+        real vy = m[1](i, j, k) / rho[0](i, j, k);
+        real vz = m[2](i, j, k) / rho[0](i, j, k);
+        real bx = B[0](i, j, k), by = B[1](i, j, k), bz = B[2](i, j, k);
         E[0](i, j, k) = vz * by - vy * bz;
         E[1](i, j, k) = vx * bz - vz * bx;
         E[2](i, j, k) = vy * bx - vx * by;
@@ -664,42 +712,44 @@ void edge_emf(or_grid* g, int c, Arr F[3][8], const Arr& Er, Arr& Eout, const Ra
   Arr* Fa = F[a];
   Arr* Fb = F[b];
   (void)g;
+  FLOP_SECTION(SEC_EDGE);
 #pragma omp parallel for schedule(static)
   for (int k = r.lo[2]; k <= r.hi[2]; ++k)
     for (int j = r.lo[1]; j <= r.hi[1]; ++j)
       for (int i = r.lo[0]; i <= r.hi[0]; ++i) {
+        FLOP_UNIT(SEC_EDGE);
         int p[3] = {i, j, k};
         // neighbour offsets: ma = one step back along a, mb = back along b
         int pa[3] = {i, j, k}; pa[a] -= 1;           // (fa-1, fb)
         int pb[3] = {i, j, k}; pb[b] -= 1;           // (fa, fb-1)
         int pab[3] = {i, j, k}; pab[a] -= 1; pab[b] -= 1;
         // a-face EMF at (fa, jb) and (fa, jb-1)
-        double Ea_0 = -Fa[BX + b](p[0], p[1], p[2]);      // (fa, fb)   -> a-face fa, b-cell fb
-        double Ea_m = -Fa[BX + b](pb[0], pb[1], pb[2]);   // (fa, fb-1)
+        real Ea_0 = -Fa[BX + b](p[0], p[1], p[2]);      // (fa, fb)   -> a-face fa, b-cell fb
+        real Ea_m = -Fa[BX + b](pb[0], pb[1], pb[2]);   // (fa, fb-1)
         // b-face EMF at (ia, fb) and (ia-1, fb)
-        double Eb_0 = Fb[BX + a](p[0], p[1], p[2]);       // a-cell fa, b-face fb
-        double Eb_m = Fb[BX + a](pa[0], pa[1], pa[2]);    // a-cell fa-1
-        double ma_0 = Fa[RHO](p[0], p[1], p[2]);
-        double ma_m = Fa[RHO](pb[0], pb[1], pb[2]);
-        double mb_0 = Fb[RHO](p[0], p[1], p[2]);
-        double mb_m = Fb[RHO](pa[0], pa[1], pa[2]);
+        real Eb_0 = Fb[BX + a](p[0], p[1], p[2]);       // a-cell fa, b-face fb
+        real Eb_m = Fb[BX + a](pa[0], pa[1], pa[2]);    // a-cell fa-1
+        real ma_0 = Fa[RHO](p[0], p[1], p[2]);
+        real ma_m = Fa[RHO](pb[0], pb[1], pb[2]);
+        real mb_0 = Fb[RHO](p[0], p[1], p[2]);
+        real mb_m = Fb[RHO](pa[0], pa[1], pa[2]);
         // reference EMF at the four zones around the edge
-        double R00 = Er(p[0], p[1], p[2]);          // zone (fa, fb)
-        double Rm0 = Er(pa[0], pa[1], pa[2]);       // zone (fa-1, fb)
-        double R0m = Er(pb[0], pb[1], pb[2]);       // zone (fa, fb-1)
-        double Rmm = Er(pab[0], pab[1], pab[2]);    // zone (fa-1, fb-1)
+        real R00 = Er(p[0], p[1], p[2]);          // zone (fa, fb)
+        real Rm0 = Er(pa[0], pa[1], pa[2]);       // zone (fa-1, fb)
+        real R0m = Er(pb[0], pb[1], pb[2]);       // zone (fa, fb-1)
+        real Rmm = Er(pab[0], pab[1], pab[2]);    // zone (fa-1, fb-1)
         // d/db at b-position fb-1/4 (between b-face fb and zone fb), upwind in a by ma_0
-        double db_hi_m = Rm0 - Eb_m, db_hi_0 = R00 - Eb_0;
-        double db_hi = ma_0 > 0.0 ? db_hi_m : (ma_0 < 0.0 ? db_hi_0 : 0.5 * (db_hi_m + db_hi_0));
+        real db_hi_m = Rm0 - Eb_m, db_hi_0 = R00 - Eb_0;
+        real db_hi = ma_0 > 0.0 ? db_hi_m : (ma_0 < 0.0 ? db_hi_0 : 0.5 * (db_hi_m + db_hi_0));
         // d/db at fb-3/4 (between zone fb-1 and b-face fb), upwind by ma_m
-        double db_lo_m = Eb_m - Rmm, db_lo_0 = Eb_0 - R0m;
-        double db_lo = ma_m > 0.0 ? db_lo_m : (ma_m < 0.0 ? db_lo_0 : 0.5 * (db_lo_m + db_lo_0));
+        real db_lo_m = Eb_m - Rmm, db_lo_0 = Eb_0 - R0m;
+        real db_lo = ma_m > 0.0 ? db_lo_m : (ma_m < 0.0 ? db_lo_0 : 0.5 * (db_lo_m + db_lo_0));
         // d/da at a-position fa-1/4 (between a-face fa and zone fa), upwind in b by mb_0
-        double da_hi_m = R0m - Ea_m, da_hi_0 = R00 - Ea_0;
-        double da_hi = mb_0 > 0.0 ? da_hi_m : (mb_0 < 0.0 ? da_hi_0 : 0.5 * (da_hi_m + da_hi_0));
+        real da_hi_m = R0m - Ea_m, da_hi_0 = R00 - Ea_0;
+        real da_hi = mb_0 > 0.0 ? da_hi_m : (mb_0 < 0.0 ? da_hi_0 : 0.5 * (da_hi_m + da_hi_0));
         // d/da at fa-3/4 (between zone fa-1 and a-face fa), upwind by mb_m
-        double da_lo_m = Ea_m - Rmm, da_lo_0 = Ea_0 - Rm0;
-        double da_lo = mb_m > 0.0 ? da_lo_m : (mb_m < 0.0 ? da_lo_0 : 0.5 * (da_lo_m + da_lo_0));
+        real da_lo_m = Ea_m - Rmm, da_lo_0 = Ea_0 - Rm0;
+        real da_lo = mb_m > 0.0 ? da_lo_m : (mb_m < 0.0 ? da_lo_0 : 0.5 * (da_lo_m + da_lo_0));
         Eout(i, j, k) = 0.25 * (Ea_0 + Ea_m + Eb_0 + Eb_m) + 0.25 * (db_lo - db_hi) +
                         0.25 * (da_lo - da_hi);
       }
@@ -713,42 +763,53 @@ void ct_update(or_grid* g, const Arr* bin, Arr* E, double tau, Arr* bout, const 
     // (curl E)_d = dE_b/da - dE_a/db
     const Range& r = rr[d];
     double da = g->dxv[a], db = g->dxv[b];
+    FLOP_SECTION(SEC_CT);
 #pragma omp parallel for schedule(static)
     for (int k = r.lo[2]; k <= r.hi[2]; ++k)
       for (int j = r.lo[1]; j <= r.hi[1]; ++j)
         for (int i = r.lo[0]; i <= r.hi[0]; ++i) {
+          FLOP_UNIT(SEC_CT);
           int pa[3] = {i, j, k}; pa[a] += 1;
           int pb[3] = {i, j, k}; pb[b] += 1;
-          double curl = (E[b](pa[0], pa[1], pa[2]) - E[b](i, j, k)) / da -
+          real curl = (E[b](pa[0], pa[1], pa[2]) - E[b](i, j, k)) / da -
                         (E[a](pb[0], pb[1], pb[2]) - E[a](i, j, k)) / db;
           bout[d](i, j, k) = bin[d](i, j, k) - tau * curl;
         }
   }
 }
 
-inline double minmod(double x, double y) {
-  if (x > 0.0 && y > 0.0) return std::fmin(x, y);
-  if (x < 0.0 && y < 0.0) return std::fmax(x, y);
+inline real minmod(real x, real y) {
+  if (x > 0.0 && y > 0.0) return r_fmin(x, y);
+  if (x < 0.0 && y < 0.0) return r_fmax(x, y);
   return 0.0;
 }
 
 // Steps 5 and 7: q^{n+1/2}_d = q^n - dt/2 (transverse flux divergence) + dt/2 S_d,
 // zone-centred B_d := average of b_d^{n+1/2} (reading R12), with the GS08
-// div B source term S_d (reading R13).
+// div B source term S_d (reading R13).  S_d supplies the part of the d-flux
+// gradient that a d-sweep leaves out because it holds B_d fixed (with the
+// energy referred to the normal field, reading R4):
+// -(dF_d/dB_d) db_d/dx_d at fixed (rho, M, E - B_d^2/2, B_t), i.e.
+// (0, B db_d, (B_t . v_t) db_d, v_t db_d) for (rho, M, E, B_t).  Following
+// GS08, each transverse field component and its energy share are limited by
+// minmod(db_d, -db_t) against the other transverse axis, whose difference
+// carries the same divergence in the transverse flux of that component.
 void transverse_state(or_grid* g, int d, double dt, const Range& r) {
   int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
   double hdt = 0.5 * dt;
   Arr* out = g->qh[d];
+  FLOP_SECTION(SEC_TRANS);
 #pragma omp parallel for schedule(static)
   for (int k = r.lo[2]; k <= r.hi[2]; ++k)
     for (int j = r.lo[1]; j <= r.hi[1]; ++j)
       for (int i = r.lo[0]; i <= r.hi[0]; ++i) {
+        FLOP_UNIT(SEC_TRANS);
         int p[3] = {i, j, k};
         int p1[3] = {i, j, k}; p1[t1] += 1;
         int p2[3] = {i, j, k}; p2[t2] += 1;
         int pd[3] = {i, j, k}; pd[d] += 1;
-        double rho = g->q[RHO](i, j, k);
-        double v[3], B[3], db[3];
+        real rho = g->q[RHO](i, j, k);
+        real v[3], B[3], db[3];
         for (int e = 0; e < 3; ++e) {
           v[e] = g->q[MX + e](i, j, k) / rho;
           B[e] = g->q[BX + e](i, j, k);
@@ -756,18 +817,18 @@ void transverse_state(or_grid* g, int d, double dt, const Range& r) {
           db[e] = (g->b[e](pe[0], pe[1], pe[2]) - g->b[e](i, j, k)) / g->dxv[e];
         }
         // GS08 source: m_t1 pairs d with t2, m_t2 pairs d with t1
-        double m2 = minmod(db[d], -db[t1]);   // used for the t2 field component
-        double m1 = minmod(db[d], -db[t2]);   // used for the t1 field component
-        double S[8];
+        real m2 = minmod(db[d], -db[t1]);   // used for the t2 field component
+        real m1 = minmod(db[d], -db[t2]);   // used for the t1 field component
+        real S[8];
         S[RHO] = 0.0;
         for (int e = 0; e < 3; ++e) S[MX + e] = B[e] * db[d];
-        S[EN] = B[d] * v[d] * db[d] + B[t1] * v[t1] * m1 + B[t2] * v[t2] * m2;
+        S[EN] = B[t1] * v[t1] * m1 + B[t2] * v[t2] * m2;
         S[BX + d] = 0.0;
         S[BX + t1] = v[t1] * m1;
         S[BX + t2] = v[t2] * m2;
         for (int c = 0; c < 8; ++c) {
           if (c == BX + d) continue;
-          double div = (g->Fp[t1][c](p1[0], p1[1], p1[2]) - g->Fp[t1][c](p[0], p[1], p[2])) / g->dxv[t1] +
+          real div = (g->Fp[t1][c](p1[0], p1[1], p1[2]) - g->Fp[t1][c](p[0], p[1], p[2])) / g->dxv[t1] +
                        (g->Fp[t2][c](p2[0], p2[1], p2[2]) - g->Fp[t2][c](p[0], p[1], p[2])) / g->dxv[t2];
           out[c](i, j, k) = g->q[c](i, j, k) - hdt * div + hdt * (g->P.source_scale * S[c]);
         }
@@ -779,22 +840,24 @@ void transverse_state(or_grid* g, int d, double dt, const Range& r) {
 // averages of b^{n+1/2} (reading R14).
 void half_reference_emf(or_grid* g, double dt, const Range& r) {
   double hdt = 0.5 * dt;
+  FLOP_SECTION(SEC_EREFH);
 #pragma omp parallel for schedule(static)
   for (int k = r.lo[2]; k <= r.hi[2]; ++k)
     for (int j = r.lo[1]; j <= r.hi[1]; ++j)
       for (int i = r.lo[0]; i <= r.hi[0]; ++i) {
-        double u[4];
+        FLOP_UNIT(SEC_EREFH);
+        real u[4];
         int comps[4] = {RHO, MX, MY, MZ};
         for (int c = 0; c < 4; ++c) {
-          double div = 0.0;
+          real div = 0.0;
           for (int e = 0; e < 3; ++e) {
             int pe[3] = {i, j, k}; pe[e] += 1;
             div += (g->Fc[e][comps[c]](pe[0], pe[1], pe[2]) - g->Fc[e][comps[c]](i, j, k)) / g->dxv[e];
           }
           u[c] = g->q[comps[c]](i, j, k) - hdt * div;
         }
-        double vx = u[1] / u[0], vy = u[2] / u[0], vz = u[3] / u[0];
-        double B[3];
+        real vx = u[1] / u[0], vy = u[2] / u[0], vz = u[3] / u[0];
+        real B[3];
         for (int e = 0; e < 3; ++e) {
           int pe[3] = {i, j, k}; pe[e] += 1;
           B[e] = 0.5 * (g->bh[e](i, j, k) + g->bh[e](pe[0], pe[1], pe[2]));
@@ -815,29 +878,32 @@ void apply_floors_and_ccb(or_grid* g) {
   const int* n = g->n;
   double gam = g->P.gamma;
   long long hits = 0, bad = 0;
+  FLOP_SECTION(SEC_FINAL);
 #pragma omp parallel for schedule(static) reduction(+ : hits, bad)
   for (int k = 0; k < n[2]; ++k)
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i) {
+        FLOP_UNIT(SEC_FINAL);
         g->q[BX](i, j, k) = 0.5 * (g->b[0](i, j, k) + g->b[0](i + 1, j, k));
         g->q[BY](i, j, k) = 0.5 * (g->b[1](i, j, k) + g->b[1](i, j + 1, k));
         g->q[BZ](i, j, k) = 0.5 * (g->b[2](i, j, k) + g->b[2](i, j, k + 1));
         // density and pressure floors (reading R1)
-        double rho = g->q[RHO](i, j, k);
+        real rho = g->q[RHO](i, j, k);
         if (rho < g->P.rho_floor) { rho = g->P.rho_floor; g->q[RHO](i, j, k) = rho; ++hits; }
-        double mx = g->q[MX](i, j, k), my = g->q[MY](i, j, k), mz = g->q[MZ](i, j, k);
-        double ke = 0.5 * (mx * mx + my * my + mz * mz) / rho;
-        double bx = g->q[BX](i, j, k), by = g->q[BY](i, j, k), bz = g->q[BZ](i, j, k);
-        double me = 0.5 * (bx * bx + by * by + bz * bz);
-        double p = (gam - 1.0) * (g->q[EN](i, j, k) - ke - me);
+        real mx = g->q[MX](i, j, k), my = g->q[MY](i, j, k), mz = g->q[MZ](i, j, k);
+        real ke = 0.5 * (mx * mx + my * my + mz * mz) / rho;
+        real bx = g->q[BX](i, j, k), by = g->q[BY](i, j, k), bz = g->q[BZ](i, j, k);
+        real me = 0.5 * (bx * bx + by * by + bz * bz);
+        real p = (gam - 1.0) * (g->q[EN](i, j, k) - ke - me);
         if (p < g->P.p_floor) {
           g->q[EN](i, j, k) = g->P.p_floor / (gam - 1.0) + ke + me;
           ++hits;
         }
-        bool ok = std::isfinite(rho) && std::isfinite(p) && std::isfinite(g->q[EN](i, j, k)) &&
-                  std::isfinite(mx) && std::isfinite(my) && std::isfinite(mz) && rho > 0.0;
+        bool ok = r_isfinite(rho) && r_isfinite(p) && r_isfinite(g->q[EN](i, j, k)) &&
+                  r_isfinite(mx) && r_isfinite(my) && r_isfinite(mz) && rho > 0.0;
         if (!ok) ++bad;
       }
+  FLOP_SECTION(SEC_NONE);
   g->floor_hits += hits;
   g->unphysical += bad;
 }
@@ -895,6 +961,7 @@ int or_set_threads(int n) {
 
 int or_load(or_grid* g, const double* U, const double* bx, const double* by, const double* bz) {
   if (!g || !U || !bx || !by || !bz) return 1;
+  FLOP_SECTION(SEC_NONE);
   int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   size_t nc = (size_t)nx * ny * nz;
   for (int k = 0; k < nz; ++k)
@@ -932,8 +999,8 @@ int or_load_primitive(or_grid* g, const double* W, const double* bx, const doubl
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         size_t c = ((size_t)k * ny + j) * nx + i;
-        double rho = W[c], vx = W[nc + c], vy = W[2 * nc + c], vz = W[3 * nc + c], p = W[4 * nc + c];
-        double bxc = g->q[BX](i, j, k), byc = g->q[BY](i, j, k), bzc = g->q[BZ](i, j, k);
+        real rho = W[c], vx = W[nc + c], vy = W[2 * nc + c], vz = W[3 * nc + c], p = W[4 * nc + c];
+        real bxc = g->q[BX](i, j, k), byc = g->q[BY](i, j, k), bzc = g->q[BZ](i, j, k);
         g->q[MX](i, j, k) = rho * vx;
         g->q[MY](i, j, k) = rho * vy;
         g->q[MZ](i, j, k) = rho * vz;
@@ -956,13 +1023,13 @@ int or_read(const or_grid* g, double* U, double* bx, double* by, double* bz, dou
         if (ci && cj && ck) {
           size_t c = ((size_t)k * ny + j) * nx + i;
           if (U)
-            for (int v = 0; v < 5; ++v) U[v * nc + c] = g->q[v](i, j, k);
+            for (int v = 0; v < 5; ++v) U[v * nc + c] = to_d(g->q[v](i, j, k));
           if (B)
-            for (int v = 0; v < 3; ++v) B[v * nc + c] = g->q[BX + v](i, j, k);
+            for (int v = 0; v < 3; ++v) B[v * nc + c] = to_d(g->q[BX + v](i, j, k));
         }
-        if (bx && cj && ck) bx[((size_t)k * ny + j) * (nx + 1) + i] = g->b[0](i, j, k);
-        if (by && ci && ck) by[((size_t)k * (ny + 1) + j) * nx + i] = g->b[1](i, j, k);
-        if (bz && ci && cj) bz[((size_t)k * ny + j) * nx + i] = g->b[2](i, j, k);
+        if (bx && cj && ck) bx[((size_t)k * ny + j) * (nx + 1) + i] = to_d(g->b[0](i, j, k));
+        if (by && ci && ck) by[((size_t)k * (ny + 1) + j) * nx + i] = to_d(g->b[1](i, j, k));
+        if (bz && ci && cj) bz[((size_t)k * ny + j) * nx + i] = to_d(g->b[2](i, j, k));
       }
   return 0;
 }
@@ -973,32 +1040,38 @@ double or_compute_dt(const or_grid* g) {
   const int* n = g->n;
   double gam = g->P.gamma;
   double wmax = 0.0;
+  FLOP_SECTION(SEC_DT);
 #pragma omp parallel for schedule(static) reduction(max : wmax)
   for (int k = 0; k < n[2]; ++k)
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i) {
-        double rho = g->q[RHO](i, j, k);
-        double v[3], B[3];
+        FLOP_UNIT(SEC_DT);
+        real rho = g->q[RHO](i, j, k);
+        real v[3], B[3];
         for (int e = 0; e < 3; ++e) {
           v[e] = g->q[MX + e](i, j, k) / rho;
           B[e] = g->q[BX + e](i, j, k);
         }
-        double ke = 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        double me = 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
-        double p = (gam - 1.0) * (g->q[EN](i, j, k) - ke - me);
-        double a2 = gam * p / rho;
-        double w = 0.0;
+        real ke = 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        real me = 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+        real p = (gam - 1.0) * (g->q[EN](i, j, k) - ke - me);
+        real a2 = gam * p / rho;
+        real w = 0.0;
         for (int d = 0; d < 3; ++d) {
           int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-          double cn2 = B[d] * B[d] / rho;
-          double ct2 = (B[t1] * B[t1] + B[t2] * B[t2]) / rho;
-          double disc = (a2 - cn2) * (a2 - cn2) + ct2 * (ct2 + 2.0 * a2 + 2.0 * cn2);
-          double cf = std::sqrt(0.5 * (a2 + cn2 + ct2 + std::sqrt(disc)));
-          w += (std::fabs(v[d]) + cf) / g->dxv[d];
+          real cn2 = B[d] * B[d] / rho;
+          real ct2 = (B[t1] * B[t1] + B[t2] * B[t2]) / rho;
+          real disc = (a2 - cn2) * (a2 - cn2) + ct2 * (ct2 + 2.0 * a2 + 2.0 * cn2);
+          real cf = r_sqrt(0.5 * (a2 + cn2 + ct2 + r_sqrt(disc)));
+          w += (r_fabs(v[d]) + cf) / g->dxv[d];
         }
-        if (w > wmax) wmax = w;
+        if (to_d(w) > wmax) wmax = to_d(w);
       }
-  return g->P.cfl / wmax;
+  FLOP_SECTION(SEC_DT);
+  real rate = wmax;
+  real out = g->P.cfl / rate;   // one division per box
+  FLOP_SECTION(SEC_NONE);
+  return to_d(out);
 }
 
 int or_step(or_grid* g, double dt) {
@@ -1046,18 +1119,22 @@ int or_step(or_grid* g, double dt) {
   {
     double cx = dt / g->dxv[0], cy = dt / g->dxv[1], cz = dt / g->dxv[2];
     int comps[5] = {RHO, MX, MY, MZ, EN};
+    FLOP_SECTION(SEC_UPDATE);
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < N2; ++k)
       for (int j = 0; j < N1; ++j)
-        for (int i = 0; i < N0; ++i)
+        for (int i = 0; i < N0; ++i) {
+          FLOP_UNIT(SEC_UPDATE);
           for (int c5 = 0; c5 < 5; ++c5) {
             int c = comps[c5];
-            double u = g->q[c](i, j, k);
+            real u = g->q[c](i, j, k);
             u = u - cx * (g->Fc[0][c](i + 1, j, k) - g->Fc[0][c](i, j, k));
             u = u - cy * (g->Fc[1][c](i, j + 1, k) - g->Fc[1][c](i, j, k));
             u = u - cz * (g->Fc[2][c](i, j, k + 1) - g->Fc[2][c](i, j, k));
             g->q[c](i, j, k) = u;
           }
+        }
+    FLOP_SECTION(SEC_NONE);
   }
   // Step 11: b^{n+1} = b^n - dt curl E^{n+1/2}; zone B from face averages
   {
@@ -1086,7 +1163,7 @@ int or_totals(const or_grid* g, double tot[8]) {
     for (int k = 0; k < n[2]; ++k)
       for (int j = 0; j < n[1]; ++j)
         for (int i = 0; i < n[0]; ++i) {
-          double x = c < 5 ? g->q[c](i, j, k) : g->b[c - 5](i, j, k);
+          double x = to_d(c < 5 ? g->q[c](i, j, k) : g->b[c - 5](i, j, k));
           double t = s + x;
           if (std::fabs(s) >= std::fabs(x)) comp += (s - t) + x;
           else comp += (x - t) + s;
@@ -1103,9 +1180,9 @@ double or_divb_max(const or_grid* g) {
   for (int k = 0; k < n[2]; ++k)
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i) {
-        double dv = (g->b[0](i + 1, j, k) - g->b[0](i, j, k)) / g->dxv[0] +
-                    (g->b[1](i, j + 1, k) - g->b[1](i, j, k)) / g->dxv[1] +
-                    (g->b[2](i, j, k + 1) - g->b[2](i, j, k)) / g->dxv[2];
+        double dv = (to_d(g->b[0](i + 1, j, k)) - to_d(g->b[0](i, j, k))) / g->dxv[0] +
+                    (to_d(g->b[1](i, j + 1, k)) - to_d(g->b[1](i, j, k))) / g->dxv[1] +
+                    (to_d(g->b[2](i, j, k + 1)) - to_d(g->b[2](i, j, k))) / g->dxv[2];
         if (std::fabs(dv) > m) m = std::fabs(dv);
       }
   return m;
@@ -1134,7 +1211,7 @@ int or_set_protection(or_grid* g, double prot_rho, double prot_p) {
 long long or_stage(const or_grid* g, int which, double* out, long long cap) {
   const int* n = g->n;
   long long w = 0;
-  auto put = [&](double x) { if (w < cap) out[w] = x; ++w; };
+  auto put = [&](real x) { if (w < cap) out[w] = to_d(x); ++w; };
   if (which >= 0 && which < 6) {
     int d = which % 3;
     const Arr* F = which < 3 ? g->Fp[d] : g->Fc[d];
@@ -1170,16 +1247,16 @@ int or_face_eigen(const double qL[8], const double qR[8], double b, double gamma
   Eigen e;
   roe_state(pl, pr, b, gamma, &e);
   if (e.bad) return 4;
-  double dq[7];
+  real dq[7];
   cons_diff(cl, cr, dq);
   for (int k = 0; k < 7; ++k) {
-    lam[k] = e.lam[k];
-    double s = 0.0;
+    lam[k] = to_d(e.lam[k]);
+    real s = 0.0;
     for (int m = 0; m < 7; ++m) s += e.L[k][m] * dq[m];
-    alpha[k] = s;
+    alpha[k] = to_d(s);
     for (int m = 0; m < 7; ++m) {
-      R[m * 7 + k] = e.R[m][k];
-      L[k * 7 + m] = e.L[k][m];
+      R[m * 7 + k] = to_d(e.R[m][k]);
+      L[k * 7 + m] = to_d(e.L[k][m]);
     }
   }
   return 0;
@@ -1202,8 +1279,35 @@ int or_flux_pencil(int ncell, const double* cells, const double* bface, double d
     const double* q = cells + (size_t)i * 8;
     c[i] = Cell{q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7]};
   }
-  return pencil_flux(ncell, c.data(), bface, dtdx, dx_over_2dt, P,
-                     reinterpret_cast<double(*)[7]>(out));
+  std::vector<real> bf(bface, bface + ncell + 1);
+  std::vector<real> fl((size_t)(ncell + 1) * 7);
+  for (size_t m = 0; m < fl.size(); ++m) fl[m] = out[m];
+  int nh = pencil_flux(ncell, c.data(), bf.data(), dtdx, dx_over_2dt, P,
+                       reinterpret_cast<real(*)[7]>(fl.data()));
+  for (size_t m = 0; m < fl.size(); ++m) out[m] = to_d(fl[m]);
+  return nh;
+}
+
+// Operation counts of the counting build, per section (flop_count.h): the
+// FP64 operations and the units (zones, faces, edges) evaluated since the last
+// reset.  Returns the number of sections, or -1 in the ordinary build.
+int or_flop_report(long long* flops, long long* units, int cap) {
+#ifdef ORACLE_COUNT_FLOPS
+  for (int s = 0; s < flopcount::SEC_COUNT && s < cap; ++s) {
+    flops[s] = flopcount::flops[s];
+    units[s] = flopcount::units[s];
+  }
+  return flopcount::SEC_COUNT;
+#else
+  (void)flops; (void)units; (void)cap;
+  return -1;
+#endif
+}
+
+void or_flop_reset() {
+#ifdef ORACLE_COUNT_FLOPS
+  for (int s = 0; s < flopcount::SEC_COUNT; ++s) flopcount::flops[s] = flopcount::units[s] = 0;
+#endif
 }
 
 // Independent 1D driver (the RJ95 one-dimensional scheme, App. A Eq.

@@ -96,6 +96,13 @@ int or_flux_pencil(int ncell, const double* cells, const double* bface,
 int or_step_1d(int n, double* q, double b, double dt, double dx, double gamma,
                const double eps[7], double sweby, double prot_rho, double prot_p, int outflow);
 
+/* Operation counting (only in the build with -DORACLE_COUNT_FLOPS): per
+ * section of the step (flop_count.h), the FP64 operations counted and the
+ * units evaluated since the last or_flop_reset.  Returns the number of
+ * sections written, or -1 in the ordinary build. */
+int or_flop_report(long long* flops, long long* units, int cap);
+void or_flop_reset(void);
+
 #ifdef __cplusplus
 }
 #endif

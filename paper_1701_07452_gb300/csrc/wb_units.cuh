@@ -699,7 +699,7 @@ __device__ __forceinline__ void trans_dir(const WbView& v, long long w, const Tr
   const long long sD = D == 0 ? 1 : (D == 1 ? v.geo.sy : v.geo.sz);
   const double hm2 = wb_minmod(z.hdb[D], wb_flip(z.hdb[t1]));  // for the t2 field component
   const double hm1 = wb_minmod(z.hdb[D], wb_flip(z.hdb[t2]));  // for the t1 field component
-  const double hSe = __fma_rn(z.Bv[D], z.hdb[D], __fma_rn(z.Bv[t1], hm1, __dmul_rn(z.Bv[t2], hm2)));
+  const double hSe = __fma_rn(z.Bv[t1], hm1, __dmul_rn(z.Bv[t2], hm2));
   const double c1 = z.c[t1], c2 = z.c[t2];
   double u[8];
 #pragma unroll

@@ -2,7 +2,8 @@
 persistent kernel with per-box dt (wb_batch_*), or by one launch per stage
 (the staged form), compared with the single-box grid path, alone vs in the
 mix, graph vs direct launch, persistent vs staged, after autotuning, and
-with a barrier wait forced to run out (error status, context still usable)."""
+with a barrier wait forced to run out (error status, context still usable);
+every box of a mix against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -165,3 +166,46 @@ def test_mixed_boundaries_both_forms(wb):
         g.advance(4)
         for a, c, e in zip(runs[0][i], runs[1][i], g.read()):
             assert np.array_equal(a, c) and np.array_equal(a, e), i
+
+
+@pytest.mark.parametrize("form", ["persistent", "staged"])
+def test_batch_boxes_match_the_oracle(wb, oracle_mod, form):
+    """Every box of an uneven mix (periodic and outflow, several workspace
+    groups) against the FP64 oracle on the same seeded input: within 1e-11
+    after one step and 1e-10 after ten, each box on its own CFL dt; totals of
+    the periodic boxes to 1e-12."""
+    from parity import state_err
+    sizes = SIZES + [(20, 18, 16)]
+    bcs = [(0, 0, 0), (1, 1, 1), (0, 0, 0), (0, 1, 0), (1, 0, 1), (0, 0, 0)]
+    boxes, states = boxes_and_states(sizes, seed0=700)
+    for b, bc in zip(boxes, bcs):
+        b["bc"] = bc
+    bt = wb.Batch(boxes, work_budget=8 << 20)
+    bt.set_form(form)
+    assert bt.get_config()["groups"] > 1
+    for i, st in enumerate(states):
+        bt.load_state(i, st)
+    orc = []
+    for b, st in zip(boxes, states):
+        o = oracle_mod.Grid(b["n"], b["length"], bc=b["bc"])
+        o.load_state(st)
+        orc.append(o)
+    t_o = [0.0] * len(orc)
+    for steps, tol in ((1, 1e-11), (9, 1e-10)):
+        bt.set_steps(-1, steps)
+        bt.advance(steps)
+        for i, o in enumerate(orc):
+            t_o[i] += o.advance(steps)
+            assert state_err(bt.read(i), o.read()) < tol, (i, steps)
+            c = bt.counters(i)
+            assert c["unphysical"] == 0 and c["steps"] == 1 + (steps == 9) * 9
+            assert abs(c["t"] - t_o[i]) <= 1e-13 * t_o[i], i
+    for i, o in enumerate(orc):
+        if boxes[i]["bc"] != (0, 0, 0):
+            continue
+        g_tot = wb.Grid(boxes[i]["n"], length=boxes[i]["length"])
+        U, bx, by, bz, _ = bt.read(i)
+        g_tot.load(U, bx, by, bz)
+        tg, to = g_tot.totals(), o.totals()
+        scale = np.array([abs(to[0])] * 4 + [abs(to[4])] + [1.0] * 3)
+        assert np.all(np.abs(tg - to) <= 1e-12 * np.maximum(scale, np.abs(to))), i

@@ -78,6 +78,25 @@ def test_turbulence_parity_100_steps(wb, oracle_mod):
     assert state_err(g.read(), o.read()) < 1e-8
 
 
+def test_turbulence_parity_100_steps_balanced_sweep(wb, oracle_mod):
+    """100 steps of the turbulence data at 64^3, where every sweep launch runs
+    the balanced form (equal runs of 32-pencil-group faces per resident warp,
+    the form the 256^3 bench box takes), against the oracle at 1e-8; totals
+    to 1e-12 of their scale."""
+    from paper_1701_07452_gb300.initial_conditions import turbulence_box
+    n = (64, 64, 64)
+    st = turbulence_box(n, seed=2)
+    g, o = make_pair(wb, oracle_mod, st, n)
+    t_g = g.advance(100)
+    t_o = o.advance(100)
+    assert abs(t_g - t_o) <= 1e-11 * t_o
+    assert state_err(g.read(), o.read()) < 1e-8
+    tg, to = g.totals(), o.totals()
+    scale = np.array([abs(to[0])] * 4 + [abs(to[4])] + [1.0] * 3)
+    assert np.all(np.abs(tg - to) <= 1e-12 * np.maximum(scale, np.abs(to)))
+    assert g.counters()["unphysical"] == 0
+
+
 @pytest.mark.parametrize("n,patches,batch", [(32, (2, 2, 2), 5), (32, (4, 2, 1), 5), (32, (8, 8, 8), 5),
                                               (64, (2, 2, 2), 3), (48, (3, 1, 2), 0), (32, (2, 2, 2), 0),
                                               (32, (4, 2, 1), 0)])

@@ -1,7 +1,7 @@
 """Serving pattern on the GPU: runs that arrive while others are resident are
 admitted as memory frees up, share launches, and each result is bit-identical
 to the same run served alone, under either tick policy and either batch
-form."""
+form, and within tolerance of the FP64 oracle run of the same request."""
 import numpy as np
 import pytest
 
@@ -92,3 +92,22 @@ def test_an_unphysical_run_fails_alone(mods):
         (arec,) = alone.run([serve.Request(r.rid, 0.0, r.n, r.steps, r.state, r.length)])
         for a, b in zip(arec.result, rec.result):
             assert np.array_equal(a, b), r.rid
+
+
+def test_served_results_match_the_oracle(mods, oracle_mod):
+    """Each served run (admitted under the budget, sharing launches with the
+    others) against the FP64 oracle advanced by the same number of steps on
+    the same seeded input: within 1e-10 (4 to 9 steps)."""
+    from parity import state_err
+    binding, serve = mods
+    reqs = requests()
+    per = max(11 * 8 * (n[0] + 10) * (n[1] + 10) * (n[2] + 10) for n in [r.n for r in reqs])
+    srv = serve.Server(state_bytes=2 * per + 4096, work_bytes=64 << 20, max_boxes=8, max_n=32,
+                       tick_steps=2, keep_results=True, policy="srpt", tick_cells=2 * 14 ** 3)
+    recs = srv.run(reqs)
+    for r, rec in zip(reqs, recs):
+        assert rec.status == "done"
+        o = oracle_mod.Grid(r.n, r.length)
+        o.load_state(r.state)
+        o.advance(r.steps)
+        assert state_err(rec.result, o.read()) < 1e-10, r.rid

@@ -279,8 +279,8 @@ def test_div_b_source_momentum_is_the_missing_flux_derivative(oracle_mod):
     source is isolated as the difference of the oracle's q^{n+1/2}_d with the
     source on and off (a test ablation), so a wrong sign or size of the
     momentum source, or a difference taken along the wrong axis, fails here.
-    (The energy and induction parts follow GS08's minmod choices, which this
-    does not fix.)"""
+    (The energy and induction rows are pinned the same way below, on data
+    where their minmod limiter is inactive.)"""
     n = (8, 8, 8)
     st = random_box(n, seed=31)
     g0 = oracle_mod.Grid(n, st["length"])
@@ -313,3 +313,126 @@ def test_div_b_source_momentum_is_the_missing_flux_derivative(oracle_mod):
             assert scale > 1e-4
             worst = max(worst, np.abs(got - want).max() / scale)
     assert worst < 1e-8, worst
+
+
+def _linear_face_box(n, grads, b0, seed):
+    """Periodic box of random zone states whose face fields grow linearly along
+    their own axis: b_e = b0_e + grads[e] * (face coordinate), so every zone
+    away from the periodic wrap sees the face differences db_e/dx_e = grads[e]
+    (the field is deliberately not solenoidal: the source of Steps 5 and 7 is
+    a function of the three differences, whatever their sum)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n
+    W = np.zeros((5, nz, ny, nx))
+    W[0] = 1.0 + 0.2 * rng.uniform(-1, 1, (nz, ny, nx))
+    for c in (1, 2, 3):
+        W[c] = 0.4 * rng.uniform(-1, 1, (nz, ny, nx))
+    W[4] = 0.8 + 0.2 * rng.uniform(-1, 1, (nz, ny, nx))
+    dx = 1.0 / np.array(n, dtype=float)
+    fx = np.arange(nx + 1) * dx[0]
+    fy = np.arange(ny + 1) * dx[1]
+    fz = np.arange(nz + 1) * dx[2]
+    bx = np.broadcast_to(b0[0] + grads[0] * fx[None, None, :], (nz, ny, nx + 1)).copy()
+    by = np.broadcast_to(b0[1] + grads[1] * fy[None, :, None], (nz, ny + 1, nx)).copy()
+    bz = np.broadcast_to(b0[2] + grads[2] * fz[:, None, None], (nz + 1, ny, nx)).copy()
+    return W, bx, by, bz
+
+
+def _isolated_source(oracle_mod, n, W, bx, by, bz, d):
+    """S_d of q^{n+1/2}_d (Steps 5, 7) isolated as the difference of the
+    oracle's transverse state with the source on and off (a test ablation)."""
+    dumps = []
+    for s in (1.0, 0.0):
+        g = oracle_mod.Grid(n, (1.0, 1.0, 1.0))
+        g.load_primitive(W, bx, by, bz)
+        dt = g.dt()
+        g.set_source_scale(s)
+        assert g.step(dt) == 0
+        dumps.append(g.stage(9 + d).reshape(8, n[2], n[1], n[0]))
+    return (dumps[0] - dumps[1]) / (0.5 * dt), dt
+
+
+def _missing_flux_derivative(U, B, d):
+    """-(dF_d/dB_d) for every row of the paper's flux vector (Sec. 3, written
+    out in linear_waves._flux), by complex step at fixed (rho, M, E - B_d^2/2,
+    B_t): the part of the d-flux gradient a sweep along d leaves out when it
+    holds B_d fixed (reading R4).  Rows (rho, Md, Mt1, Mt2, Bt1, Bt2, E)."""
+    t1, t2 = (d + 1) % 3, (d + 2) % 3
+    rho, M, E = U[0], U[1:4], U[4]
+    h = 1e-30
+    bn = B[d] + 1j * h
+    eref = E - 0.5 * B[d] ** 2
+    u = [rho, M[d], M[t1], M[t2], B[t1], B[t2], eref + 0.5 * bn * bn]
+    return -lw._flux(u, bn, lw.GAMMA).imag / h
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_div_b_source_energy_and_induction_are_the_missing_flux_derivative(oracle_mod, d):
+    """The energy and induction rows of the div B source of Steps 5 and 7
+    (reading R13) against the physics they must supply.  A sweep along d
+    evolves the 7-variable system with B_d held fixed and its energy referred
+    to the normal field (E - B_d^2/2, reading R4); the d-flux gradient it
+    leaves out is -(dF_d/dB_d) db_d/dx_d, for the transverse field components
+    (v_t db_d) and for the energy ((B_t . v_t) db_d) as for the momentum.
+    GS08 limits the induction and energy shares by minmod(db_d, -db_t) of the
+    other transverse axis; on data where both limiters pick db_d (here
+    db_t1 = -2 db_d and db_t2 = -3 db_d, uniform) the source must equal that
+    derivative in every row.  A wrong sign, a swapped component, an extra
+    term (such as B_d v_d db_d in the energy) or a difference along the wrong
+    axis fails here."""
+    n = (8, 8, 8)
+    g0 = 0.35
+    grads = [0.0, 0.0, 0.0]
+    grads[d] = g0
+    grads[(d + 1) % 3] = -2.0 * g0
+    grads[(d + 2) % 3] = -3.0 * g0
+    W, bx, by, bz = _linear_face_box(n, grads, (0.45, -0.4, 0.3), seed=50 + d)
+    S, _ = _isolated_source(oracle_mod, n, W, bx, by, bz, d)
+    g = oracle_mod.Grid(n, (1.0, 1.0, 1.0))
+    g.load_primitive(W, bx, by, bz)
+    U, _, _, _, B = g.read()
+    want = _missing_flux_derivative(U, B, d) * grads[d]
+    t1, t2 = (d + 1) % 3, (d + 2) % 3
+    inner = (slice(0, n[2] - 1), slice(0, n[1] - 1), slice(0, n[0] - 1))  # away from the wrap
+    rows = {0: 0, 1: 1 + d, 2: 1 + t1, 3: 1 + t2, 4: 5 + t1, 5: 5 + t2, 6: 4}
+    worst = 0.0
+    for row, comp in rows.items():
+        got = S[comp][inner]
+        w = want[row][inner]
+        scale = max(np.abs(want[1:]).max(), 1e-300)
+        worst = max(worst, float(np.abs(got - w).max() / scale))
+    assert worst < 1e-8, worst
+    assert np.abs(want[6][inner]).max() > 1e-3   # the energy row is exercised
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_div_b_source_pairing_reduces_to_the_planar_problem(oracle_mod, d):
+    """The minmod pairing of the induction source (reading R13): on a
+    solenoidal field that is uniform along t2 (the planar problem of
+    Sec. "MHD in Two Dimensions" seen from a d-sweep), db_d = -db_t1, so the
+    out-of-plane component B_t2 and its energy share must receive the whole
+    missing flux derivative v_t2 db_d, (B_t2 v_t2) db_d -- its limiter, which
+    compares db_d with the t1 difference that carries the same divergence,
+    must not act.  A pairing with the other transverse axis (db_t2 = 0) would
+    give zero.  The in-plane component B_t1 is limited against db_t2 = 0 and
+    receives nothing, as in the planar scheme whose in-plane field the corner
+    EMFs carry."""
+    n = (8, 8, 8)
+    g0 = 0.3
+    grads = [0.0, 0.0, 0.0]
+    grads[d] = g0
+    grads[(d + 1) % 3] = -g0
+    W, bx, by, bz = _linear_face_box(n, grads, (0.45, -0.4, 0.3), seed=60 + d)
+    S, _ = _isolated_source(oracle_mod, n, W, bx, by, bz, d)
+    g = oracle_mod.Grid(n, (1.0, 1.0, 1.0))
+    g.load_primitive(W, bx, by, bz)
+    U, _, _, _, B = g.read()
+    t1, t2 = (d + 1) % 3, (d + 2) % 3
+    v = U[1:4] / U[0]
+    inner = (slice(0, n[2] - 1), slice(0, n[1] - 1), slice(0, n[0] - 1))
+    want_bt2 = (v[t2] * g0)[inner]
+    want_e = (B[t2] * v[t2] * g0)[inner]
+    scale = np.abs(want_bt2).max()
+    assert np.abs(S[5 + t2][inner] - want_bt2).max() < 1e-8 * scale
+    assert np.abs(S[4][inner] - want_e).max() < 1e-8 * max(np.abs(want_e).max(), 1e-300)
+    assert np.abs(S[5 + t1][inner]).max() < 1e-8 * scale
