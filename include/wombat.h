@@ -190,16 +190,17 @@ int wb_profile_sweeps(wb_grid* g, int enable);
 int wb_profile_read(wb_grid* g, double* sweep_ms, long long* launches);
 
 /* One CTU+CT step of a single small box that allocates no device memory.
- * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc (code running while a stream is being captured into
- * a CUDA graph, allocator-restricted plug-ins, or hosts that hand over only
- * device buffers), so it cannot size a wb_grid workspace for them.  Its
- * intermediates live in a static device array of 24 MiB inside this library
- * (held by every GPU that loads the library until process exit).  A box
- * needs about 520 (nx+10)(ny+10)(nz+10) + 8 (nx+1)(ny+1)(nz+1) bytes of it
- * (state, one step's intermediates with keep_stages = 0, reductions), so
- * cubes up to 25^3 interior zones fit; larger boxes return WB_ERR_INVALID
- * with a message in wb_noalloc_last_error().
+ * The paper has no counterpart.  Some callers cannot call cudaMalloc: a
+ * plug-in inside a host application that owns every device allocation, an
+ * embedding that is handed device buffers and nothing else, or a real-time
+ * loop in which cudaMalloc's implicit device synchronisation is not allowed.
+ * They cannot give wb_grid_create a workspace, so this entry point keeps one
+ * step's intermediates in a static device array of 24 MiB inside this
+ * library (held by every GPU that loads the library until process exit).  A
+ * box needs about 520 (nx+10)(ny+10)(nz+10) + 8 (nx+1)(ny+1)(nz+1) bytes of
+ * it (state, one step's intermediates with keep_stages = 0, reductions): a
+ * cube of 26^3 interior zones fits, 27^3 does not; a box that does not fit
+ * returns WB_ERR_INVALID with a message in wb_noalloc_last_error().
  *  d        descriptor of one box: patches must be (1,1,1); batch_patches is
  *           ignored
  *  U, bx, by, bz          device input state (layouts above)
@@ -210,10 +211,13 @@ int wb_profile_read(wb_grid* g, double* sweep_ms, long long* launches);
  *           synchronise and does not report unphysical states (they show as
  *           non-finite outputs).
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
- * Every call on a device shares the one array: calls whose GPU work overlaps
- * (other streams, other threads) race and corrupt each other's results, so
- * serialise them on one stream. */
+ * cudaGetSymbolAddress (a host-side set-up done once per device); make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one array and finds the previous call's contents in it (the call clears
+ * what must start at zero): calls whose GPU work overlaps (other streams,
+ * other threads) race and corrupt each other's results, so serialise them on
+ * one stream.  wb_noalloc_last_error returns the message of the calling
+ * thread's last failed call (valid until that thread's next call). */
 int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const double* by,
                     const double* bz, double* U_out, double* bx_out, double* by_out,
                     double* bz_out, double* dt_out, void* stream);

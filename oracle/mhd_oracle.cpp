@@ -214,8 +214,10 @@ void roe_state(const Prim& pL, const Prim& pR, real b, double gamma, Eigen* e) {
     if (a2 >= ca2) { e->af = 1.0; e->as = 0.0; }
     else { e->af = 0.0; e->as = 1.0; }
   } else {
-    // cf^2 - a^2 and a^2 - cs^2 without cancellation
-    real t1 = ca2 + ct2 - a2;
+    // cf^2 - a^2 and a^2 - cs^2 without cancellation (ca^2 - a^2 first: the
+    // difference of two nearly equal squares is exact, a sum rounded before
+    // it is not)
+    real t1 = (ca2 - a2) + ct2;
     real cf2_a2 = (t1 >= 0.0) ? 0.5 * (t1 + sd) : 2.0 * a2 * ct2 / (sd - t1);
     real t2 = a2 - ca2 + ct2;
     real cf2_ca2 = (t2 >= 0.0) ? 0.5 * (t2 + sd) : 2.0 * ca2 * ct2 / (sd - t2);
@@ -1148,9 +1150,14 @@ int or_step(or_grid* g, double dt) {
     for (int d = 0; d < 3; ++d) g->b[d].d.swap(tmp[d].d);
   }
   long long unph0 = g->unphysical;
+  // Step 11: the zone field is the average of the face field as the boundary
+  // condition leaves it, so the face ghosts are filled first (on an outflow
+  // axis the high boundary face becomes a copy of the last owned face,
+  // reading R16); then the zone fields and their ghosts
+  for (int d = 0; d < 3; ++d) fill_array(g, g->b[d], d);
   apply_floors_and_ccb(g);
   g->hll_faces += nhll;
-  ghost_fill(g);
+  for (int v = 0; v < 8; ++v) fill_array(g, g->q[v], -1);
   return g->unphysical > unph0 ? 4 : 0;
 }
 

@@ -160,6 +160,13 @@ struct BoxInfo {
   int wrap;  // periodic on every axis: interior-only stages + periodic images
 };
 
+// Axes whose high boundary face is an outflow copy of the last owned face
+// (every box is its own domain): the final update's zone-field rule there.
+__device__ __forceinline__ int outflow_mask(const BoxInfo& bi) {
+  return (bi.bc[0] == WB_BC_OUTFLOW ? 1 : 0) | (bi.bc[1] == WB_BC_OUTFLOW ? 2 : 0) |
+         (bi.bc[2] == WB_BC_OUTFLOW ? 4 : 0);
+}
+
 struct BatchParams {
   const BoxInfo* boxes;
   WbScalars* scal;            // per box
@@ -276,7 +283,7 @@ __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, in
     }
     case BS_EREF_H: wbu::eref_half(v, 0, 0, dt, i, j, k); break;
     case BS_FINAL: {
-      const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, hits, bad);
+      const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, outflow_mask(bi), hits, bad);
       *wmax = fmax(*wmax, w);
       if (w != w) *wmax = w;
       break;
@@ -703,7 +710,7 @@ __global__ void __launch_bounds__(kNtZone, zone_min_blocks(CLS))
       } else if (CLS == SC_EREF_H) {
         wbu::eref_half(v, 0, 0, dt, i, j, k);
       } else {
-        const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, &hits, &bad);
+        const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, outflow_mask(bi), &hits, &bad);
         wmax = fmax(wmax, w);
         if (w != w) wmax = w;
       }

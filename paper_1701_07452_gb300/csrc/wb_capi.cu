@@ -195,6 +195,7 @@ WbPhys wb_phys_of(const wb_desc* d) {
     p.eps[k] = d->eps[k];
     p.two_eps[k] = 2.0 * d->eps[k];
     p.inv4eps[k] = d->eps[k] > 0.0 ? 1.0 / (4.0 * d->eps[k]) : 0.0;
+    p.inv4eps_m1[k] = d->eps[k] > 0.0 ? p.inv4eps[k] - 1.0 : 0.0;
     if (d->eps[k] == 0.0) p.eps_zero |= 1 << k;
   }
   p.sweby = d->sweby_beta;
@@ -249,6 +250,12 @@ StageArgs stage_args(wb_grid* g, long long p0, int nslots) {
   v.scal = g->scal;
   a.phys = g->phys;
   a.nslots = nslots;
+  a.p0 = p0;
+  a.ohi_bc = 0;
+  for (int d = 0; d < 3; ++d) {
+    a.np[d] = g->map.np[d];
+    if (g->map.bc[d] == WB_BC_OUTFLOW) a.ohi_bc |= 1 << d;
+  }
   return a;
 }
 
@@ -841,10 +848,9 @@ static __device__ __align__(256) double wb_noalloc_scratch[kNoallocBytes / sizeo
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[256];  // device address of the array, per device ordinal
-std::string g_noalloc_err;
+thread_local std::string g_noalloc_err;  // the calling thread's last failure
 
 int noalloc_fail(int code, const std::string& msg) {
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
   g_noalloc_err = msg;
   return code;
 }
@@ -872,7 +878,7 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
     char buf[200];
     std::snprintf(buf, sizeof(buf),
                   "box %dx%dx%d needs %zu bytes of scratch; the static limit is %zu bytes "
-                  "(24 MiB, cubes up to 25^3 zones)",
+                  "(24 MiB: cubes up to 26^3 zones)",
                   d->n[0], d->n[1], d->n[2], L.total, kNoallocBytes);
     return noalloc_fail(WB_ERR_INVALID, buf);
   }
@@ -885,10 +891,8 @@ int wb_step_noalloc(const wb_desc* d, const double* U, const double* bx, const d
     if (!g_noalloc_addr[dev]) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, wb_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        g_noalloc_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-        return WB_ERR_CUDA;
-      }
+      if (e != cudaSuccess || !p)
+        return noalloc_fail(WB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_noalloc_addr[dev] = p;
     }
     base = g_noalloc_addr[dev];

@@ -14,6 +14,7 @@ struct WbPhys {
   float gamma_f;  // gamma for the FP32 screen of the signal rate
   double hgm2;  // (gamma - 2) / 2
   double eps[7], two_eps[7], inv4eps[7];
+  double inv4eps_m1[7];  // 1/(4 eps_k) - 1: Q_k(nu) - nu^2 = nu^2 (1/(4 eps) - 1) + eps
   int eps_zero;  // bit k set when eps_k == 0
   double sweby;
   int minmod;  // sweby == 1

@@ -33,6 +33,12 @@ struct StageArgs {
   long long slot_q, slot_w;
   WbPhys phys;
   int nslots;
+  // the final update's view of the domain boundary: slot s holds patch
+  // p0 + s of a grid with np[] patches per axis; bit a of ohi_bc is set when
+  // axis a is outflow (its high boundary face is a copy of the last owned one)
+  long long p0;
+  int np[3];
+  int ohi_bc;
 };
 
 // Global description needed by the halo fill and by load/read scatter.

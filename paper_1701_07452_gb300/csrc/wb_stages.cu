@@ -159,8 +159,15 @@ __global__ void k_final(StageArgs A) {
   const bool ok = box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k);
   double w = 0.0;
   int hits = 0, bad = 0;
+  // axes along which this slot's patch is the last one of an outflow axis
+  const long long p = A.p0 + blockIdx.y;
+  const long long pc[3] = {p % A.np[0], (p / A.np[0]) % A.np[1], p / ((long long)A.np[0] * A.np[1])};
+  int ohi = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (((A.ohi_bc >> d) & 1) && pc[d] == A.np[d] - 1) ohi |= 1 << d;
   if (ok) w = wbu::final_update(A.v, blockIdx.y * A.slot_q, blockIdx.y * A.slot_w, dt, A.phys, i, j, k,
-                                &hits, &bad);
+                                ohi, &hits, &bad);
   if (hits) atomicAdd((unsigned long long*)&A.v.scal->floor_hits, (unsigned long long)hits);
   if (bad) atomicAdd((unsigned long long*)&A.v.scal->unphysical, (unsigned long long)bad);
   block_max_atomic(w, &A.v.scal->wmax_next);

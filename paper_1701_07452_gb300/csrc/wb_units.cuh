@@ -78,8 +78,10 @@ __device__ __forceinline__ void load_cell(const double* const* q, long long off,
   const double me = wb_half(__dadd_rn(bn2, bt2));
   const double p = __dmul_rn(P.gm1, __dsub_rn(__dsub_rn(e, ke), me));
   const double pstar = __dadd_rn(p, me);
+  const double ep = __dadd_rn(e, pstar);
   c.eref = __dsub_rn(e, wb_half(bn2));
-  c.hr = __dmul_rn(__dadd_rn(__fma_rn(P.g_over_gm1, p, ke), bt2), c.ir);
+  // rho h = gamma/(gamma-1) P + rho v^2/2 + |B_t|^2 = (E + P*) - B_n^2
+  c.hr = __dmul_rn(__dsub_rn(ep, bn2), c.ir);
   // half fluxes: the face needs (F_L + F_R) / 2
   const double hmn = wb_half(c.mn), hvn = wb_half(c.vn), hbn = wb_half(bn);
   c.F[0] = hmn;
@@ -89,7 +91,7 @@ __device__ __forceinline__ void load_cell(const double* const* q, long long off,
   c.F[4] = __fma_rn(c.bt1, hvn, __dmul_rn(-hbn, c.vt1));
   c.F[5] = __fma_rn(c.bt2, hvn, __dmul_rn(-hbn, c.vt2));
   const double bv = __fma_rn(c.bt2, c.vt2, __fma_rn(c.bt1, c.vt1, __dmul_rn(bn, c.vn)));
-  c.F[6] = __fma_rn(__dadd_rn(e, pstar), hvn, __dmul_rn(-hbn, bv));
+  c.F[6] = __fma_rn(ep, hvn, __dmul_rn(-hbn, bv));
 }
 
 // Per-face record (shared memory, structure of arrays over the block).
@@ -124,9 +126,9 @@ using Rec = RecT<kBlock>;
 // EZ have eps_k = 0, where Q is |nu|; the branch test runs on the integer pipe.
 template <int EZ>
 __device__ __forceinline__ double Qk_m_nu2(double nu, int k, const WbPhys& P) {
-  if (EZ & (1 << k)) return WB_FMA(-nu, nu, wb_fabs(nu));
-  const double q = wb_abs_less(nu, P.two_eps[k]) ? WB_FMA(WB_MUL(nu, nu), P.inv4eps[k], P.eps[k]) : wb_fabs(nu);
-  return WB_FMA(-nu, nu, q);
+  if ((EZ & (1 << k)) || !wb_abs_less(nu, P.two_eps[k])) return WB_FMA(-nu, nu, wb_fabs(nu));
+  // |nu| < 2 eps: nu^2 / (4 eps) + eps - nu^2 = nu^2 (1/(4 eps) - 1) + eps
+  return WB_FMA(WB_MUL(nu, nu), P.inv4eps_m1[k], P.eps[k]);
 }
 
 // Gas pressure of a zone from its sweep-frame fields (Sec. 3, Eq. totenergy)
@@ -248,37 +250,41 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   const double ca = WB_MUL(wb_fabs(b), isrho);
   const double cf = WB_MUL(cf2, icf);
   const double cs = WB_MUL(WB_MUL(a, ca), icf);  // c_f c_s = a c_a
+  // 1/|B_t| and c_t = |B_t| / sqrt(rho_); a transverse field whose square is
+  // not a normal double (underflowing noise ahead of a front) counts as 0
+  double ib = 0.0, ct = 0.0;
+  if (wb_normal_pos(bt2s)) {
+    ib = wb_rsqrt(bt2s);
+    ct = WB_MUL(WB_MUL(bt2s, ib), isrho);
+  }
   double af, as;
   if (wb_le_nonneg(sd, WB_MUL(1e-12, sum))) {
     const bool fast = wb_le_nonneg(ca2, a2);
     af = fast ? 1.0 : 0.0;
     as = fast ? 0.0 : 1.0;
   } else {
-    // cf^2 - a^2 and cf^2 - ca^2 without cancellation; at most one of the
-    // two needs a quotient
-    const double t1 = WB_SUB(WB_ADD(ca2, ct2), a2);
-    const double t2 = WB_ADD(WB_SUB(a2, ca2), ct2);
-    const bool n1 = wb_neg(t1), n2 = wb_neg(t2);
-    double qd = 0.0;
-    if (n1 || n2) {
-      const double num = n1 ? WB_MUL(WB_MUL(2.0, a2), ct2) : WB_MUL(WB_MUL(2.0, ca2), ct2);
-      const double den = n1 ? WB_SUB(sd, t1) : WB_SUB(sd, t2);
-      qd = WB_MUL(num, wb_rcp(den));
-    }
-    const double cf2_a2 = n1 ? qd : wb_half(WB_ADD(t1, sd));
-    const double cf2_ca2 = n2 ? qd : wb_half(WB_ADD(t2, sd));
-    const double af2 = wb_clamp01(WB_MUL(WB_MUL(WB_MUL(a2, cf2_ca2), WB_MUL(icf, icf)), rsd));
-    const double as2 = wb_clamp01(WB_MUL(cf2_a2, rsd));
-    // subnormal squares (from underflowing transverse fields) count as 0
-    af = wb_normal_pos(af2) ? WB_MUL(af2, wb_rsqrt(af2)) : 0.0;
-    as = wb_normal_pos(as2) ? WB_MUL(as2, wb_rsqrt(as2)) : 0.0;
+    // With t1 = ca^2 + ct^2 - a^2: alpha_f^2 = (sd - t1) / (2 sd) and
+    // alpha_s^2 = (sd + t1) / (2 sd) (cf^2 + cs^2 = a^2 + ca^2 + ct^2,
+    // cf^2 - cs^2 = sd), and (sd - t1)(sd + t1) = disc - t1^2 = 4 a^2 ct^2,
+    // so alpha_f alpha_s = a ct / sd.  The larger of the two comes from its
+    // square, x = (sd + |t1|) / (2 sd) in [1/2, 1], without cancellation, and
+    // the smaller from the product: a ct / (sd larger) = a ct rsd / sqrt(x).
+    // t1 takes the difference ca^2 - a^2 first: it is exact where the two
+    // nearly cancel (the degenerate neighbourhood, where sd is small).
+    const double t1 = WB_ADD(WB_SUB(ca2, a2), ct2);
+    const bool slow_major = !wb_neg(t1);
+    const double x = wb_half(WB_MUL(WB_ADD(sd, slow_major ? t1 : wb_flip(t1)), rsd));
+    const double y = wb_rsqrt(x);
+    const double major = WB_MUL(x, y);
+    const double minor = WB_MUL(WB_MUL(WB_MUL(a, ct), rsd), y);
+    af = slow_major ? minor : major;
+    as = slow_major ? major : minor;
   }
   const double ra2 = WB_MUL(rho, a2);
   double b1n, b2n;
   if (wb_le_nonneg(bt2s, WB_MUL(1e-24, WB_ADD(WB_ADD(ra2, b2), bt2s)))) {
     b1n = b2n = 0.70710678118654752440;
   } else {
-    const double ib = wb_rsqrt(bt2s);
     b1n = WB_MUL(bt1, ib);
     b2n = WB_MUL(bt2, ib);
   }
@@ -915,10 +921,14 @@ __device__ __forceinline__ double signal_rate(double rho, double mx, double my, 
 // rate): U^{n+1} = ((U^n - dt/dx dF*) - dt/dy dG*) - dt/dz dH* at one interior
 // zone, zone B = mean of b^{n+1}.  Returns the zone's signal rate (NaN if the
 // state is unphysical); floor hits are added to *hits.  The rate is the one
-// signal_rate gives for the stored result.
+// signal_rate gives for the stored result.  ohi: bit d set when the zone
+// row's high end along d is the domain boundary of an outflow axis, whose
+// boundary face the ghost fill makes a copy of the last owned face (the
+// zero-gradient rule); the last zone's field then averages that copy, so the
+// stored state is the one a load of the same faces gives.
 __device__ __forceinline__ double final_update(const WbView& v, long long qo, long long wo,
                                                double dt, const WbPhys& P, int i, int j, int k,
-                                               int* hits, int* bad) {
+                                               int ohi, int* hits, int* bad) {
   const WbGeo& g = v.geo;
   const long long q = qo + wb_at(g, i, j, k);
   const long long wi = wo + wb_at(g, i, j, k);
@@ -936,9 +946,13 @@ __device__ __forceinline__ double final_update(const WbView& v, long long qo, lo
     u[c] = x;
   }
   double B[3];
+  const int idx[3] = {i, j, k};
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    B[e] = wb_half(__dadd_rn(v.b[e][q], v.b[e][q + s[e]]));
+    const bool last = ((ohi >> e) & 1) && idx[e] == g.n[e] - 1;
+    const double lo = v.b[e][q];
+    const double hi = last ? lo : v.b[e][q + s[e]];
+    B[e] = wb_half(__dadd_rn(lo, hi));
     v.q[F_BX + e][q] = B[e];
   }
   // the tests below run on the integer pipe (FP64 compares take FP64 issue)

@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = ["random_box", "turbulence_box", "turbulence_box_device", "expansion_box", "mode_table",
            "curl_faces", "cpaw_box", "field_loop_box", "shock_tube_1d", "blast_box", "SHOCK_TUBES",
-           "orszag_tang_box", "random_box_2d", "State"]
+           "orszag_tang_box", "random_box_2d", "shock_tube_rotated", "curl_faces_open", "State"]
 
 
 class State(dict):
@@ -244,6 +244,79 @@ def shock_tube_1d(name, n):
     by = np.repeat(by_z[None, None, :], 2, axis=1)
     bz = np.repeat(bz_z[None, None, :], 2, axis=0)
     return State(W=W, bx=bx, by=by, bz=bz, length=(1.0, 1e3, 1e3))
+
+
+ROTATED_N = np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0)
+ROTATED_E2 = np.array([-1.0, 1.0, 0.0]) / math.sqrt(2.0)
+ROTATED_E3 = np.cross(ROTATED_N, ROTATED_E2)
+
+
+def curl_faces_open(Ax, Ay, Az, dx, dy, dz):
+    """Face fields b = curl A of a non-periodic box from edge potentials that
+    include the high edges: Ax[nz+1][ny+1][nx] on ((i+1/2)dx, j dy, k dz),
+    Ay[nz+1][ny][nx+1] on (i dx, (j+1/2)dy, k dz), Az[nz][ny+1][nx+1] on
+    (i dx, j dy, (k+1/2)dz).  Returns bx[nz][ny][nx+1], by[nz][ny+1][nx],
+    bz[nz+1][ny][nx] with every face of the box, so that each zone's
+    discrete div b is zero to rounding."""
+    bx = (Az[:, 1:, :] - Az[:, :-1, :]) / dy - (Ay[1:, :, :] - Ay[:-1, :, :]) / dz
+    by = (Ax[1:, :, :] - Ax[:-1, :, :]) / dz - (Az[:, :, 1:] - Az[:, :, :-1]) / dx
+    bz = (Ay[:, :, 1:] - Ay[:, :, :-1]) / dx - (Ax[:, 1:, :] - Ax[:, :-1, :]) / dy
+    return bx, by, bz
+
+
+def shock_tube_rotated(name, n, boost=(0.0, 0.0)):
+    """The named shock tube in an n^3 cube of side 1 (outflow on every axis)
+    with its normal along n = (1, 1, 1)/sqrt 3, equally inclined to the three
+    primary planes (Sec. "RJ95 2a" tilts the normal out of all of them), the
+    discontinuity on the plane through the box centre.  The
+    1D states (rho, v_n, v_t2, v_t3, B_t2, B_t3, P), B_n, are laid out in the
+    frame (n, e2, e3); the field is B_n n + curl(G3(s) e2 - G2(s) e3) with
+    s = n . (x - centre) and G2, G3 the continuous piecewise-linear integrals
+    of B_t2, B_t3, evaluated on the edges (div b = 0 to rounding).  boost =
+    (V2, V3) adds the uniform velocity V2 e2 + V3 e3 to both states (MHD is
+    Galilean invariant: the solution is the same, its transverse velocity
+    shifted by the boost)."""
+    st = SHOCK_TUBES[name]
+    d = 1.0 / n
+    e1, e2, e3 = ROTATED_N, ROTATED_E2, ROTATED_E3
+    L, R = st["left"], st["right"]
+
+    def coords(xo, yo, zo, sx, sy, sz):
+        i = (np.arange(sx) + xo)[None, None, :] * d - 0.5
+        j = (np.arange(sy) + yo)[None, :, None] * d - 0.5
+        k = (np.arange(sz) + zo)[:, None, None] * d - 0.5
+        return i, j, k
+
+    x, y, z = coords(0.5, 0.5, 0.5, n, n, n)
+    sc = e1[0] * x + e1[1] * y + e1[2] * z
+    left = sc < 0.0
+    W = np.empty((5, n, n, n))
+    W[0] = np.where(left, L[0], R[0])
+    vn = np.where(left, L[1], R[1])
+    v2 = np.where(left, L[2], R[2]) + boost[0]
+    v3 = np.where(left, L[3], R[3]) + boost[1]
+    for a in range(3):
+        W[1 + a] = vn * e1[a] + v2 * e2[a] + v3 * e3[a]
+    W[4] = np.where(left, L[6], R[6])
+
+    def G(sv, bl, br):   # integral of a field that is bl for s < 0, br for s > 0
+        return np.where(sv < 0.0, bl * sv, br * sv)
+
+    bn = st["bx"]
+
+    def potential(comp, xo, yo, zo, sx, sy, sz):
+        xx, yy, zz = coords(xo, yo, zo, sx, sy, sz)
+        sv = e1[0] * xx + e1[1] * yy + e1[2] * zz
+        pos = (xx, yy, zz)
+        # (bn/2) (n x r) + G3(s) e2 - G2(s) e3
+        cross = 0.5 * bn * (e1[(comp + 1) % 3] * pos[(comp + 2) % 3] - e1[(comp + 2) % 3] * pos[(comp + 1) % 3])
+        return cross + G(sv, L[5], R[5]) * e2[comp] - G(sv, L[4], R[4]) * e3[comp]
+
+    Ax = potential(0, 0.5, 0.0, 0.0, n, n + 1, n + 1)
+    Ay = potential(1, 0.0, 0.5, 0.0, n + 1, n, n + 1)
+    Az = potential(2, 0.0, 0.0, 0.5, n + 1, n + 1, n)
+    bx, by, bz = curl_faces_open(Ax, Ay, Az, d, d, d)
+    return State(W=W, bx=bx, by=by, bz=bz, length=(1.0, 1.0, 1.0))
 
 
 def blast_box(nx, ny, nz, b0=10.0, p_in=100.0, r0=0.125, shift=(0.0, 0.0, 0.0)):

@@ -1,6 +1,8 @@
 """Linear-wave initial data of the paper's convergence tests (Sec. 'Linear Wave
 Convergence'): background rho = 1, P = 3/5, gamma = 5/3, B = (1, sqrt 2, 1/2),
-v_1 = 1, amplitude A0 = 1e-6 times a right eigenvector of the flux Jacobian.
+v_1 = 1 (or a background at rest, v = 0, as in the oblique setup the paper
+takes from GS08), amplitude A0 = 1e-6 times a right eigenvector of the flux
+Jacobian.
 The eigenvector comes from numpy's eigen-solver applied to the complex-step
 Jacobian of the paper's flux vector (Sec. 3), not from the oracle."""
 import math
@@ -25,15 +27,16 @@ def _flux(u, bn, gam):
                      (E + Ps) * vn - bn * (bn * vn + bt1 * vt1 + bt2 * vt2)])
 
 
-def background_u():
-    v, B = V_WAVE, B_WAVE
+def background_u(v=None):
+    v = V_WAVE if v is None else np.asarray(v, float)
+    B = B_WAVE
     E = PRES / (GAMMA - 1) + 0.5 * RHO * v @ v + 0.5 * B @ B
     return np.array([RHO, RHO * v[0], RHO * v[1], RHO * v[2], B[1], B[2], E])
 
 
-def eigenmode(mode):
+def eigenmode(mode, v=None):
     """(lambda, r) for the wave-frame 7-variable system (rho, M1, M2, M3, B2, B3, E)."""
-    u0 = background_u().astype(complex)
+    u0 = background_u(v).astype(complex)
     J = np.zeros((7, 7))
     for m in range(7):
         u = u0.copy()
@@ -69,15 +72,17 @@ def frame(kvec):
     return e1, e2, e3
 
 
-def state_oblique(mode, n, kvec=(1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0), length=(3.0, 1.5, 1.5)):
+def state_oblique(mode, n, kvec=(1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0), length=(3.0, 1.5, 1.5),
+                  v=None):
     """Oblique wave on a 2n x n x n grid of size (3, 3/2, 3/2), wave vector k
-    (wavelength 1); face b = uniform mean + curl of an edge potential."""
-    lam, r = eigenmode(mode)
+    (wavelength 1); face b = uniform mean + curl of an edge potential.  v: the
+    wave-frame background velocity (default (1, 0, 0); (0, 0, 0) at rest)."""
+    lam, r = eigenmode(mode, v)
     e1, e2, e3 = frame(kvec)
     nx, ny, nz = 2 * n, n, n
     dx, dy, dz = length[0] / nx, length[1] / ny, length[2] / nz
     R = np.stack([e1, e2, e3], axis=1)   # wave frame -> grid
-    u0 = background_u()
+    u0 = background_u(v)
     rho_b, m_b, e_b = u0[0], R @ u0[1:4], u0[6]
     Bbar = R @ B_WAVE
     dm = R @ r[1:4]

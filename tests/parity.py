@@ -1,33 +1,42 @@
 """Parity metric shared by the GPU tests: per-zone relative difference with a
-guard for sign-changing components, |g - o| / max(|o|, 1e-3 max_box |o|),
-taken over every variable of the state.  The guard keeps the metric a
-relative one wherever a component is at least 0.1 % of its box maximum; below
-that it bounds the absolute error by 1e-3 max|o| times the tolerance.  (The
-GPU contracts multiply-adds, the oracle does not, so zones where a momentum
-or field component crosses zero carry rounding differences of a few ulps of
-the box scale, which no finite relative bound without a guard can accept.)"""
+guard for sign-changing components, |g - o| / max(|o|, guard max_box |o|),
+taken over every variable of the state.  Two guards are used:
+  * GUARD = 1e-3 (the default): relative wherever a component is at least
+    0.1 % of its box maximum, an absolute bound of 1e-3 max|o| times the
+    tolerance below that;
+  * TIGHT = 1e-6: relative down to a millionth of the box maximum.
+The GPU evaluates the step in other algebraic forms (closed-form
+projections, fused multiply-adds) than the oracle, so where a momentum or
+field component crosses zero the two differ by a few ulps of the box scale;
+no finite relative bound without a guard can accept those zones.  The tests
+assert the stated tolerances under both guards (1e-11 after one step, 1e-8
+after 100 steps; after 10 steps 1e-10 under GUARD, 1e-8 under TIGHT)."""
 import numpy as np
 
 
-def rel_err(g, o, guard=1e-3):
+GUARD = 1e-3
+TIGHT = 1e-6
+
+
+def rel_err(g, o, guard=GUARD):
     g = np.asarray(g, dtype=np.float64)
     o = np.asarray(o, dtype=np.float64)
     scale = np.maximum(np.abs(o), guard * max(np.abs(o).max(), 1e-300))
     return float(np.max(np.abs(g - o) / scale))
 
 
-def state_err(gs, os_):
+def state_err(gs, os_, guard=GUARD):
     """gs, os_: (U, bx, by, bz, B) tuples; worst rel_err over variables."""
     worst = 0.0
     U1, U2 = gs[0], os_[0]
     for c in range(U1.shape[0]):
-        worst = max(worst, rel_err(U1[c], U2[c]))
+        worst = max(worst, rel_err(U1[c], U2[c], guard))
     for a, b in zip(gs[1:], os_[1:]):
         if a.ndim == 4:
             for c in range(a.shape[0]):
-                worst = max(worst, rel_err(a[c], b[c]))
+                worst = max(worst, rel_err(a[c], b[c], guard))
         else:
-            worst = max(worst, rel_err(a, b))
+            worst = max(worst, rel_err(a, b, guard))
     return worst
 
 
