@@ -18,7 +18,8 @@
 //                             one exchange per step
 //   hll_flux, protection      App. A, the protection floor and the HLL flux
 //                             (Eqs. for u-bar of the HLL scheme, b+ and b-)
-// Readings where the paper is silent are tagged R1..R21 as in the design notes.
+// Readings where the paper is silent are tagged R1..R27; the comment at each
+// tag states the reading taken.
 //
 // The div B source of Steps 5 and 7 (reading R13, after GS08, which is not
 // available) is pinned to the flux derivative it supplies in every row

@@ -43,7 +43,8 @@ int or_load_primitive(or_grid* g, const double* W, const double* bx, const doubl
                       const double* bz);
 int or_read(const or_grid* g, double* U, double* bx, double* by, double* bz,
             double* B);
-/* CFL time step from the current state (reading R3 of the design notes). */
+/* CFL time step from the current state: C_cfl / max over interior zones of
+ * sum_d (|v_d| + c_f,d) / dx_d (the paper gives no formula; reading R3). */
 double or_compute_dt(const or_grid* g);
 /* One CTU+CT step with the given dt. Returns 0 or 4 (unphysical). */
 int or_step(or_grid* g, double dt);

@@ -451,7 +451,8 @@ __device__ __forceinline__ void unit_pair(int s, int d, const BoxInfo& bi, long 
   else unit_pair_emf(s, d, bi, it0, it1, dt);
 }
 
-// dt of one box for the coming step (reading R3 of the design notes)
+// dt of one box for the coming step: C_cfl / max zone signal rate, the rate
+// sum_d (|v_d| + c_f,d) / dx_d (reading R3)
 __device__ void box_dt(const BatchParams& B, int box) {
   WbScalars* s = B.scal + box;
   if (B.steps_left[box] <= 0) { s->dt = 0.0; return; }
