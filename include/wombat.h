@@ -45,7 +45,10 @@ extern "C" {
 #define WB_ERR_TIMEOUT 5     /* a bounded device wait ran out */
 
 #define WB_BC_PERIODIC 0
-#define WB_BC_OUTFLOW 1      /* zero-gradient copy of the nearest zone */
+#define WB_BC_OUTFLOW 1      /* zero-gradient copy of the nearest zone; on the high side the
+                                boundary face is a copy of the last owned face, and the
+                                last zone's field averages that copy (Step 11), so a read
+                                followed by a load gives the same state */
 
 /* Grid of equal patches (Sec. "Domain Decomposition": a Patch is a
  * self-contained sub-grid with its own 5 boundary zones).
