@@ -441,8 +441,10 @@ def serve_figures(requests, steps_scale=1.0, policies=("srpt",)):
         reqs.append(sv.Request(r, float(arrivals[r]), (int(ns[r]),) * 3, int(nsteps[r]), st))
     runs = {}
     for policy in policies:
+        # srpt: up to 25 steps per tick for the runs of least remaining work,
+        # 4e6 zones per step (1e8 cell-updates per tick)
         srv = sv.Server(state_bytes=150 << 30, work_bytes=40 << 30, max_boxes=requests,
-                        max_n=int(ns.max()), tick_steps=5, policy=policy, tick_cells=1.5e8)
+                        max_n=int(ns.max()), tick_steps=25, policy=policy, tick_cells=1e8)
         recs = srv.run(reqs)
         runs[policy] = (sv.summarize(recs), srv.ticks)
         del srv
@@ -454,8 +456,9 @@ def serve_figures(requests, steps_scale=1.0, policies=("srpt",)):
            "ticks": ticks, "policy": policies[0],
            "workload": f"{requests} requests, Poisson 50/s (seed 5), edge log-uniform 32..192, "
                        f"steps U{{50..500}}" + (f" x {steps_scale}" if steps_scale != 1.0 else "") +
-                       ", turbulence data seed 5000+r, 150 GB state budget, 5 steps per tick "
-                       "(srpt: least remaining work first, up to 1.5e8 cell-updates per tick)"}
+                       ", turbulence data seed 5000+r, 150 GB state budget, 25 steps per tick "
+                       "(srpt: least remaining work first, up to 4e6 zones a step, 1e8 cell-updates "
+                       "per tick)"}
     for policy in policies[1:]:
         o = runs[policy][0]
         res[policy] = {"cell_updates_per_s": o["cell_updates_per_s"], "p50_s": o["p50_s"],

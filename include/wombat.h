@@ -235,8 +235,12 @@ const char* wb_noalloc_last_error(void);
  * from a device work counter, and a bounded grid-wide barrier separates the
  * stages of a step.  The state of all boxes stays resident; the step's
  * intermediates are shared by workspace groups of boxes whose combined
- * workspace fits work_budget bytes (0 = 64 GiB).  Boxes are periodic or
- * outflow on their own; patches must be (1,1,1).
+ * workspace fits work_budget bytes (0 = 64 GiB).  Only boxes with steps
+ * granted by wb_batch_set_steps are grouped (all resident boxes while none
+ * has any), so a launch does no stage work for the others; a change of that
+ * set regroups the batch before the next launch (and re-captures its
+ * graph).  Boxes are periodic or outflow on their own; patches must be
+ * (1,1,1).
  * wb_batch_bytes / wb_batch_create: caller-owned device memory as for grids.
  * wb_batch_load: as wb_load_state / wb_load_primitive for one box.
  * wb_batch_set_steps: steps left for one box (box = -1: all boxes); a box with

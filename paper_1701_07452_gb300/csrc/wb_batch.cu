@@ -763,6 +763,12 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 struct wb_batch {
   int cap;
   std::vector<char> alive;
+  // steps granted by the last wb_batch_set_steps per box (host mirror), and
+  // whether the box sits in the current workspace groups: only boxes with
+  // steps granted are grouped, so a pool whose policy runs a few of its
+  // resident runs per launch does not pay for the others' stage work lists
+  std::vector<int> granted;
+  std::vector<char> grouped;
   std::vector<wb_desc> d;
   std::vector<WbGeo> geo;
   std::vector<BoxInfo> info;
@@ -900,6 +906,19 @@ void build_prefix(const wb_batch* b, std::vector<long long>& pre, std::vector<lo
     }
 }
 
+// Whether box i belongs in the workspace groups: a resident box with steps
+// granted; when no box has steps granted, every resident box (a batch before
+// its first wb_batch_set_steps is grouped as a whole).
+bool any_granted(const wb_batch* b) {
+  for (int j = 0; j < b->cap; ++j)
+    if (b->alive[j] && b->granted[j] > 0) return true;
+  return false;
+}
+
+bool wants_group(const wb_batch* b, int i, bool any) {
+  return b->alive[i] && (!any || b->granted[i] > 0);
+}
+
 // Regroup the resident boxes (in slot order) into workspace groups, point
 // their workspace views into the shared region and upload every table.
 int rebuild(wb_batch* b) {
@@ -912,11 +931,14 @@ int rebuild(wb_batch* b) {
   // the longest items (the big boxes' pencil segments) and ends with the
   // shortest, so the blocks that finish last leave little idle time
   std::vector<int> order;
-  for (int i = 0; i < b->cap; ++i)
-    if (b->alive[i]) {
-      order.push_back(i);
-      b->nbox = i + 1;
-    }
+  std::vector<char> want(b->cap);
+  const bool any = any_granted(b);
+  for (int i = 0; i < b->cap; ++i) want[i] = wants_group(b, i, any);
+  for (int i = 0; i < b->cap; ++i) {
+    b->grouped[i] = want[i];
+    if (b->alive[i]) b->nbox = i + 1;
+    if (b->grouped[i]) order.push_back(i);
+  }
   std::stable_sort(order.begin(), order.end(), [b](int x, int y) { return b->geo[x].V > b->geo[y].V; });
   for (int i : order) {
     const WbGeo& g = b->geo[i];
@@ -1136,6 +1158,8 @@ int wb_pool_create(const wb_desc* physics, size_t state_bytes, size_t work_bytes
   PoolSizes P = pool_sizes(state_bytes, work_bytes, max_boxes, max_n);
   b->cap = max_boxes;
   b->alive.assign(max_boxes, 0);
+  b->granted.assign(max_boxes, 0);
+  b->grouped.assign(max_boxes, 0);
   b->d.resize(max_boxes);
   b->geo.resize(max_boxes);
   b->info.resize(max_boxes);
@@ -1226,6 +1250,7 @@ int wb_pool_admit(wb_batch* b, const wb_desc* d, int* box) {
   b->free_.erase(it);
   if (len > need) b->free_[off + need] = len - need;
   b->alive[slot] = 1;
+  b->granted[slot] = 0;
   b->d[slot] = *d;
   b->geo[slot] = g;
   b->state_off[slot] = off;
@@ -1265,6 +1290,7 @@ int wb_pool_release(wb_batch* b, int box) {
   }
   b->free_[off] = len;
   b->alive[box] = 0;
+  b->granted[box] = 0;
   b->dirty = true;
   cudaError_t e = cudaMemsetAsync(b->d_steps + box, 0, sizeof(int), b->stream);
   return bcuda(b, e, "release");
@@ -1412,6 +1438,13 @@ int wb_batch_set_steps(wb_batch* b, int box, int nsteps) {
   if (box < 0)
     for (int i = 0; i < b->cap; ++i)
       if (!b->alive[i]) v[i] = 0;
+  for (int i = 0; i < count; ++i) b->granted[first + i] = v[i];
+  const bool any = any_granted(b);
+  for (int i = 0; i < b->cap; ++i)
+    if (wants_group(b, i, any) != (b->grouped[i] != 0)) {
+      b->dirty = true;
+      break;
+    }
   cudaError_t e = cudaMemcpyAsync(b->d_steps + first, v.data(), sizeof(int) * count, cudaMemcpyHostToDevice,
                                   b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

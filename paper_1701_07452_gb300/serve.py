@@ -23,9 +23,14 @@ the bench, 136 about 5 % slower).
 Two tick policies.  "fair": every resident run advances up to tick_steps per
 tick (processor sharing).  "srpt": each tick grants up to tick_steps steps to
 the resident runs in order of least remaining work (zones x steps left)
-until the granted cell-updates reach tick_cells, the rest wait; short runs
-then finish within a few ticks of admission while the GPU stays full.  A
-run's result does not depend on the policy (each box advances on its own).
+until the granted cell-updates reach tick_cells, the rest wait.  The zones a
+step carries, tick_cells / tick_steps, set the latency of short runs: a run
+advances one step per step of the tick, so with many steps per tick and few
+zones per step (25 and 4e6 on the bench's stream) short runs finish soon
+after admission, while the pool launches only the granted runs' work (runs
+without steps are left out of its workspace groups) and the GPU stays
+nearly as busy.  A run's result does not depend on the policy (each box
+advances on its own).
 """
 from __future__ import annotations
 
