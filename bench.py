@@ -703,6 +703,14 @@ def main():
                          "sweep_share_of_step": sweep_ms / ms},
             "step_roofline": step_roofline(value, peak),
             "cpu_baseline": cpu,
+            "paper_context": {
+                "note": "the paper's own CPU figures for the same 3D CTU+CT MHDTVD step (context, "
+                        "not a target; other hardware, unstated initial data)",
+                "zone_updates_per_s_per_node": {"XC_KNL Xeon Phi 7250": 6.5e6, "XC_BDW 2x Xeon E5-2695": 4.5e6,
+                                                "XE_IL Opteron 6281": 2.0e6},
+                "single_broadwell_core_cce": 2.7e5,
+                "source": "Sec. 'Patch Size Optimization'; Table 'Effect of vectorization on floating "
+                          "point instruction count' (8 x 32^3 zones x 100 steps in 96 s)"},
             "clocks": clk_summary,
             "gpu_launches": launches_per_step * args.steps,
         }
