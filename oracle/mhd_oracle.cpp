@@ -191,7 +191,10 @@ void roe_state(const Prim& pL, const Prim& pR, real b, double gamma, Eigen* e) {
   real v2 = e->vn * e->vn + e->vt1 * e->vt1 + e->vt2 * e->vt2;
   real bt2sum = e->bt1 * e->bt1 + e->bt2 * e->bt2;
   e->a2 = (gamma - 1.0) * (H - 0.5 * v2 - (b * b + bt2sum) / e->rho) - (gamma - 2.0) * e->X;
-  if (!(e->a2 >= std::numeric_limits<double>::min())) {  // no real sound speed
+  // No usable sound speed: a^2 <= 0, or a^2 below the smallest normal double,
+  // where it has lost significant bits and the 1/(2 a^2) factors of the left
+  // eigenvectors (App. A) lose them too or overflow (below ~5.6e-309).
+  if (!(e->a2 >= std::numeric_limits<double>::min())) {
     e->bad = true;
     return;
   }
