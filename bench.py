@@ -67,14 +67,14 @@ ALG_FLOPS_PER_CELL_UPDATE = 5871.0
 # profiles/stages_96cube_fp64_counts.md).  Counted per face of the box the
 # figure leaves out the ~2 % of overlap systems a 256^3 launch adds.
 EXEC_FLOPS_PER_FACE = 449.6
-EXEC_STAGE_FLOPS_PER_ZONE = 442.9
+EXEC_STAGE_FLOPS_PER_ZONE = 444.0
 # DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the
 # mean of the six sweeps of a step from one ncu capture
 # (profiles/k_sweep_256cube_dram.md), valid only for the kernel sources it was
 # taken on (their SHA-256 over csrc/wb_sweep.cu, wb_units.cuh, wb_device.cuh);
 # the algorithmic figure is 128 B per face.
-SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.6815e9,
-                      "src_sha256": "3e1b5b2c6b146cdcd6aee1d0a7c5110398ba271d02a64a434cb19c86223387ef"}
+SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.6776e9,
+                      "src_sha256": "26e3c4ff6cfb4d6774dbb8065697758c9418a7bdf91fc6f8605f77f938f59036"}
 SWEEP_BYTES_PER_FACE = 128.0
 # algorithmic state bytes per cell-update: 5 conserved fields and 3 face fields
 # read and written once (the step's HBM roofline)

@@ -218,15 +218,18 @@ __device__ bool grid_barrier(const BatchParams& B, unsigned nblocks) {
   return s_ok != 0;
 }
 
-__device__ __forceinline__ void warp_max_atomic(double w, unsigned long long* dst) {
-  unsigned long long bits = (w >= 0.0) ? (unsigned long long)__double_as_longlong(w)
-                                       : (w != w ? 0x7ff8000000000000ULL : 0ULL);
+// Warp max of signal-rate keys (wb_rate_bits), one atomicMax per warp.
+__device__ __forceinline__ void warp_max_key(unsigned long long bits, unsigned long long* dst) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
     bits = other > bits ? other : bits;
   }
   if ((threadIdx.x & 31) == 0 && bits) atomicMax(dst, bits);
+}
+
+__device__ __forceinline__ void warp_max_atomic(double w, unsigned long long* dst) {
+  warp_max_key(wb_rate_bits(w), dst);
 }
 
 template <int D, int EZ, bool PROT>
@@ -254,7 +257,7 @@ __device__ __forceinline__ int sweep_item(const BoxInfo& bi, bool corr, const Wb
 template <int EZ, bool PROT>
 __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, int box,
                                           const BoxInfo& bi, long long item, double dt,
-                                          const wbu::Rec rec[2], double* wmax, int* hits, int* bad,
+                                          const wbu::Rec rec[2], unsigned long long* wkey, int* hits, int* bad,
                                           int* hll) {
   const WbView& v = bi.v;
   const int* n = v.geo.n;
@@ -284,8 +287,9 @@ __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, in
     case BS_EREF_H: wbu::eref_half(v, 0, 0, dt, i, j, k); break;
     case BS_FINAL: {
       const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, outflow_mask(bi), hits, bad);
-      *wmax = fmax(*wmax, w);
-      if (w != w) *wmax = w;
+      // running max of the rate keys: integer compares, and a NaN stays
+      const unsigned long long kw = wb_rate_bits(w);
+      if (kw > *wkey) *wkey = kw;
       break;
     }
     default: break;
@@ -558,22 +562,22 @@ __global__ void __launch_bounds__(wbu::kBlock, 4) k_batch(BatchParams B, int nst
             continue;
           }
           const double dt = *(volatile const double*)&B.scal[box].dt;
-          if (!(dt > 0.0)) continue;
+          if (!wb_pos(dt)) continue;
           const BoxInfo& bi = B.boxes[box];
           const long long nitems = stage_items(s, sub, bi.v.geo, bi.wrap != 0, B.seg_len);
           const long long i0 = (c - pre[lo]) * ipc;
           long long i1 = i0 + ipc;
           if (i1 > nitems) i1 = nitems;
-          double wmax = 0.0;
+          unsigned long long wkey = 0ULL;
           int hits = 0, bad = 0, hll = 0;
           if (stage_pairs(s)) {
             for (long long it = i0 + threadIdx.x; it < i1; it += 2 * kB)
               unit_pair(s, sub, bi, it, it + kB < i1 ? it + kB : -1, dt);
           } else {
             for (long long it = i0 + threadIdx.x; it < i1; it += kB)
-              unit_item<EZ, PROT>(B, s, sub, box, bi, it, dt, rec, &wmax, &hits, &bad, &hll);
+              unit_item<EZ, PROT>(B, s, sub, box, bi, it, dt, rec, &wkey, &hits, &bad, &hll);
           }
-          if (s == BS_FINAL) warp_max_atomic(wmax, &B.scal[box].wmax_next);
+          if (s == BS_FINAL) warp_max_key(wkey, &B.scal[box].wmax_next);
           if (hits) atomicAdd((unsigned long long*)&B.scal[box].floor_hits, (unsigned long long)hits);
           if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
           if (hll) atomicAdd((unsigned long long*)&B.scal[box].hll_faces, (unsigned long long)hll);
@@ -657,7 +661,7 @@ __global__ void __launch_bounds__(kB, 4) k_bstage_sweep(BatchParams B, int grp, 
   const bool corr = s == BS_CORR;
   drain_stage(B, grp, s, ctr, [&](int box, int d, long long cc) {
     const double dt = B.scal[box].dt;
-    if (!(dt > 0.0)) return;
+    if (!wb_pos(dt)) return;
     const BoxInfo& bi = B.boxes[box];
     const long long nitems = stage_items(s, d, bi.v.geo, bi.wrap != 0, B.seg_len);
     const long long it = cc * kB + threadIdx.x;
@@ -684,7 +688,7 @@ __global__ void __launch_bounds__(kNtZone, zone_min_blocks(CLS))
       return;
     }
     const double dt = B.scal[box].dt;
-    if (!(dt > 0.0)) return;
+    if (!wb_pos(dt)) return;
     const BoxInfo& bi = B.boxes[box];
     const long long nitems = stage_items(s, d, bi.v.geo, bi.wrap != 0, B.seg_len);
     const long long i0 = cc * ipc;
@@ -700,7 +704,7 @@ __global__ void __launch_bounds__(kNtZone, zone_min_blocks(CLS))
     }
     const WbView& v = bi.v;
     const WbBox b = stage_box(s, d, v.geo.n, bi.wrap != 0);
-    double wmax = 0.0;
+    unsigned long long wkey = 0ULL;
     int hits = 0, bad = 0;
     for (long long it = i0 + threadIdx.x; it < i1; it += NT) {
       int i, j, k;
@@ -712,12 +716,12 @@ __global__ void __launch_bounds__(kNtZone, zone_min_blocks(CLS))
         wbu::eref_half(v, 0, 0, dt, i, j, k);
       } else {
         const double w = wbu::final_update(v, 0, 0, dt, B.phys, i, j, k, outflow_mask(bi), &hits, &bad);
-        wmax = fmax(wmax, w);
-        if (w != w) wmax = w;
+        const unsigned long long kw = wb_rate_bits(w);
+        if (kw > wkey) wkey = kw;
       }
     }
     if (CLS == SC_FINAL) {
-      warp_max_atomic(wmax, &B.scal[box].wmax_next);
+      warp_max_key(wkey, &B.scal[box].wmax_next);
       if (hits) atomicAdd((unsigned long long*)&B.scal[box].floor_hits, (unsigned long long)hits);
       if (bad) atomicAdd((unsigned long long*)&B.scal[box].unphysical, (unsigned long long)bad);
     }

@@ -204,9 +204,14 @@ __device__ __forceinline__ bool wb_normal_pos(double x) {
   const long long b = __double_as_longlong(x);
   return b >= 0x0010000000000000LL && b < 0x7ff0000000000000LL;
 }
-// x == 0 (either sign)
+// x == 0 (either sign), on the integer pipe.  The sign bit is shifted out of
+// the high word in PTX: written as a C expression on the bit pattern the test
+// is exactly x == 0.0, which the compiler emits as an FP64 compare (an
+// FP64-pipe instruction, counted by a probe kernel's counters).
 __device__ __forceinline__ bool wb_zero(double x) {
-  return (__double_as_longlong(x) << 1) == 0;
+  int h;
+  asm("shl.b32 %0, %1, 1;" : "=r"(h) : "r"(__double2hiint(x)));
+  return (h | __double2loint(x)) == 0;
 }
 // a <= b for a, b >= 0 (non-negative, non-NaN operands)
 __device__ __forceinline__ bool wb_le_nonneg(double a, double b) {
@@ -267,6 +272,18 @@ __device__ __forceinline__ double wb_copysign_abs(double mag, double s) {
   long long m = __double_as_longlong(mag) & 0x7fffffffffffffffLL;
   long long sg = __double_as_longlong(s) & (long long)0x8000000000000000ULL;
   return __longlong_as_double(m | sg);
+}
+
+// Key of a signal rate w for an unsigned atomicMax: the bits of w > 0, 0 for
+// w <= 0, the canonical NaN for any NaN (so that a NaN rate poisons the max),
+// from the bit pattern alone: the FP64 compares (w >= 0, w != w) would each
+// take an FP64-pipe instruction.
+__device__ __forceinline__ unsigned long long wb_rate_bits(double w) {
+  const long long b = __double_as_longlong(w);
+  int mh;
+  asm("and.b32 %0, %1, 0x7fffffff;" : "=r"(mh) : "r"(__double2hiint(w)));
+  const bool nan = mh > 0x7ff00000 || (mh == 0x7ff00000 && __double2loint(w) != 0);
+  return nan ? 0x7ff8000000000000ULL : (b > 0 ? (unsigned long long)b : 0ULL);
 }
 
 // atomic max of a non-negative double through its bit pattern (exact, order independent)

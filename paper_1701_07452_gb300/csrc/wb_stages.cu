@@ -28,7 +28,7 @@ inline dim3 grid_for(long long n, int nslots, int bs) {
 
 // Step 2: zone-centred reference EMF from q^n.
 __global__ void k_eref(StageArgs A, WbBox box) {
-  if (!(A.v.scal->dt > 0.0)) return;
+  if (!wb_pos(A.v.scal->dt)) return;
   int i, j, k;
   if (!box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   wbu::eref(A.v, blockIdx.y * A.slot_q, blockIdx.y * A.slot_w, i, j, k);
@@ -52,7 +52,7 @@ struct Boxes3 {
 // Steps 3 and 9: the three corner-EMF components, one thread per index of
 // the union of their boxes.
 __global__ void k_edges(StageArgs A, bool corr, Boxes3 B) {
-  if (!(A.v.scal->dt > 0.0)) return;
+  if (!wb_pos(A.v.scal->dt)) return;
   int i, j, k;
   if (!box_index(B.u, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long wo = blockIdx.y * A.slot_w;
@@ -64,7 +64,7 @@ __global__ void k_edges(StageArgs A, bool corr, Boxes3 B) {
 // Steps 4 and 11: constrained transport of the three face components.
 __global__ void k_ct(StageArgs A, bool fin, Boxes3 B) {
   const double dt = A.v.scal->dt;
-  if (!(dt > 0.0)) return;
+  if (!wb_pos(dt)) return;
   int i, j, k;
   if (!box_index(B.u, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long qo = blockIdx.y * A.slot_q, wo = blockIdx.y * A.slot_w;
@@ -77,7 +77,7 @@ __global__ void k_ct(StageArgs A, bool fin, Boxes3 B) {
 // directions of a zone in one thread.
 __global__ void k_transverse(StageArgs A, Boxes3 B) {
   const double dt = A.v.scal->dt;
-  if (!(dt > 0.0)) return;
+  if (!wb_pos(dt)) return;
   int i, j, k;
   if (!box_index(B.u, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const int mask = (wbu::in_box(B.b[0], i, j, k) ? 1 : 0) | (wbu::in_box(B.b[1], i, j, k) ? 2 : 0) |
@@ -88,7 +88,7 @@ __global__ void k_transverse(StageArgs A, Boxes3 B) {
 // Step 8: half-step reference EMF.
 __global__ void k_eref_half(StageArgs A, WbBox box) {
   const double dt = A.v.scal->dt;
-  if (!(dt > 0.0)) return;
+  if (!wb_pos(dt)) return;
   int i, j, k;
   if (!box_index(box, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   wbu::eref_half(A.v, blockIdx.y * A.slot_q, blockIdx.y * A.slot_w, dt, i, j, k);
@@ -138,9 +138,10 @@ __global__ void k_wrap_patches(WrapList L, WbGeo g, GridMap m, int depth, long l
 }
 
 __device__ __forceinline__ void block_max_atomic(double w, unsigned long long* dst) {
-  // warp-shuffle max, then one atomic per warp (exact, order independent)
-  unsigned long long bits = (w >= 0.0) ? (unsigned long long)__double_as_longlong(w)
-                                       : (w != w ? 0x7ff8000000000000ULL : 0ULL);
+  // warp-shuffle max, then one atomic per warp (exact, order independent);
+  // the bits of w >= 0, 0 for w < 0, the canonical NaN for any NaN (tests on
+  // the bit pattern: an FP64 compare takes an FP64-pipe instruction)
+  unsigned long long bits = wb_rate_bits(w);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
@@ -152,7 +153,7 @@ __device__ __forceinline__ void block_max_atomic(double w, unsigned long long* d
 // Step 10 (+ zone field of Step 11, floors, next signal rate) on interior zones.
 __global__ void k_final(StageArgs A) {
   const double dt = A.v.scal->dt;
-  if (!(dt > 0.0)) return;
+  if (!wb_pos(dt)) return;
   const WbGeo& g = A.v.geo;
   WbBox box = {{0, 0, 0}, {g.n[0] - 1, g.n[1] - 1, g.n[2] - 1}};
   int i, j, k;

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kBlock, WB_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs
   constexpr int W = (D == 2) ? 1 : 2;
   __shared__ double srec[2][wbu::R_WORDS][kBlock];
   const double dt = *A.dt;
-  if (!(dt > 0.0)) return;
+  if (!wb_pos(dt)) return;
   const int nu_ = A.box.hi[U] - A.box.lo[U] + 1;
   const int nw_ = A.box.hi[W] - A.box.lo[W] + 1;
   const long long npen = (long long)nu_ * nw_;

@@ -837,7 +837,7 @@ __device__ __forceinline__ double signal_rate_core(double ir, const double vv[3]
 // outside [2^-60, 2^61), subnormals, inf and NaN clear *ok.
 __device__ __forceinline__ float wb_f32_of(double x, bool* ok) {
   const long long b = __double_as_longlong(x);
-  if ((b << 1) == 0) return 0.0f;
+  if (wb_zero(x)) return 0.0f;
   const int hi = (int)(b >> 32);
   const int ex = (hi >> 20) & 0x7ff;
   if (ex < 1023 - 60 || ex > 1023 + 60) {
