@@ -66,15 +66,15 @@ ALG_FLOPS_PER_CELL_UPDATE = 5871.0
 # kernels of the step together (profiles/k_sweep_96cube_ncu_full.md,
 # profiles/stages_96cube_fp64_counts.md).  Counted per face of the box the
 # figure leaves out the ~2 % of overlap systems a 256^3 launch adds.
-EXEC_FLOPS_PER_FACE = 449.6
-EXEC_STAGE_FLOPS_PER_ZONE = 444.0
+EXEC_FLOPS_PER_FACE = 451.5
+EXEC_STAGE_FLOPS_PER_ZONE = 443.3
 # DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the
 # mean of the six sweeps of a step from one ncu capture
 # (profiles/k_sweep_256cube_dram.md), valid only for the kernel sources it was
 # taken on (their SHA-256 over csrc/wb_sweep.cu, wb_units.cuh, wb_device.cuh);
 # the algorithmic figure is 128 B per face.
-SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.6776e9,
-                      "src_sha256": "26e3c4ff6cfb4d6774dbb8065697758c9418a7bdf91fc6f8605f77f938f59036"}
+SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.6774e9,
+                      "src_sha256": "c9bd2e4865153e1d4165dffa00a9000d80cdbee60193294d502906606a7ad037"}
 SWEEP_BYTES_PER_FACE = 128.0
 # algorithmic state bytes per cell-update: 5 conserved fields and 3 face fields
 # read and written once (the step's HBM roofline)

@@ -194,8 +194,9 @@ WbPhys wb_phys_of(const wb_desc* d) {
   for (int k = 0; k < 7; ++k) {
     p.eps[k] = d->eps[k];
     p.two_eps[k] = 2.0 * d->eps[k];
-    p.inv4eps[k] = d->eps[k] > 0.0 ? 1.0 / (4.0 * d->eps[k]) : 0.0;
-    p.inv4eps_m1[k] = d->eps[k] > 0.0 ? p.inv4eps[k] - 1.0 : 0.0;
+    p.four_eps[k] = 4.0 * d->eps[k];
+    p.inv16eps[k] = d->eps[k] > 0.0 ? 1.0 / (16.0 * d->eps[k]) : 0.0;
+    p.inv4eps_m1[k] = d->eps[k] > 0.0 ? 1.0 / (4.0 * d->eps[k]) - 1.0 : 0.0;
     if (d->eps[k] == 0.0) p.eps_zero |= 1 << k;
   }
   p.sweby = d->sweby_beta;

@@ -13,7 +13,7 @@ struct WbPhys {
   double gamma, gm1, gm2, g_over_gm1, inv_gm1, gm2_over_gm1, cfl;
   float gamma_f;  // gamma for the FP32 screen of the signal rate
   double hgm2;  // (gamma - 2) / 2
-  double eps[7], two_eps[7], inv4eps[7];
+  double eps[7], two_eps[7], four_eps[7], inv16eps[7];
   double inv4eps_m1[7];  // 1/(4 eps_k) - 1: Q_k(nu) - nu^2 = nu^2 (1/(4 eps) - 1) + eps
   int eps_zero;  // bit k set when eps_k == 0
   double sweby;
@@ -216,6 +216,23 @@ __device__ __forceinline__ bool wb_zero(double x) {
 // a <= b for a, b >= 0 (non-negative, non-NaN operands)
 __device__ __forceinline__ bool wb_le_nonneg(double a, double b) {
   return __double_as_longlong(a) <= __double_as_longlong(b);
+}
+// 2 x, exact: the exponent field raised by one on the integer pipe for a
+// normal x whose double is normal; zero, subnormals, the top binade, inf and
+// NaN take an FP64 add (rare).
+__device__ __forceinline__ double wb_twice(double x) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (ex != 0 && ex < 0x7fe) return __hiloint2double(hi + (1 << 20), __double2loint(x));
+  return __dadd_rn(x, x);
+}
+// a < b in the order of the bit patterns read as sign and magnitude (the
+// order of the values, with -0 before +0; not for NaN), on the integer pipe
+__device__ __forceinline__ bool wb_order_less(double a, double b) {
+  long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
+  ka ^= (ka >> 63) & 0x7fffffffffffffffLL;
+  kb ^= (kb >> 63) & 0x7fffffffffffffffLL;
+  return ka < kb;
 }
 // min(max(x, 0), 1)
 __device__ __forceinline__ double wb_clamp01(double x) {

@@ -206,7 +206,7 @@ __device__ __forceinline__ void hll_face(const Cell& L, const Cell& R, double bn
   f[R_RHO] = kHllFace;
 }
 
-// Roe state, eigen-system, alpha_k, nu_k and g-tilde_k of one interface.
+// Roe state, eigen-system, alpha_k, nu_k and g-tilde_k (doubled) of one interface.
 // Returns 0 for an MHDTVD face, 1 when the protection floor asks for the HLL
 // flux (the record holds the Roe state), 2 when the Roe state has no real
 // sound speed (HLL without Roe speeds).  The protection test is compiled in
@@ -266,17 +266,17 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
     // With t1 = ca^2 + ct^2 - a^2: alpha_f^2 = (sd - t1) / (2 sd) and
     // alpha_s^2 = (sd + t1) / (2 sd) (cf^2 + cs^2 = a^2 + ca^2 + ct^2,
     // cf^2 - cs^2 = sd), and (sd - t1)(sd + t1) = disc - t1^2 = 4 a^2 ct^2,
-    // so alpha_f alpha_s = a ct / sd.  The larger of the two comes from its
-    // square, x = (sd + |t1|) / (2 sd) in [1/2, 1], without cancellation, and
-    // the smaller from the product: a ct / (sd larger) = a ct rsd / sqrt(x).
+    // so alpha_f alpha_s = a ct / sd.  The larger of the two is sqrt(m / (2 sd))
+    // with m = sd + |t1| (no cancellation), = m r for r = 1/sqrt(2 sd m), and
+    // the smaller a ct / (sd m r) = 2 a ct r: one reciprocal square root.
     // t1 takes the difference ca^2 - a^2 first: it is exact where the two
     // nearly cancel (the degenerate neighbourhood, where sd is small).
     const double t1 = WB_ADD(WB_SUB(ca2, a2), ct2);
     const bool slow_major = !wb_neg(t1);
-    const double x = wb_half(WB_MUL(WB_ADD(sd, slow_major ? t1 : wb_flip(t1)), rsd));
-    const double y = wb_rsqrt(x);
-    const double major = WB_MUL(x, y);
-    const double minor = WB_MUL(WB_MUL(WB_MUL(a, ct), rsd), y);
+    const double m = WB_ADD(sd, slow_major ? t1 : wb_flip(t1));
+    const double r = wb_rsqrt(wb_twice(WB_MUL(sd, m)));
+    const double major = WB_MUL(m, r);
+    const double minor = WB_MUL(WB_MUL(a, ct), wb_twice(r));
     af = slow_major ? minor : major;
     as = slow_major ? major : minor;
   }
@@ -334,7 +334,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
     const double nu = nuk[k];
     f[R_AL + k] = al[k];
     f[R_NU + k] = nu;
-    gt[k] = WB_MUL(Qk_m_nu2<EZ>(nu, k, P), wb_half(al[k]));
+    gt[k] = WB_MUL(Qk_m_nu2<EZ>(nu, k, P), al[k]);  // 2 g-tilde
   }
   f[R_RHO] = rho; f[R_SRHO] = srho; f[R_A] = a; f[R_PG] = WB_MUL(ra2, P.inv_gm1); f[R_CF] = cf;
   f[R_ASCS] = ascs; f[R_AFCF] = afcf; f[R_AF] = af; f[R_AS] = as; f[R_B1] = b1n; f[R_B2] = b2n; f[R_S] = S;
@@ -346,24 +346,33 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   return 0;
 }
 
-// beta_k of App. A without forming gamma_k: Q(nu + gamma) alpha equals
-// |nu alpha + dg| sign(alpha) when |nu alpha + dg| >= 2 eps |alpha|, else
-// (nu alpha + dg)^2 / (4 eps alpha) + eps alpha
+// beta_k of App. A from the limited slopes carried doubled, G = 2 g (the
+// limiter commutes with the factor 2), without forming gamma_k.  With
+// w = nu alpha + g_{i+1} - g_i, Q(nu + gamma) alpha = Q(w / alpha) alpha.  Where
+// Q(x) = |x| (eps_k = 0, or |w| >= 2 eps |alpha|) that is |w| sign(alpha), and
+// beta = |w| sign(alpha) - (g_i + g_{i+1}) is nu alpha - G_i when w has the sign
+// of alpha, else -nu alpha - G_{i+1}: the larger of the two for alpha > 0, the
+// smaller for alpha < 0, one FMA after an integer-pipe choice of operands.
+// Inside the band, Q(x) alpha = w^2 / (4 eps alpha) + eps alpha, with
+// 2 w = 2 nu alpha + G_{i+1} - G_i.  alpha = 0 needs no case of its own: this
+// face's g-tilde is then 0, the limiter makes G_i = G_{i+1} = 0 and either form
+// gives 0.
 template <int EZ>
-__device__ __forceinline__ double beta_k(double al, double nu, double gi, double gi1, int k,
+__device__ __forceinline__ double beta_k(double al, double nu, double Gi, double Gi1, int k,
                                          const WbPhys& P) {
-  const double w = WB_FMA(nu, al, WB_SUB(gi1, gi));  // (nu + gamma) alpha
-  double qa;
-  if (wb_zero(al)) {
-    qa = 0.0;                                           // gamma = 0, Q(nu) 0
-  } else if ((EZ & (1 << k)) || !wb_abs_less(w, WB_MUL(P.two_eps[k], al))) {
-    qa = wb_copysign_abs(w, al);                        // |nu + gamma| >= 2 eps
-  } else if (wb_abs_less(al, 1e-290)) {
-    qa = WB_MUL(P.eps[k], al);                          // w^2/(4 eps alpha) < eps |alpha|
-  } else {
-    qa = WB_FMA(WB_MUL(WB_MUL(w, w), P.inv4eps[k]), wb_rcp(al), WB_MUL(P.eps[k], al));
+  if (EZ & (1 << k)) {
+    const double b1 = WB_FMA(nu, al, -Gi), b2 = WB_FMA(-nu, al, -Gi1);
+    return (wb_order_less(b1, b2) != wb_neg(al)) ? b2 : b1;
   }
-  return WB_SUB(qa, WB_ADD(gi, gi1));
+  const double d = WB_FMA(wb_twice(nu), al, WB_SUB(Gi1, Gi));  // 2 w
+  if (!wb_abs_less(d, WB_MUL(P.four_eps[k], al))) {
+    const bool same = (__double_as_longlong(d) ^ __double_as_longlong(al)) >= 0;
+    return WB_FMA(same ? nu : wb_flip(nu), al, -(same ? Gi : Gi1));
+  }
+  // |nu + gamma| < 2 eps: beta = (2 w)^2 / (16 eps alpha) + eps alpha - (g_i + g_{i+1})
+  const double t = WB_FMA(P.eps[k], al, -wb_half(WB_ADD(Gi, Gi1)));
+  if (wb_abs_less(al, 1e-290)) return t;  // (2 w)^2 / (16 eps alpha) < eps |alpha|
+  return WB_FMA(WB_MUL(WB_MUL(d, d), P.inv16eps[k]), wb_rcp(al), t);
 }
 
 // u-bar = (F_L + F_R)/2 - (dx/(2 dt)) sum_k beta_k R_k  (App. A)
@@ -439,7 +448,7 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
   const double dx_2dt = WB_MUL(wb_half(g.dx[D]), wb_rcp(dt));
   Cell cL, cR;
   load_cell<D, NC>(q, off_in, P, cL);
-  double gt_p[7], g_p[7];  // g-tilde of face f-1; g of zone f-2
+  double gt_p[7], g_p[7];  // 2 g-tilde of face f-1; 2 g of zone f-2
   int nhll = 0;
   // HLL faces are counted on interior faces only (distinct faces, whatever
   // part of the ghost rings the region covers)
@@ -460,7 +469,7 @@ __device__ __forceinline__ int sweep_segment(const WbGeo& g, const double* const
       for (int k = 0; k < 7; ++k) gt[k] = 0.0;
     }
     if (f >= fa) {
-      // g of zone f-1 from g-tilde of faces f (i+1/2) and f-1 (i-1/2)
+      // 2 g of zone f-1 from 2 g-tilde of faces f (i+1/2) and f-1 (i-1/2)
       double gz[7];
 #pragma unroll
       for (int k = 0; k < 7; ++k) gz[k] = wb_sweby(gt[k], gt_p[k], P.sweby, P.minmod);
