@@ -71,6 +71,36 @@ def test_random_box_parity(wb, oracle_mod, n, steps, tol):
     assert g.counters()["unphysical"] == 0
 
 
+@pytest.mark.parametrize("eps,sweby", [
+    ((0.1, 0.05, 0.1, 0.02, 0.1, 0.05, 0.1), 1.0),   # every wave with an entropy fix: generic sweep
+    ((0.1, 0.0, 0.1, 0.0, 0.1, 0.0, 0.1), 1.5),      # the default eps_k, SWEBY beta = 1.5
+    ((0.0,) * 7, 2.0),                                # no entropy fix, SWEBY beta = 2
+    ((0.25, 0.0, 0.25, 0.0, 0.25, 0.0, 0.25), 1.0),   # a wide band on the fast and slow waves
+])
+def test_entropy_fix_and_limiter_parity(wb, oracle_mod, eps, sweby):
+    """The App. A flux with other entropy-fix parameters eps_k (the sweep
+    specialised for eps = 0 on the Alfven and entropy waves, and the generic
+    one, whose beta_k takes the Q_k band test on every wave) and other SWEBY
+    beta, against the oracle: 1e-11 after one step, 1e-10 after ten; a batch
+    box with the same parameters gives the grid's bits."""
+    from paper_1701_07452_gb300.initial_conditions import random_box
+    n = (24, 20, 16)
+    st = random_box(n, seed=7)
+    for steps, tol in ((1, 1e-11), (10, 1e-10)):
+        g, o = make_pair(wb, oracle_mod, st, n, eps=eps, sweby=sweby)
+        t_g = g.advance(steps)
+        t_o = o.advance(steps)
+        assert abs(t_g - t_o) <= 1e-13 * t_o
+        err = state_err(g.read(), o.read())
+        assert err < tol, (steps, err)
+    bt = wb.Batch([{"n": n, "length": st["length"]}], eps=eps, sweby=sweby)
+    bt.load_state(0, st)
+    bt.set_steps(-1, 10)
+    bt.advance(10)
+    for a, b in zip(bt.read(0), g.read()):
+        assert np.array_equal(a, b)
+
+
 def test_turbulence_parity_100_steps(wb, oracle_mod):
     from paper_1701_07452_gb300.initial_conditions import turbulence_box
     n = (24, 24, 24)
