@@ -324,6 +324,22 @@ int wb_batch_steps_left(wb_batch* b, int* out);
  * Uses the grid's reduction words; synchronises the grid's stream. */
 int wb_selftest_math(wb_grid* g, int n, double worst[2]);
 
+/* Self-test of the integer-pipe helpers the kernels use in place of FP64
+ * compares and sign operations (tests and edits on the IEEE bit patterns;
+ * each FP64 compare would take an FP64-pipe issue slot): counts[h] = the
+ * number of n inputs on which helper h disagrees with its FP64 definition,
+ * for h = 0 zero test (x == 0), 1 exact doubling (x + x), 2 order (a < b),
+ * 3 signal-rate max key, 4 x > 0 and finite, 5 x < 0, 6 positive normal,
+ * 7 |a| < |b|, 8 minmod, 9 halving (x / 2 for |x| >= 2^-1021), 10 |x|,
+ * 11 -x, 12 a <= b for a, b >= 0, 13 x below a finite floor >= 0,
+ * 14 finiteness.  The inputs: every pair of 16 special values (signed
+ * zeros, subnormals, the ends of the normal range, infinities, NaN), then
+ * random bit patterns with independent, adjacent, opposite or equal
+ * partners.  Uses the grid's reduction words; synchronises the grid's
+ * stream.  All counts are 0 for a correct build. */
+#define WB_BITS_TESTS 15
+int wb_selftest_bits(wb_grid* g, int n, long long counts[WB_BITS_TESTS]);
+
 /* Checked build (the library compiled with -DWB_CHECKED; a substitute for a
  * device memory checker): every zone index a kernel forms, and the stencil
  * neighbours of each stage, are tested against the padded storage of a

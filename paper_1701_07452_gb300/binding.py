@@ -25,7 +25,7 @@ EXPORTED = (
     "wb_load_primitive", "wb_compute_dt", "wb_advance", "wb_read_state", "wb_conserved_totals",
     "wb_divb_max", "wb_counters", "wb_last_error", "wb_debug_stage", "wb_measure_fp64_peak",
     "wb_profile_sweeps", "wb_profile_read", "wb_step_noalloc", "wb_noalloc_last_error",
-    "wb_selftest_math", "wb_batch_bytes", "wb_batch_create", "wb_batch_destroy", "wb_batch_load",
+    "wb_selftest_math", "wb_selftest_bits", "wb_batch_bytes", "wb_batch_create", "wb_batch_destroy", "wb_batch_load",
     "wb_batch_set_steps", "wb_batch_advance", "wb_batch_read", "wb_batch_counters",
     "wb_batch_autotune", "wb_batch_config", "wb_batch_get_config", "wb_batch_last_error",
     "wb_pool_bytes", "wb_pool_create", "wb_pool_admit", "wb_pool_release", "wb_pool_free_bytes",
@@ -119,6 +119,7 @@ def lib(build: bool = True):
             L.wb_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
             L.wb_step_noalloc.argtypes = [ctypes.POINTER(WbDesc)] + [vp] * 10
             L.wb_selftest_math.argtypes = [vp, ctypes.c_int, dp]
+            L.wb_selftest_bits.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
             L.wb_batch_bytes.argtypes = [ctypes.c_int, ctypes.POINTER(WbDesc), ctypes.c_size_t,
                                          ctypes.POINTER(ctypes.c_size_t)]
             L.wb_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(WbDesc), ctypes.c_size_t, vp,
@@ -318,6 +319,15 @@ class Grid:
         out = np.zeros(2)
         self._check(lib().wb_selftest_math(self._h, int(n), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return float(out[0]), float(out[1])
+
+    BITS_TESTS = ("zero", "twice", "order_less", "rate_key", "pos", "neg", "normal_pos", "abs_less",
+                  "minmod", "half", "fabs", "flip", "le_nonneg", "below_floor", "finite")
+
+    def selftest_bits(self, n: int = 1 << 22):
+        """Mismatches of each integer-pipe helper against its FP64 definition."""
+        out = np.zeros(len(self.BITS_TESTS), dtype=np.int64)
+        self._check(lib().wb_selftest_bits(self._h, int(n), out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))))
+        return dict(zip(self.BITS_TESTS, (int(x) for x in out)))
 
     def stage(self, which: int):
         nx, ny, nz = self.n

@@ -803,6 +803,17 @@ int wb_selftest_math(wb_grid* g, int n, double worst[2]) {
   return WB_OK;
 }
 
+int wb_selftest_bits(wb_grid* g, int n, long long counts[WB_BITS_TESTS]) {
+  if (!g || !counts || n < 1) return fail(g, WB_ERR_INVALID, "bad argument");
+  cudaError_t e = cudaMemsetAsync(g->red, 0, WB_BITS_TESTS * sizeof(unsigned long long), g->stream);
+  if (e != cudaSuccess) return check_cuda(g, e, "selftest");
+  wb_launch_bits_selftest(n, g->red, g->stream);
+  e = cudaMemcpyAsync(counts, g->red, WB_BITS_TESTS * sizeof(long long), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return check_cuda(g, e, "selftest");
+  return WB_OK;
+}
+
 int wb_measure_fp64_peak(void* stream, double* flops) {
   if (!flops) return WB_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -92,6 +92,7 @@ void wb_launch_copy_box(const double* src, long long slot, const WbGeo& geo, con
                         double* dst, cudaStream_t s);
 void wb_launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
 void wb_launch_math_selftest(int n, unsigned long long* worst, cudaStream_t s);
+void wb_launch_bits_selftest(int n, unsigned long long* counts, cudaStream_t s);
 
 // check words of the translation units (checked build; 0 otherwise)
 unsigned wb_check_take_sweep();

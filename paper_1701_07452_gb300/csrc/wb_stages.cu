@@ -2,6 +2,7 @@
 // Steps 2-5 and 7-11) plus the ghost fill, time step and diagnostics.
 // Every kernel maps one thread to one zone, face or edge of an index box and
 // one patch slot (blockIdx.y); all arrays share the padded patch geometry.
+#include "../../include/wombat.h"
 #include "wb_device.cuh"
 #include "wb_internal.h"
 #include <cstring>
@@ -574,3 +575,96 @@ void wb_launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {
 }
 
 WB_CHECK_ACCESSOR(wb_check_take_stages)
+
+// Self-test of the integer-pipe helpers against their FP64 definitions: for
+// each helper, the number of inputs on which the two disagree (counts[h],
+// h < WB_BITS_TESTS).  Inputs: a table of special values (signed zeros,
+// subnormals, the normal range's ends, infinities, NaN) paired with each
+// other, then random bit patterns (every class of double, NaN included) and
+// pairs of nearby or opposite values.
+namespace {
+constexpr int kSpecials = 16;
+__device__ double special_value(int k) {
+  const double tiny = __longlong_as_double(1LL);                      // smallest subnormal
+  const double sub = __longlong_as_double(0x000fffffffffffffLL);      // largest subnormal
+  const double v[kSpecials] = {0.0, -0.0, tiny, -tiny, sub, -sub, 2.2250738585072014e-308,
+                               -2.2250738585072014e-308, 1.0, -1.0, 1.7976931348623157e308,
+                               -1.7976931348623157e308, __longlong_as_double(0x7ff0000000000000LL),
+                               __longlong_as_double((long long)0xfff0000000000000ULL),
+                               __longlong_as_double(0x7ff8000000000000LL), 4.4501477170144028e-308};
+  return v[k];
+}
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ bool same_bits(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+__global__ void k_bits_selftest(int n, unsigned long long* counts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a, b;
+  if (i < kSpecials * kSpecials) {
+    a = special_value(i / kSpecials);
+    b = special_value(i % kSpecials);
+  } else {
+    const unsigned long long za = mix64(0x9e3779b97f4a7c15ULL * (unsigned long long)i);
+    const unsigned long long zb = mix64(za + 0x632be59bd9b4e019ULL);
+    a = __longlong_as_double((long long)za);
+    switch (i & 3) {
+      case 0: b = __longlong_as_double((long long)zb); break;            // independent pattern
+      case 1: b = __longlong_as_double((long long)za + 1 - (long long)(zb & 2)); break;  // one ulp away
+      case 2: b = -a; break;
+      default: b = a; break;
+    }
+  }
+  const bool na = isnan(a), nb = isnan(b);
+  unsigned bad = 0;
+  // 0 zero test
+  if (wb_zero(a) != (a == 0.0)) bad |= 1u << 0;
+  // 1 exact doubling
+  { const double t = wb_twice(a), r = a + a;
+    if (na ? !isnan(t) : !same_bits(t, r)) bad |= 1u << 1; }
+  // 2 order of the values (signed zeros and NaN excluded)
+  if (!na && !nb && !(a == 0.0 && b == 0.0) && wb_order_less(a, b) != (a < b)) bad |= 1u << 2;
+  // 3 signal-rate key
+  { const unsigned long long want = na ? 0x7ff8000000000000ULL
+                                       : (a > 0.0 ? (unsigned long long)__double_as_longlong(a) : 0ULL);
+    if (wb_rate_bits(a) != want) bad |= 1u << 3; }
+  // 4 positive and finite, 5 negative, 6 positive normal, 14 finite
+  if (wb_pos(a) != (a > 0.0 && isfinite(a))) bad |= 1u << 4;
+  if (wb_neg(a) != (a < 0.0)) bad |= 1u << 5;
+  if (wb_normal_pos(a) != (a >= 2.2250738585072014e-308 && isfinite(a))) bad |= 1u << 6;
+  if (wb_finite(a) != (bool)isfinite(a)) bad |= 1u << 14;
+  // 7 magnitude order, 8 minmod (values; NaN excluded)
+  if (!na && !nb) {
+    if (wb_abs_less(a, b) != (fabs(a) < fabs(b))) bad |= 1u << 7;
+    const bool same_sign = (a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0);
+    const double mm = same_sign ? (fabs(a) < fabs(b) ? a : b) : 0.0;
+    if (!(wb_minmod(a, b) == mm)) bad |= 1u << 8;
+  }
+  // 9 halving, exact for |a| >= 2^-1021 and for inf / NaN (documented domain)
+  if (na ? !isnan(wb_half(a)) : (fabs(a) >= 4.4501477170144028e-308 && !same_bits(wb_half(a), a * 0.5)))
+    bad |= 1u << 9;
+  // 10 absolute value, 11 negation (bit patterns)
+  if (!same_bits(wb_fabs(a), __longlong_as_double(__double_as_longlong(a) & 0x7fffffffffffffffLL)))
+    bad |= 1u << 10;
+  if (!same_bits(wb_flip(a), __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ULL)))
+    bad |= 1u << 11;
+  // 12 a <= b for non-negative operands
+  { const double x = fabs(a), y = fabs(b);
+    if (!isnan(x) && !isnan(y) && wb_le_nonneg(x, y) != (x <= y)) bad |= 1u << 12; }
+  // 13 below a finite, non-negative floor
+  { const double f = fabs(b);
+    if (isfinite(f) && wb_below_floor(a, f) != (a < f)) bad |= 1u << 13; }
+  for (int h = 0; h < WB_BITS_TESTS; ++h)
+    if (bad & (1u << h)) atomicAdd(&counts[h], 1ULL);
+}
+}  // namespace
+
+void wb_launch_bits_selftest(int n, unsigned long long* counts, cudaStream_t s) {
+  k_bits_selftest<<<(n + 255) / 256, 256, 0, s>>>(n, counts);
+}

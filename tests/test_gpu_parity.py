@@ -261,6 +261,18 @@ def test_fp64_reciprocal_helpers_match_cuda(wb):
     assert e_rsq < 4.5e-16, e_rsq
 
 
+def test_integer_pipe_helpers_match_fp64_definitions(wb):
+    """Every bit-pattern helper that stands in for an FP64 compare, a sign
+    operation or a power-of-two scaling (zero and sign tests, orders, minmod,
+    the signal-rate max key, halving and exact doubling) agrees with its FP64
+    definition on all pairs of 16 special values and on 4M random bit patterns
+    (NaN, infinities, subnormals and signed zeros included)."""
+    g = wb.Grid((8, 8, 8))
+    bad = g.selftest_bits(1 << 22)
+    assert len(bad) == 15
+    assert all(v == 0 for v in bad.values()), bad
+
+
 def test_lagged_dt_parity(wb, oracle_mod):
     from paper_1701_07452_gb300.initial_conditions import random_box
     st = random_box(12, seed=21)
