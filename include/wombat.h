@@ -330,8 +330,8 @@ int wb_selftest_math(wb_grid* g, int n, double worst[2]);
  * number of n inputs on which helper h disagrees with its FP64 definition,
  * for h = 0 zero test (x == 0), 1 exact doubling (x + x), 2 order (a < b),
  * 3 signal-rate max key, 4 x > 0 and finite, 5 x < 0, 6 positive normal,
- * 7 |a| < |b|, 8 minmod, 9 halving (x / 2 for |x| >= 2^-1021), 10 |x|,
- * 11 -x, 12 a <= b for a, b >= 0, 13 x below a finite floor >= 0,
+ * 7 |a| < |b|, 8 minmod, 9 halving (x / 2 for |x| >= 2^-1021), 10 |x| and
+ * 11 -x (not NaN), 12 a <= b for a, b >= 0, 13 x below a finite floor >= 0,
  * 14 finiteness.  The inputs: every pair of 16 special values (signed
  * zeros, subnormals, the ends of the normal range, infinities, NaN), then
  * random bit patterns with independent, adjacent, opposite or equal
