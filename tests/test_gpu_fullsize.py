@@ -7,11 +7,15 @@ The oracle runs one full step of the whole box on the host cores (seconds),
 so every zone is compared after one step, with the 1-step tolerance of the
 parity tests.  Later steps are checked by what holds at any size: every
 conserved total, div b at roundoff, and the CFL time step of the evolved
-state against the oracle's dt of the same state."""
+state against the oracle's dt of the same state.  The full 100 steps of the
+box, every zone against the oracle, take about ten minutes of oracle time on
+16 host cores and run when WB_FULLSIZE_LONG=1 is set."""
+import os
+
 import numpy as np
 import pytest
 
-from parity import state_err
+from parity import TIGHT, state_err
 
 pytestmark = pytest.mark.gpu
 
@@ -87,3 +91,28 @@ def test_full_size_batch_equals_grid(wb, state):
     bt.advance(2)
     for a, b in zip(bt.read(0), g.read()):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.skipif(os.environ.get("WB_FULLSIZE_LONG") != "1",
+                    reason="about ten minutes of oracle time: set WB_FULLSIZE_LONG=1")
+def test_full_size_hundred_steps_every_zone(wb, oracle_mod, state):
+    """The bench's 256^3 box after 100 steps, every zone against the oracle
+    at the 100-step tolerance (1e-8 per zone, under both guards), the time
+    reached to 1e-11 and the conserved totals to 1e-12 of their scale."""
+    n = (N, N, N)
+    g = wb.Grid(n, length=state["length"])
+    g.load_state(state)
+    o = oracle_mod.Grid(n, state["length"])
+    o.load_state(state)
+    t_g = g.advance(100)
+    t_o = o.advance(100)
+    assert abs(t_g - t_o) <= 1e-11 * t_o
+    gs, os_ = g.read(), o.read()
+    err, err_tight = state_err(gs, os_), state_err(gs, os_, TIGHT)
+    print(f"256^3 x 100 steps: max rel err {err:.3e} (guard 1e-3 of the box maximum), "
+          f"{err_tight:.3e} (guard 1e-6); t = {t_g:.6f}")
+    assert err < 1e-8 and err_tight < 1e-8
+    tg, to = g.totals(), o.totals()
+    scale = np.array([abs(to[0])] * 4 + [abs(to[4])] + [1.0] * 3)
+    assert np.all(np.abs(tg - to) <= 1e-12 * np.maximum(scale, np.abs(to)))
+    assert g.counters()["unphysical"] == 0
