@@ -549,6 +549,14 @@ __device__ __forceinline__ void eref(const WbView& v, long long qo, long long wo
   eref_finish(v, in);
 }
 
+// The mean of the two one-sided differences, for a zero mass flux.  Not
+// inlined: inlined, the compiler if-converts it and every warp issues its
+// instructions with every lane predicated off (the FP64 pipe's warp-level
+// count exceeded its thread-level count by a third in the corner-EMF kernel).
+static __device__ __noinline__ double mean_diff(double xm, double ym, double x0, double y0) {
+  return __dmul_rn(0.5, __dadd_rn(__dsub_rn(xm, ym), __dsub_rn(x0, y0)));
+}
+
 // Difference x - y upwind of the mass flux m: (xm - ym) from the minus-side
 // zone if m > 0, (x0 - y0) from the plus-side zone if m < 0, the mean of both
 // if m = 0.  The operands are selected first (integer pipe), so one FP64
@@ -556,10 +564,11 @@ __device__ __forceinline__ void eref(const WbView& v, long long qo, long long wo
 // has a zero mass flux, so the common case carries none of its arithmetic.
 __device__ __forceinline__ double upwind_diff(double m, double xm, double ym, double x0, double y0) {
   const bool minus = wb_neg(m);
-  double d = (minus ? x0 : xm) - (minus ? y0 : ym);
+  double d = __dsub_rn(minus ? x0 : xm, minus ? y0 : ym);
   const bool zero = wb_zero(m);
   if (__any_sync(__activemask(), zero)) {
-    if (zero) d = 0.5 * ((xm - ym) + (x0 - y0));
+    const double mean = mean_diff(xm, ym, x0, y0);
+    if (zero) d = mean;
   }
   return d;
 }
