@@ -67,14 +67,14 @@ ALG_FLOPS_PER_CELL_UPDATE = 5871.0
 # profiles/stages_96cube_fp64_counts.md).  Counted per face of the box the
 # figure leaves out the ~2 % of overlap systems a 256^3 launch adds.
 EXEC_FLOPS_PER_FACE = 451.5
-EXEC_STAGE_FLOPS_PER_ZONE = 443.8
+EXEC_STAGE_FLOPS_PER_ZONE = 444.2
 # DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the
 # mean of the six sweeps of a step from one ncu capture
 # (profiles/k_sweep_256cube_dram.md), valid only for the kernel sources it was
 # taken on (their SHA-256 over csrc/wb_sweep.cu, wb_units.cuh, wb_device.cuh);
 # the algorithmic figure is 128 B per face.
-SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.6818e9,
-                      "src_sha256": "2842b47755d90d507764d582904c199eb233cc684bcc362211d69b2f692bb9dd"}
+SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.6815e9,
+                      "src_sha256": "6bf5eae760bdb4f2453898b9f62a885d66b0299e039e0aa2f79f3fe6ab090d39"}
 SWEEP_BYTES_PER_FACE = 128.0
 # algorithmic state bytes per cell-update: 5 conserved fields and 3 face fields
 # read and written once (the step's HBM roofline)

@@ -126,9 +126,13 @@ using Rec = RecT<kBlock>;
 // EZ have eps_k = 0, where Q is |nu|; the branch test runs on the integer pipe.
 template <int EZ>
 __device__ __forceinline__ double Qk_m_nu2(double nu, int k, const WbPhys& P) {
-  if ((EZ & (1 << k)) || !wb_abs_less(nu, P.two_eps[k])) return WB_FMA(-nu, nu, wb_fabs(nu));
-  // |nu| < 2 eps: nu^2 / (4 eps) + eps - nu^2 = nu^2 (1/(4 eps) - 1) + eps
-  return WB_FMA(WB_MUL(nu, nu), P.inv4eps_m1[k], P.eps[k]);
+  if (EZ & (1 << k)) return WB_FMA(-nu, nu, wb_fabs(nu));
+  // |nu| - nu^2, or for |nu| < 2 eps nu^2 / (4 eps) + eps - nu^2 = nu^2 (1/(4 eps) - 1) + eps:
+  // one FMA of operands chosen on the integer pipe, FMA(x, nu, y) with (x, y) = (-nu, |nu|)
+  // or (nu (1/(4 eps) - 1), eps), so that no warp issues both forms
+  const bool band = wb_abs_less(nu, P.two_eps[k]);
+  const double x = band ? WB_MUL(nu, P.inv4eps_m1[k]) : wb_flip(nu);
+  return WB_FMA(x, nu, band ? P.eps[k] : wb_fabs(nu));
 }
 
 // Gas pressure of a zone from its sweep-frame fields (Sec. 3, Eq. totenergy)
