@@ -67,7 +67,7 @@ ALG_FLOPS_PER_CELL_UPDATE = 5871.0
 # profiles/stages_96cube_fp64_counts.md).  Counted per face of the box the
 # figure leaves out the ~2 % of overlap systems a 256^3 launch adds.
 EXEC_FLOPS_PER_FACE = 451.5
-EXEC_STAGE_FLOPS_PER_ZONE = 444.2
+EXEC_STAGE_FLOPS_PER_ZONE = 435.0
 # DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the
 # mean of the six sweeps of a step from one ncu capture
 # (profiles/k_sweep_256cube_dram.md), valid only for the kernel sources it was

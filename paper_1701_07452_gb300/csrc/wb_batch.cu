@@ -281,7 +281,8 @@ __device__ __forceinline__ void unit_item(const BatchParams& B, int s, int d, in
   switch (s) {
     case BS_TRANS: {
       const int mask = trans_mask(n, i, j, k);
-      if (mask) wbu::transverse_set(v, 0, 0, dt, mask, i, j, k);
+      if (mask == 7) wbu::transverse_set(v, 0, 0, dt, 7, i, j, k);  // constant mask: see k_transverse
+      else if (mask) wbu::transverse_set(v, 0, 0, dt, mask, i, j, k);
       break;
     }
     case BS_EREF_H: wbu::eref_half(v, 0, 0, dt, i, j, k); break;
@@ -711,7 +712,8 @@ __global__ void __launch_bounds__(kNtZone, zone_min_blocks(CLS))
       item_ijk(b, it, &i, &j, &k);
       if (CLS == SC_TRANS) {
         const int mask = trans_mask(v.geo.n, i, j, k);
-        if (mask) wbu::transverse_set(v, 0, 0, dt, mask, i, j, k);
+        if (mask == 7) wbu::transverse_set(v, 0, 0, dt, 7, i, j, k);  // constant mask: see k_transverse
+        else if (mask) wbu::transverse_set(v, 0, 0, dt, mask, i, j, k);
       } else if (CLS == SC_EREF_H) {
         wbu::eref_half(v, 0, 0, dt, i, j, k);
       } else {
