@@ -95,7 +95,8 @@ __device__ __forceinline__ void load_cell(const double* const* q, long long off,
 }
 
 // Per-face record (shared memory, structure of arrays over the block).
-// R_PG = rho a^2 / (gamma-1); R_KX = v^2/2 + (gamma-2)/(gamma-1) X;
+// R_PG = rho a^2 / (gamma-1); R_KX = (gamma-2)/(gamma-1) X - v^2/2 (= K - v^2 for the
+// K = v^2/2 + (gamma-2)/(gamma-1) X of the energy row);
 // R_AFCF = alpha_f c_f, R_ASCS = alpha_s c_s.
 enum {
   R_AL = 0, R_NU = 7, R_RHO = 14, R_SRHO, R_A, R_PG, R_CF, R_ASCS, R_AFCF, R_AF, R_AS, R_B1, R_B2, R_S,
@@ -316,16 +317,18 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   const double dpr = WB_MUL(dp, ri2a2);
   const double afcf = WB_MUL(af, cf), ascs = WB_MUL(as, cs);
   const double dbbi = WB_MUL(dbb, i2ra);
-  const double Af = WB_MUL(WB_FMA(afcf, dvn, -WB_MUL(ascs, dvbS)), ri2a2);
+  // alpha_{1,7} = Cf -+ Xf / (2 rho a^2), alpha_{3,5} = Cs -+ Xs / (2 rho a^2): the factor
+  // goes into the FMAs that form them
+  const double Xf = WB_FMA(afcf, dvn, -WB_MUL(ascs, dvbS));
   const double Cf = WB_FMA(as, dbbi, WB_MUL(af, dpr));
-  const double As = WB_MUL(WB_FMA(ascs, dvn, WB_MUL(afcf, dvbS)), ri2a2);
+  const double Xs = WB_FMA(ascs, dvn, WB_MUL(afcf, dvbS));
   const double Cs = WB_FMA(-af, dbbi, WB_MUL(as, dpr));
   const double hAa = WB_MUL(hisr, dbpS);
   double al[7];
-  al[0] = WB_SUB(Cf, Af);
-  al[6] = WB_ADD(Cf, Af);
-  al[2] = WB_SUB(Cs, As);
-  al[4] = WB_ADD(Cs, As);
+  al[0] = WB_FMA(-ri2a2, Xf, Cf);
+  al[6] = WB_FMA(ri2a2, Xf, Cf);
+  al[2] = WB_FMA(-ri2a2, Xs, Cs);
+  al[4] = WB_FMA(ri2a2, Xs, Cs);
   al[1] = WB_FMA(hir, dvp, hAa);
   al[5] = WB_FMA(hir, dvp, -hAa);
   al[3] = WB_FMA(-dp, ia2, drho);
@@ -343,7 +346,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   f[R_RHO] = rho; f[R_SRHO] = srho; f[R_A] = a; f[R_PG] = WB_MUL(ra2, P.inv_gm1); f[R_CF] = cf;
   f[R_ASCS] = ascs; f[R_AFCF] = afcf; f[R_AF] = af; f[R_AS] = as; f[R_B1] = b1n; f[R_B2] = b2n; f[R_S] = S;
   f[R_VN] = vn; f[R_VT1] = vt1; f[R_VT2] = vt2; f[R_BT1] = bt1; f[R_BT2] = bt2;
-  f[R_KX] = WB_FMA(gX, P.inv_gm1, hv2);
+  f[R_KX] = WB_FMA(gX, P.inv_gm1, -hv2);  // K - v^2 (the energy row of face_flux)
 #pragma unroll
   for (int m = 0; m < 7; ++m) f[R_FAVG + m] = WB_ADD(L.F[m], R.F[m]);
   if (PROT && P.prot && protection_hit(L, R, rho, ra2, af, as, al, P)) return 1;
@@ -407,9 +410,10 @@ __device__ __forceinline__ void face_flux(const Rc& f, const double gi[7], const
   const double u1 = WB_FMA(vn, wr, WB_MUL(rho, wvn));
   const double u2 = WB_FMA(vt1, wr, WB_MUL(rho, wvt1));
   const double u3 = WB_FMA(vt2, wr, WB_MUL(rho, wvt2));
-  const double vw = WB_FMA(vn, wvn, WB_FMA(vt1, wvt1, WB_MUL(vt2, wvt2)));
-  const double u6 = WB_FMA(f[R_BT2], wbt2, WB_FMA(f[R_BT1], wbt1,
-                    WB_FMA(rho, vw, WB_FMA(f[R_PG], tfs, WB_MUL(f[R_KX], wr)))));
+  // energy: B_t . w_Bt + p/(gamma-1) row + K w_rho + rho v . w_v, with
+  // rho v . w_v = v . u - v^2 w_rho and the record holding K - v^2
+  const double u6 = WB_FMA(f[R_BT2], wbt2, WB_FMA(f[R_BT1], wbt1, WB_FMA(f[R_PG], tfs,
+                    WB_FMA(f[R_KX], wr, WB_FMA(vn, u1, WB_FMA(vt1, u2, WB_MUL(vt2, u3)))))));
   out[0] = WB_FMA(-dx_2dt, wr, f[R_FAVG + 0]);
   out[1] = WB_FMA(-dx_2dt, u1, f[R_FAVG + 1]);
   out[2] = WB_FMA(-dx_2dt, u2, f[R_FAVG + 2]);
