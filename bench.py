@@ -66,15 +66,15 @@ ALG_FLOPS_PER_CELL_UPDATE = 5871.0
 # kernels of the step together (profiles/k_sweep_96cube_ncu_full.md,
 # profiles/stages_96cube_fp64_counts.md).  Counted per face of the box the
 # figure leaves out the ~2 % of overlap systems a 256^3 launch adds.
-EXEC_FLOPS_PER_FACE = 452.6
-EXEC_STAGE_FLOPS_PER_ZONE = 431.4
+EXEC_FLOPS_PER_FACE = 450.8
+EXEC_STAGE_FLOPS_PER_ZONE = 431.8
 # DRAM bytes (read + write) of one k_sweep launch at the 256^3 workload, the
 # mean of the six sweeps of a step from one ncu capture
 # (profiles/k_sweep_256cube_dram.md), valid only for the kernel sources it was
 # taken on (their SHA-256 over csrc/wb_sweep.cu, wb_units.cuh, wb_device.cuh);
 # the algorithmic figure is 128 B per face.
-SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.6810e9,
-                      "src_sha256": "1698ae0d42bea25f34e7e89b5533682861982fc216e732144da5609a649fd2d3"}
+SWEEP_DRAM_CAPTURE = {"n": 256, "bytes": 3.6763e9,
+                      "src_sha256": "68f8615198707e20999cb9332cdfca1bc16d4505845845c06e39a34523ecfa46"}
 SWEEP_BYTES_PER_FACE = 128.0
 # algorithmic state bytes per cell-update: 5 conserved fields and 3 face fields
 # read and written once (the step's HBM roofline)

@@ -36,7 +36,7 @@ namespace {
 
 // threads per block and resident blocks per SM the sweep is compiled for
 // (registers per thread follow from their product; the face records take
-// 2 x 39 doubles per thread of shared memory)
+// 2 x 38 doubles per thread of shared memory)
 #ifndef WB_SWEEP_BLOCK
 #define WB_SWEEP_BLOCK 64
 #endif

@@ -100,7 +100,7 @@ __device__ __forceinline__ void load_cell(const double* const* q, long long off,
 // R_AFCF = alpha_f c_f, R_ASCS = alpha_s c_s.
 enum {
   R_AL = 0, R_NU = 7, R_RHO = 14, R_SRHO, R_A, R_PG, R_CF, R_ASCS, R_AFCF, R_AF, R_AS, R_B1, R_B2, R_S,
-  R_VN, R_VT1, R_VT2, R_BT1, R_BT2, R_KX, R_FAVG, R_WORDS = R_FAVG + 7
+  R_VN, R_VT1, R_VT2, R_BTM, R_KX, R_FAVG, R_WORDS = R_FAVG + 7
 };
 
 // One thread's face record in shared memory, word w at p[w * BS] (the block's
@@ -257,10 +257,11 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   const double cs = WB_MUL(WB_MUL(a, ca), icf);  // c_f c_s = a c_a
   // 1/|B_t| and c_t = |B_t| / sqrt(rho_); a transverse field whose square is
   // not a normal double (underflowing noise ahead of a front) counts as 0
-  double ib = 0.0, ct = 0.0;
+  double ib = 0.0, ct = 0.0, btm = 0.0;  // btm = |B_t|
   if (wb_normal_pos(bt2s)) {
     ib = wb_rsqrt(bt2s);
-    ct = WB_MUL(WB_MUL(bt2s, ib), isrho);
+    btm = WB_MUL(bt2s, ib);
+    ct = WB_MUL(btm, isrho);
   }
   double af, as;
   if (wb_le_nonneg(sd, WB_MUL(1e-12, sum))) {
@@ -345,7 +346,7 @@ __device__ __forceinline__ int face_system(const Cell& L, const Cell& R, double 
   }
   f[R_RHO] = rho; f[R_SRHO] = srho; f[R_A] = a; f[R_PG] = WB_MUL(ra2, P.inv_gm1); f[R_CF] = cf;
   f[R_ASCS] = ascs; f[R_AFCF] = afcf; f[R_AF] = af; f[R_AS] = as; f[R_B1] = b1n; f[R_B2] = b2n; f[R_S] = S;
-  f[R_VN] = vn; f[R_VT1] = vt1; f[R_VT2] = vt2; f[R_BT1] = bt1; f[R_BT2] = bt2;
+  f[R_VN] = vn; f[R_VT1] = vt1; f[R_VT2] = vt2; f[R_BTM] = btm;
   f[R_KX] = WB_FMA(gX, P.inv_gm1, -hv2);  // K - v^2 (the energy row of face_flux)
 #pragma unroll
   for (int m = 0; m < 7; ++m) f[R_FAVG + m] = WB_ADD(L.F[m], R.F[m]);
@@ -411,9 +412,13 @@ __device__ __forceinline__ void face_flux(const Rc& f, const double gi[7], const
   const double u2 = WB_FMA(vt1, wr, WB_MUL(rho, wvt1));
   const double u3 = WB_FMA(vt2, wr, WB_MUL(rho, wvt2));
   // energy: B_t . w_Bt + p/(gamma-1) row + K w_rho + rho v . w_v, with
-  // rho v . w_v = v . u - v^2 w_rho and the record holding K - v^2
-  const double u6 = WB_FMA(f[R_BT2], wbt2, WB_FMA(f[R_BT1], wbt1, WB_FMA(f[R_PG], tfs,
-                    WB_FMA(f[R_KX], wr, WB_FMA(vn, u1, WB_FMA(vt1, u2, WB_MUL(vt2, u3)))))));
+  // rho v . w_v = v . u - v^2 w_rho and the record holding K - v^2, and
+  // B_t . w_Bt = |B_t| w_beta: beta is B_t / |B_t|, so the beta-perpendicular
+  // part has no component along B_t (where |B_t|^2 is below 1e-24 of the
+  // energy scale and beta is set to (1, 1)/sqrt 2 instead, the term is of that
+  // size either way)
+  const double u6 = WB_FMA(f[R_BTM], bb, WB_FMA(f[R_PG], tfs,
+                    WB_FMA(f[R_KX], wr, WB_FMA(vn, u1, WB_FMA(vt1, u2, WB_MUL(vt2, u3))))));
   out[0] = WB_FMA(-dx_2dt, wr, f[R_FAVG + 0]);
   out[1] = WB_FMA(-dx_2dt, u1, f[R_FAVG + 1]);
   out[2] = WB_FMA(-dx_2dt, u2, f[R_FAVG + 2]);
