@@ -219,6 +219,19 @@ def test_linear_wave_second_order_1d(oracle_mod, mode):
     assert slope > 1.7, (errs, slope)
 
 
+@pytest.mark.skipif(os.environ.get("WB_ORACLE_LONG") != "1",
+                    reason="about ten minutes of oracle time: set WB_ORACLE_LONG=1")
+@pytest.mark.parametrize("mode", ["fast", "alfven", "slow", "entropy"])
+def test_linear_wave_second_order_1d_to_1024(oracle_mod, mode):
+    """Second order up to N = 1024, the range over which the paper reports
+    the 1D modes converge (Sec. "Linear Wave Convergence")."""
+    errs = [wave_1d_error(oracle_mod, mode, n) for n in (256, 512, 1024)]
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    print(f"{mode}: L1 errors {errs}, slopes {slopes}")
+    assert errs[0] > errs[1] > errs[2]
+    assert min(slopes) > 1.8, (errs, slopes)
+
+
 def test_lagged_dt_sequence(oracle_mod):
     """dt_lag: step n takes the CFL dt of the start state of step n-1 (the
     paper delays the dt reduction by one step); steps 0 and 1 both take the
